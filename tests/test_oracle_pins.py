@@ -1,0 +1,352 @@
+"""Pins for the FP64 oracle (CPU only).
+
+Each test checks the oracle against something other than itself: a published
+generator output, a library routine (scipy's vq/kmeans2/cdist, numpy sorts),
+a hand-worked example, a closed form or an invariant of the method.  The
+method is PQ as described in Sec. 2.1 (per-subspace k-means, encode, decode),
+RMSE (Sec. 2.1/Sec. 3), the inverted index (Sec. 2.2) and the chunked fit
+(Sec. 3).
+"""
+import os
+
+import numpy as np
+import pytest
+from scipy.cluster.vq import kmeans2, vq
+from scipy.spatial.distance import cdist
+
+import oracle as orc
+from paper_2604_21645_gb300 import datagen
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _sections(path):
+    sec, out = None, {}
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line.isalpha() and line.isupper():
+            sec = line
+            out[sec] = []
+            continue
+        out[sec].append([float(v) for v in line.split()])
+    return out
+
+
+# -- generator -------------------------------------------------------------------
+
+def test_splitmix64_published_outputs():
+    vals = [int(l, 16) for l in open(os.path.join(GOLDEN, "splitmix64_seed0.txt")) if not l.startswith("#")]
+    assert [orc.sm64(0, i) for i in range(4)] == vals
+
+
+def test_scale53_is_uniform_index():
+    n = 1000
+    assert orc.scale53(0, n) == 0
+    assert orc.scale53((1 << 53) - 1, n) == n - 1
+    idx = [orc.scale53(orc.draw(7, 3, i) >> 11, 10) for i in range(20000)]
+    counts = np.bincount(idx, minlength=10)
+    # chi-square with 9 dof: 99.9th percentile is 27.9
+    chi2 = ((counts - 2000.0) ** 2 / 2000.0).sum()
+    assert chi2 < 27.9
+
+
+def test_streams_differ():
+    a = [orc.draw(1, 0, i) for i in range(8)]
+    b = [orc.draw(1, 1, i) for i in range(8)]
+    assert len(set(a) & set(b)) == 0
+
+
+# -- assignment and update (Sec. 2.1) ---------------------------------------------
+
+def test_assign_matches_scipy_vq():
+    rng = np.random.default_rng(0)
+    X = rng.normal(size=(300, 12)).astype(np.float32)
+    cb = rng.normal(size=(3, 20, 4)).astype(np.float32)
+    codes, mind, gap = orc.assign(X, cb)
+    for m in range(3):
+        ref, dist = vq(X[:, 4 * m:4 * m + 4].astype(np.float64), cb[m].astype(np.float64))
+        assert np.array_equal(codes[:, m], ref)
+        np.testing.assert_allclose(mind[:, m], dist ** 2, rtol=1e-12)
+        full = cdist(X[:, 4 * m:4 * m + 4].astype(np.float64), cb[m].astype(np.float64), "sqeuclidean")
+        full.sort(axis=1)
+        np.testing.assert_allclose(gap[:, m], full[:, 1] - full[:, 0], rtol=1e-9, atol=1e-12)
+
+
+def test_assign_ties_go_to_lowest_index():
+    X = np.array([[0.0, 0.0], [1.0, 1.0]], dtype=np.float32)
+    cb = np.array([[[5.0, 5.0], [1.0, 1.0], [1.0, 1.0], [0.0, 0.0], [0.0, 0.0]]], dtype=np.float32)
+    codes, _, gap = orc.assign(X, cb)
+    assert codes[:, 0].tolist() == [3, 1]
+    assert gap[:, 0].tolist() == [0.0, 0.0]
+    # equal distance on both sides of a point
+    X2 = np.array([[1.0]], dtype=np.float32)
+    cb2 = np.array([[[2.0], [0.0]]], dtype=np.float32)
+    assert orc.assign(X2, cb2)[0][0, 0] == 0
+
+
+def test_update_is_the_mean_and_keeps_empty():
+    rng = np.random.default_rng(1)
+    X = rng.normal(size=(500, 6)).astype(np.float32)
+    cb = rng.normal(size=(2, 9, 3)).astype(np.float32)
+    codes = rng.integers(0, 8, size=(500, 2)).astype(np.int32)  # centroid 8 stays empty
+    new, counts = orc.update(X, codes, cb)
+    for m in range(2):
+        sub = X[:, 3 * m:3 * m + 3].astype(np.float64)
+        for k in range(9):
+            sel = codes[:, m] == k
+            assert counts[m, k] == sel.sum()
+            if sel.any():
+                assert np.array_equal(new[m, k], sub[sel].mean(axis=0).astype(np.float32)) or \
+                    np.allclose(new[m, k], sub[sel].mean(axis=0), rtol=1e-7, atol=0)
+            else:
+                assert np.array_equal(new[m, k], cb[m, k])
+
+
+def test_lloyd_single_subspace_is_plain_kmeans():
+    """M = 1 reduces PQ fit to plain k-means; scipy's kmeans2 with a given init is the same Lloyd loop."""
+    X = datagen.mixture(3000, 4, 6, "cont", 11).astype(np.float64)
+    init = X[[5, 700, 1400, 2100, 2800, 2999]].copy()
+    ours, _ = orc.pq_fit(X.astype(np.float32), 1, 6, 15, 0, init=init[None].astype(np.float32))
+    ref, lab = kmeans2(X, init.copy(), iter=15, minit="matrix", missing="raise")
+    np.testing.assert_allclose(ours[0], ref, rtol=2e-6, atol=2e-7)
+
+
+def test_lloyd_subspaces_are_independent_kmeans():
+    X = datagen.mixture(2000, 8, 5, "cont", 12)
+    M, Ks = 2, 5
+    init = np.stack([X[[1, 400, 800, 1200, 1600], 4 * m:4 * m + 4] for m in range(M)])
+    ours, _ = orc.pq_fit(X, M, Ks, 10, 0, init=init)
+    for m in range(M):
+        ref, _ = kmeans2(X[:, 4 * m:4 * m + 4].astype(np.float64), init[m].astype(np.float64), iter=10,
+                         minit="matrix", missing="raise")
+        np.testing.assert_allclose(ours[m], ref, rtol=2e-6, atol=2e-7)
+
+
+def test_lloyd_sse_never_increases():
+    X = datagen.mixture(4000, 16, 12, "cont", 13)
+    _, sse = orc.pq_fit(X, 4, 32, 20, 99)
+    assert np.all(np.diff(sse) <= 1e-9 * sse[:-1])
+    assert sse[-1] < sse[0]
+
+
+def test_sse_matches_rmse_after_fit():
+    X = datagen.mixture(1500, 8, 4, "cont", 14)
+    cb, sse = orc.pq_fit(X, 2, 8, 5, 3)
+    # an extra zero-iteration fit from the result: its assignment SSE equals N*D*RMSE^2
+    codes = orc.pq_encode(X, cb)
+    r = orc.pq_rmse(X, codes, cb)
+    _, sse2 = orc.pq_fit(X, 2, 8, 1, 0, init=cb)
+    np.testing.assert_allclose(sse2[0], r * r * X.size, rtol=1e-12)
+
+
+# -- k-means++ seeding --------------------------------------------------------------
+
+def test_kmeanspp_distinct_points_all_picked():
+    """Ks equal to the number of distinct points: every point becomes a seed, so the error is 0."""
+    rng = np.random.default_rng(2)
+    X = rng.normal(size=(32, 6)).astype(np.float32)
+    cb = orc.kmeanspp(X, 3, 32, 5)
+    for m in range(3):
+        got = {tuple(r) for r in cb[m]}
+        want = {tuple(r) for r in X[:, 2 * m:2 * m + 2]}
+        assert got == want
+    codes = orc.pq_encode(X, cb)
+    assert orc.pq_rmse(X, codes, cb) == 0.0
+
+
+def test_kmeanspp_d2_sampling_frequencies():
+    """Second seed drawn with probability proportional to the squared distance to the first."""
+    X = np.array([[0.0], [1.0], [3.0], [6.0]], dtype=np.float32)
+    trials = 12000
+    first = np.zeros(4)
+    second = np.zeros((4, 4))
+    for s in range(trials):
+        cb = orc.kmeanspp(X, 1, 2, s)
+        i0 = int(np.where(X[:, 0] == cb[0, 0, 0])[0][0])
+        i1 = int(np.where(X[:, 0] == cb[0, 1, 0])[0][0])
+        first[i0] += 1
+        second[i0, i1] += 1
+    chi2 = ((first - trials / 4) ** 2 / (trials / 4)).sum()
+    assert chi2 < 16.3  # 3 dof, 99.9th percentile
+    for i0 in range(4):
+        d2 = (X[:, 0] - X[i0, 0]) ** 2
+        p = d2 / d2.sum()
+        exp = p * first[i0]
+        mask = exp > 0
+        assert second[i0, ~mask].sum() == 0  # zero-weight points never drawn
+        chi2 = ((second[i0, mask] - exp[mask]) ** 2 / exp[mask]).sum()
+        assert chi2 < 16.3
+
+
+def test_kmeanspp_single_positive_weight():
+    X = np.array([[1.0], [1.0], [1.0], [9.0], [1.0]], dtype=np.float32)
+    for s in range(50):
+        cb = orc.kmeanspp(X, 1, 2, s)
+        assert set(cb[0, :, 0].tolist()) == {1.0, 9.0}
+
+
+def test_kmeanspp_subsample_rows_are_data_rows():
+    X = datagen.mixture(30000, 4, 3, "cont", 15)  # N > 100*Ks for Ks = 8
+    cb = orc.kmeanspp(X, 2, 8, 1)
+    for m in range(2):
+        sub = X[:, 2 * m:2 * m + 2]
+        for r in cb[m]:
+            assert np.any(np.all(sub == r, axis=1))
+
+
+# -- encode / decode / RMSE (Sec. 2.1, Sec. 3) ---------------------------------------
+
+def test_rmse_hand_worked_example():
+    g = _sections(os.path.join(GOLDEN, "rmse_4x4.txt"))
+    X = np.array(g["X"], dtype=np.float32)
+    cb = np.zeros((2, 2, 2), dtype=np.float32)
+    for m, k, a, b in g["CODEBOOK"]:
+        cb[int(m), int(k)] = (a, b)
+    codes = orc.pq_encode(X, cb)
+    assert codes.tolist() == np.array(g["CODES"], dtype=np.uint8).tolist()
+    np.testing.assert_allclose(orc.pq_rmse(X, codes, cb), g["RMSE"][0][0], rtol=1e-15)
+
+
+def test_decode_reconstruction_and_zero_rmse():
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=(16, 8)).astype(np.float32)
+    cb = np.stack([X[:, 2 * m:2 * m + 2] for m in range(4)])  # every row is a codeword
+    codes = orc.pq_encode(X, cb)
+    assert np.array_equal(orc.pq_decode(codes, cb), X)
+    assert orc.pq_rmse(X, codes, cb) == 0.0
+
+
+def test_more_subspaces_or_codewords_lower_rmse():
+    """Sec. 2.1: a larger M or Ks gives a lower reconstruction error (trend on mixture data)."""
+    X = datagen.mixture(6000, 16, 64, "cont", 16)
+    def rmse(M, Ks):
+        cb, _ = orc.pq_fit(X, M, Ks, 8, 4)
+        return orc.pq_rmse(X, orc.pq_encode(X, cb), cb)
+    assert rmse(8, 16) < rmse(4, 16) < rmse(2, 16)
+    assert rmse(4, 64) < rmse(4, 16) < rmse(4, 4)
+
+
+# -- inverted index (Sec. 2.2, Sec. 3.1) ----------------------------------------------
+
+def _small_index(seed=17, N=3000, D=16, M=4, Ks=16, nlist=12):
+    X = datagen.mixture(N, D, 20, "int255", seed)
+    cb, _ = orc.pq_fit(X, M, Ks, 6, seed)
+    codes = orc.pq_encode(X, cb)
+    idx = orc.ivf_build(X, codes, nlist, 6, seed + 1)
+    return X, cb, codes, idx
+
+
+def test_ivf_lists_partition_rows():
+    X, cb, codes, idx = _small_index()
+    off, ids = idx["offsets"], idx["ids"]
+    assert off[0] == 0 and off[-1] == X.shape[0]
+    assert np.array_equal(np.sort(ids), np.arange(X.shape[0]))
+    lab = cdist(X.astype(np.float64), idx["coarse"].astype(np.float64), "sqeuclidean").argmin(axis=1)
+    assert np.array_equal(idx["list_of_row"], lab)
+    for l in range(len(off) - 1):
+        seg = ids[off[l]:off[l + 1]]
+        assert np.all(np.diff(seg) > 0)
+        assert np.all(lab[seg] == l)
+        assert np.array_equal(idx["list_codes"][off[l]:off[l + 1]], codes[seg])
+
+
+def test_ivf_full_probe_equals_exhaustive_adc():
+    X, cb, codes, idx = _small_index()
+    Q = datagen.queries(40, X.shape[1], 20, "int255", 17)
+    M, Ks, ds = cb.shape
+    ids, dist, _ = orc.ivf_search(idx, cb, Q, nprobe=12, k=25)
+    for q in range(Q.shape[0]):
+        lut = np.stack([cdist(Q[q:q + 1, m * ds:(m + 1) * ds].astype(np.float64), cb[m].astype(np.float64),
+                              "sqeuclidean")[0] for m in range(M)])
+        adc = lut[np.arange(M)[None, :], codes].sum(axis=1)
+        order = np.lexsort((np.arange(X.shape[0]), adc))[:25]
+        assert np.array_equal(ids[q], order)
+        np.testing.assert_allclose(dist[q], adc[order], rtol=1e-12)
+
+
+def test_ivf_probe_order_and_padding():
+    X, cb, codes, idx = _small_index()
+    Q = datagen.queries(10, X.shape[1], 20, "int255", 18)
+    ids, dist, probes = orc.ivf_search(idx, cb, Q, nprobe=3, k=X.shape[0])
+    dc = cdist(Q.astype(np.float64), idx["coarse"].astype(np.float64), "sqeuclidean")
+    for q in range(10):
+        want = np.lexsort((np.arange(dc.shape[1]), dc[q]))[:3]
+        assert np.array_equal(probes[q], want)
+        n_cand = sum(idx["offsets"][l + 1] - idx["offsets"][l] for l in want)
+        assert np.all(ids[q, n_cand:] == -1) and np.all(np.isinf(dist[q, n_cand:]))
+        assert np.all(ids[q, :n_cand] >= 0)
+
+
+def test_exact_knn_matches_cdist():
+    X = datagen.mixture(800, 8, 5, "int255", 19)
+    Q = datagen.queries(20, 8, 5, "int255", 19)
+    ids, dist = orc.exact_knn(X, Q, 10)
+    full = cdist(Q.astype(np.float64), X.astype(np.float64), "sqeuclidean")
+    for q in range(20):
+        order = np.lexsort((np.arange(800), full[q]))[:10]
+        assert np.array_equal(ids[q], order)
+
+
+# -- chunked divide and conquer (Sec. 3) ------------------------------------------------
+
+def test_chunked_single_chunk_reduces_to_plain_fit():
+    X = datagen.mixture(3000, 8, 10, "cont", 20)
+    gC, codes, r, local = orc.pq_fit_chunked(X, [0, 3000], 2, 16, 6, 5)
+    # the pooled dataset is the chunk's own codewords; the global fit on it reproduces them
+    for m in range(2):
+        assert {tuple(v) for v in gC[m]} == {tuple(v) for v in local[0, m]}
+    codes_local = orc.pq_encode(X, local[0])
+    np.testing.assert_allclose(r, orc.pq_rmse(X, codes_local, local[0]), rtol=1e-12)
+
+
+def test_chunked_rmse_close_to_single_fit():
+    """Sec. 3: the global model fitted on pooled chunk codewords reconstructs about as well as one fit."""
+    X = datagen.mixture(12000, 8, 24, "cont", 21)
+    off = [0, 2500, 5200, 9000, 12000]
+    _, _, r_chunk, _ = orc.pq_fit_chunked(X, off, 2, 16, 10, 6)
+    cb, _ = orc.pq_fit(X, 2, 16, 10, 6)
+    r_single = orc.pq_rmse(X, orc.pq_encode(X, cb), cb)
+    assert abs(r_chunk - r_single) / r_single < 0.1
+
+
+# -- soft-assignment refinement ------------------------------------------------------------
+
+def test_softpq_gradients_match_finite_differences():
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(7, 6))
+    cb = rng.normal(size=(2, 5, 3))
+    tau = 0.7
+    dC, dX = orc.softpq_backward(X, cb, tau)
+    h = 1e-6
+    for arr, grad in ((cb, dC), (X, dX)):
+        num = np.zeros_like(arr)
+        it = np.nditer(arr, flags=["multi_index"])
+        for _ in it:
+            i = it.multi_index
+            old = arr[i]
+            arr[i] = old + h
+            lp = orc.softpq_forward(X, cb, tau)
+            arr[i] = old - h
+            lm = orc.softpq_forward(X, cb, tau)
+            arr[i] = old
+            num[i] = (lp - lm) / (2 * h)
+        np.testing.assert_allclose(grad, num, rtol=1e-6, atol=1e-9)
+
+
+def test_softpq_limits():
+    rng = np.random.default_rng(5)
+    X = rng.normal(size=(50, 4))
+    cb = rng.normal(size=(2, 6, 2))
+    # tau -> 0: hard assignment, loss = SSE / N
+    X32 = X.astype(np.float32)
+    cb32 = cb.astype(np.float32)
+    _, mind, gap = orc.assign(X32, cb32)
+    tau0 = gap.min() / 200.0  # second-best weight below exp(-200)
+    hard = orc.softpq_forward(X32.astype(np.float64), cb32.astype(np.float64), tau0)
+    np.testing.assert_allclose(hard, mind.sum() / 50, rtol=1e-9)
+    # tau -> inf: uniform weights, xhat = mean codeword
+    big = orc.softpq_forward(X, cb, 1e12)
+    mean_cw = np.concatenate([cb[m].mean(axis=0) for m in range(2)])
+    np.testing.assert_allclose(big, ((X - mean_cw) ** 2).sum() / 50, rtol=1e-9)
