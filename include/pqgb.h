@@ -1,0 +1,183 @@
+/*
+ * pqgb.h -- C ABI of libpqgb.so: product quantization (PQ) fit / encode /
+ * decode-RMSE and an inverted-file index with asymmetric-distance (IVF-ADC)
+ * k-nearest-neighbour search, on one sm_103a GPU.
+ *
+ * The operations follow the paper's statement of the method:
+ *   - PQ fit (Sec. 2.1): the D dimensions are split into M contiguous
+ *     subspaces of Ds = D/M dimensions; each subspace is clustered by k-means
+ *     into Ks centroids, the codebooks.
+ *   - PQ encode (Sec. 2.1): every row's sub-vector in subspace m is replaced
+ *     by the index of its nearest centroid; a row becomes M codes.
+ *   - Decode and RMSE (Sec. 2.1, Sec. 3): the reconstruction is the
+ *     concatenation of the selected centroids; accuracy is the root mean
+ *     squared reconstruction error.
+ *   - Inverted index and query (Sec. 2.2, Sec. 3.1): ids are stored per
+ *     list over the codes; a query returns its k nearest neighbours, scored
+ *     with the PQ distance table.
+ *   - Chunked divide and conquer (Sec. 3): per-chunk fits, codewords pooled
+ *     into a centroid dataset, a global refit, then a global encode + RMSE.
+ *
+ * Conventions shared by every call:
+ *   - Layouts are row-major and little-endian.  X is N x D float32; codebooks
+ *     are M x Ks x Ds float32 (subspace-major); codes are N x M uint8.
+ *   - Pointers are DEVICE pointers owned by the caller unless stated
+ *     otherwise.  The library never frees caller memory.  Scratch space is
+ *     taken with stream-ordered cudaMallocAsync on the caller's stream and
+ *     returned before the call's work completes.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued asynchronously; calls return after enqueue
+ *     unless documented to synchronize.
+ *   - Return value: PQ_OK or a negative status.  Argument errors are found
+ *     before anything is enqueued.  Asynchronous device failures (including
+ *     a device-side bounded wait that ran out, PQ_ETIMEOUT) are recorded and
+ *     returned by pq_sync_status() or by the next synchronizing call.
+ *     pq_last_error() gives a message for the last failure on this thread.
+ *   - Distances are squared Euclidean.  Argmin ties go to the lowest index;
+ *     query results are ordered by (distance, id).
+ *   - Codes are exact: every nearest-centroid decision is either proven by an
+ *     FP32 (or BF16) error bound or re-decided in FP64 by direct differences.
+ */
+#ifndef PQGB_H
+#define PQGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    PQ_OK = 0,
+    PQ_EINVAL = -1,   /* bad argument (shape, null pointer, alignment)      */
+    PQ_ENOMEM = -2,   /* device scratch or host allocation failed           */
+    PQ_ECUDA = -3,    /* a CUDA runtime call failed                         */
+    PQ_ETIMEOUT = -4, /* a device-side bounded wait ran out                 */
+    PQ_ENOTSUP = -5   /* valid but unsupported shape/precision combination  */
+};
+
+/* Arithmetic of the distance contraction used to find nearest centroids. */
+enum {
+    PQ_PREC_FP32 = 0, /* FP32 FFMA on CUDA cores                               */
+    PQ_PREC_BF16 = 1  /* BF16 tcgen05 tensor-core GEMM, FP32 accumulation,
+                         exact FP32 re-rank of the candidates                  */
+};
+
+#define PQ_STATS_MAX_ITERS 64
+
+/* Diagnostics of one pq_fit / pq_encode call (host struct, optional). */
+typedef struct pq_stats {
+    int32_t iters;            /* Lloyd iterations run                          */
+    int32_t reserved;
+    int64_t fp64_rechecks;    /* (row, subspace) decisions re-taken in FP64     */
+    int64_t empty_clusters;   /* codewords left without members, all iterations */
+    int64_t kernel_launches;  /* kernels this call launched                     */
+    double sse[PQ_STATS_MAX_ITERS]; /* total squared error of each iteration's
+                                       assignment (before its update)           */
+} pq_stats;
+
+/*
+ * pq_fit -- PQ codebooks by per-subspace k-means (Sec. 2.1).
+ *   X               [N][D] float32, 16-byte aligned, N >= Ks.
+ *   D, M            D % M == 0, Ds = D/M <= 32.
+ *   Ks              1 <= Ks <= 256.
+ *   iters           Lloyd iterations, 0 <= iters <= PQ_STATS_MAX_ITERS.
+ *   seed            k-means++ seed (SplitMix64 streams; when N > 100*Ks the
+ *                   seeding runs on a with-replacement subsample of 100*Ks rows).
+ *   prec            PQ_PREC_FP32 or PQ_PREC_BF16.
+ *   init_codebooks  [M][Ks][Ds] or NULL (NULL = k-means++ seeding).
+ *   codebooks       [M][Ks][Ds] output (may alias init_codebooks).
+ *   stats           host pq_stats or NULL; non-NULL makes the call synchronize.
+ * Each iteration assigns every (row, subspace) to its nearest codeword, then
+ * replaces every codeword by the mean of its members (FP32 compensated sums,
+ * FP64 final reduction); a codeword without members keeps its value.
+ */
+int pq_fit(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, int32_t iters, uint64_t seed,
+           int32_t prec, const float *init_codebooks, float *codebooks, pq_stats *stats, void *stream);
+
+/*
+ * pq_init_kmeanspp -- only the k-means++ seeding step of pq_fit.
+ *   Same arguments as pq_fit; writes codebooks [M][Ks][Ds].
+ */
+int pq_init_kmeanspp(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, uint64_t seed, float *codebooks,
+                     void *stream);
+
+/*
+ * pq_encode -- PQ codes (Sec. 2.1).
+ *   codes   [N][M] uint8 output.
+ *   sse     NULL, or a device double that receives the total squared
+ *           reconstruction error sum_{n,d} (x - xhat)^2 (overwritten).
+ *   stats   host pq_stats or NULL (non-NULL synchronizes).
+ */
+int pq_encode(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, const float *codebooks, int32_t prec,
+              uint8_t *codes, double *sse, pq_stats *stats, void *stream);
+
+/*
+ * pq_decode_rmse -- reconstruction and its RMSE (Sec. 2.1, Sec. 3).
+ *   codes [N][M] uint8, codebooks [M][Ks][Ds].
+ *   X     [N][D] or NULL; if non-NULL, *rmse (host) receives
+ *         sqrt(sum (x - xhat)^2 / (N*D)) and the call synchronizes.
+ *   Xhat  [N][D] output or NULL.
+ * At least one of X (with rmse) and Xhat must be given.
+ */
+int pq_decode_rmse(const uint8_t *codes, const float *codebooks, const float *X, int64_t N, int32_t D, int32_t M,
+                   int32_t Ks, float *Xhat, double *rmse, void *stream);
+
+/* Opaque inverted-file index, allocated by ivf_build and owned by the library until ivf_free. */
+typedef struct ivf_index ivf_index;
+
+/*
+ * ivf_build -- inverted lists over PQ codes (Sec. 2.2, Sec. 3.1).
+ *   X      [N][D] float32 rows; codes [N][M] their PQ codes.
+ *   nlist  coarse lists, 1 <= nlist <= N; the coarse quantizer is k-means on
+ *          the raw rows (k-means++ seeding from `seed`, `iters` Lloyd steps).
+ *   out    receives the new index (device-resident lists: ids ascending
+ *          within a list).  The call synchronizes once to size the lists.
+ */
+int ivf_build(const float *X, const uint8_t *codes, int64_t N, int32_t D, int32_t M, int32_t nlist, int32_t iters,
+              uint64_t seed, int32_t prec, ivf_index **out, void *stream);
+
+/*
+ * ivf_search -- k nearest neighbours by ADC over the probed lists (Sec. 2.2).
+ *   codebooks [M][Ks][Ds] (the codebooks the stored codes were made with).
+ *   Q         [nq][D] float32 queries.
+ *   nprobe    1 <= nprobe <= nlist lists probed (nearest coarse centroids).
+ *   k         1 <= k <= 1024 results per query.
+ *   ids       [nq][k] int64 output, dists [nq][k] float32 output, ordered by
+ *             (ADC distance, id); missing results are id -1, distance +inf.
+ */
+int ivf_search(const ivf_index *index, const float *codebooks, int32_t Ks, const float *Q, int64_t nq,
+               int32_t nprobe, int32_t k, int64_t *ids, float *dists, void *stream);
+
+/* Index accessors: copies of the device-resident parts (device destinations). */
+int ivf_get_info(const ivf_index *index, int64_t *N, int32_t *D, int32_t *M, int32_t *nlist);
+int ivf_copy_coarse(const ivf_index *index, float *coarse /* [nlist][D] */, void *stream);
+int ivf_copy_lists(const ivf_index *index, int64_t *offsets /* [nlist+1] */, int64_t *ids /* [N] */,
+                   uint8_t *list_codes /* [N][M] */, void *stream);
+void ivf_free(ivf_index *index);
+
+/* Synchronize `stream` and return (and clear) any recorded device failure. */
+int pq_sync_status(void *stream);
+/* Message of the last failure on the calling thread ("" if none). */
+const char *pq_last_error(void);
+/* Kernels launched by this library since load (a monotone counter). */
+int64_t pq_launch_count(void);
+
+/*
+ * Per-kernel timing for measurement (no counterpart in the paper).
+ * pq_profile_enable(1) clears old records and starts recording a CUDA event
+ * pair around every kernel launch on the launch's own stream; (0) stops.
+ * pq_profile_collect synchronizes the device and returns, for kernel `name`,
+ * the number of recorded launches and their summed device time in ms.
+ * pq_profile_names writes the comma-separated recorded names into buf
+ * (PQ_EINVAL if it does not fit).
+ */
+int pq_profile_enable(int on);
+int pq_profile_collect(const char *name, int64_t *count, double *total_ms);
+int pq_profile_names(char *buf, int len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PQGB_H */

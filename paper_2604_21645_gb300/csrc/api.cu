@@ -1,0 +1,558 @@
+// api.cu -- the extern "C" entry points of libpqgb.so (declared in pqgb.h):
+// argument validation, stream-ordered scratch, and the order of kernels that
+// makes up PQ fit / encode / decode-RMSE (Sec. 2.1, Sec. 3) and the inverted
+// index build / query (Sec. 2.2, Sec. 3.1).
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace pqgb {
+
+static std::atomic<int64_t> g_launches{0};
+static thread_local char g_msg[512] = "";
+static std::mutex g_err_mu;
+static int *g_err_word[64] = {};
+
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int fail(int status, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+    return status;
+}
+
+int cuda_check(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation) return fail(PQ_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(PQ_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int *device_error_word(int device)
+{
+    if (device < 0 || device >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    if (!g_err_word[device]) {
+        int *p = nullptr;
+        if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+        if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return nullptr;
+        g_err_word[device] = p;
+    }
+    return g_err_word[device];
+}
+
+struct ProfRec {
+    const char *name;
+    cudaEvent_t a, b;
+};
+static std::mutex g_prof_mu;
+static std::atomic<bool> g_prof_on{false};
+static std::vector<ProfRec> g_prof;
+static std::vector<cudaEvent_t> g_ev_pool;
+
+static cudaEvent_t take_event()
+{
+    if (!g_ev_pool.empty()) {
+        cudaEvent_t e = g_ev_pool.back();
+        g_ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+ProfScope::ProfScope(const char *name, cudaStream_t st) : s(st)
+{
+    if (!g_prof_on.load(std::memory_order_relaxed)) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfRec r{name, take_event(), take_event()};
+    if (!r.a || !r.b) return;
+    cudaEventRecord(r.a, s);
+    idx = (int)g_prof.size();
+    g_prof.push_back(r);
+}
+
+ProfScope::~ProfScope()
+{
+    if (idx < 0) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEventRecord(g_prof[idx].b, s);
+}
+
+void *Scratch::raw(size_t bytes, bool zero)
+{
+    if (status) return nullptr;
+    void *p = nullptr;
+    const size_t b = (bytes + 255) & ~size_t(255);
+    cudaError_t e = cudaMallocAsync(&p, b ? b : 256, s);
+    if (e != cudaSuccess) { status = cuda_check(e, "cudaMallocAsync"); return nullptr; }
+    ptrs.push_back(p);
+    if (zero) {
+        e = cudaMemsetAsync(p, 0, b ? b : 256, s);
+        if (e != cudaSuccess) { status = cuda_check(e, "cudaMemsetAsync"); return nullptr; }
+    }
+    return p;
+}
+
+Scratch::~Scratch()
+{
+    for (void *p : ptrs) cudaFreeAsync(p, s);
+}
+
+}  // namespace pqgb
+
+using namespace pqgb;
+
+struct ivf_index {
+    int device = 0;
+    int64_t N = 0;
+    int D = 0, M = 0, nlist = 0;
+    float *coarse = nullptr;       // [nlist][D]
+    float *half_norm = nullptr;    // [nlist]
+    float *maxes = nullptr;        // [2]
+    int64_t *offsets = nullptr;    // [nlist+1]
+    int64_t *ids = nullptr;        // [N]
+    uint8_t *codes = nullptr;      // [N][M]
+};
+
+namespace {
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+int check_pq_shape(int64_t N, int D, int M, int Ks, bool need_ks_le_n)
+{
+    if (N < 0) return fail(PQ_EINVAL, "N=%lld must be >= 0", (long long)N);
+    if (D <= 0 || M <= 0 || D % M != 0) return fail(PQ_EINVAL, "D=%d must be a positive multiple of M=%d", D, M);
+    if (Ks < 1 || Ks > 256) return fail(PQ_EINVAL, "Ks=%d must be in [1, 256]", Ks);
+    if (need_ks_le_n && N < Ks) return fail(PQ_EINVAL, "N=%lld must be >= Ks=%d", (long long)N, Ks);
+    const int ds = D / M;
+    if (ds > 32) return fail(PQ_EINVAL, "subspace width D/M=%d must be <= 32", ds);
+    return PQ_OK;
+}
+
+int check_prec(int prec)
+{
+    if (prec != PQ_PREC_FP32 && prec != PQ_PREC_BF16) return fail(PQ_EINVAL, "prec=%d unknown", prec);
+    return PQ_OK;
+}
+
+int run_pass(PqPass &p, int prec, cudaStream_t s)
+{
+    if (prec == PQ_PREC_BF16) {
+        if (!tc_pass_supported(p.D, p.M, p.Ks))
+            return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and Ks == 256");
+        return launch_pq_pass_tc(p, s);
+    }
+    return launch_pq_pass_f32(p, s);
+}
+
+int status_from_device(int *err_word, cudaStream_t s, int *host_err)
+{
+    PQ_TRY_CUDA(cudaMemcpyAsync(host_err, err_word, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PQ_TRY_CUDA(cudaStreamSynchronize(s));
+    return PQ_OK;
+}
+
+// Seeding rows: all rows, or 100*Ks drawn with replacement (gathered).
+int seed_codebooks(const float *X, int64_t N, int D, int M, int Ks, uint64_t seed, float *C, Scratch &ws, int *err,
+                   cudaStream_t s)
+{
+    const int64_t cap = 100LL * Ks;
+    const float *P = X;
+    int64_t n = N;
+    if (N > cap) {
+        float *G = ws.get<float>((size_t)cap * D);
+        if (ws.status) return ws.status;
+        PQ_TRY(launch_gather_subsample(X, N, D, cap, seed, G, s));
+        P = G;
+        n = cap;
+    }
+    return launch_kmeanspp(P, D, n, D / M, M, Ks, seed, C, ws, err, s);
+}
+
+// Lloyd iterations over PQ codebooks C (in place).
+int lloyd(const float *X, int64_t N, int D, int M, int Ks, int iters, int prec, float *C, double *sse_dev,
+          unsigned long long *counters /* [2]: rechecks, empties */, Scratch &ws, cudaStream_t s)
+{
+    PqPass p;
+    p.X = X;
+    p.N = N;
+    p.D = D;
+    p.M = M;
+    p.Ks = Ks;
+    p.ds = D / M;
+    p.C = C;
+    p.gx = pq_pass_blocks_per_subspace(p);
+    p.part = ws.get<double>((size_t)p.gx * M * Ks * p.ds);
+    p.part_cnt = ws.get<int>((size_t)p.gx * M * Ks);
+    if (ws.status) return ws.status;
+    p.rechecks = counters;
+    for (int t = 0; t < iters; ++t) {
+        p.sse = sse_dev ? sse_dev + t : nullptr;
+        PQ_TRY(run_pass(p, prec, s));
+        PQ_TRY(launch_pq_finalize(p.part, p.part_cnt, p.gx, M, Ks, p.ds, C, counters + 1, s));
+    }
+    return PQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pq_init_kmeanspp(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, uint64_t seed, float *codebooks,
+                     void *stream)
+{
+    g_msg[0] = 0;
+    PQ_TRY(check_pq_shape(N, D, M, Ks, true));
+    if (!X || !codebooks) return fail(PQ_EINVAL, "null pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    PQ_TRY_CUDA(cudaGetDevice(&dev));
+    int *err = device_error_word(dev);
+    if (!err) return fail(PQ_ENOMEM, "device error word");
+    Scratch ws(s);
+    PQ_TRY(seed_codebooks(X, N, D, M, Ks, seed, codebooks, ws, err, s));
+    return ws.status;
+}
+
+int pq_fit(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, int32_t iters, uint64_t seed, int32_t prec,
+           const float *init_codebooks, float *codebooks, pq_stats *stats, void *stream)
+{
+    g_msg[0] = 0;
+    PQ_TRY(check_pq_shape(N, D, M, Ks, true));
+    PQ_TRY(check_prec(prec));
+    if (!X || !codebooks) return fail(PQ_EINVAL, "null pointer");
+    if (!aligned16(X)) return fail(PQ_EINVAL, "X must be 16-byte aligned");
+    if (iters < 0 || iters > PQ_STATS_MAX_ITERS) return fail(PQ_EINVAL, "iters=%d must be in [0, %d]", iters,
+                                                             PQ_STATS_MAX_ITERS);
+    if (prec == PQ_PREC_BF16 && !tc_pass_supported(D, M, Ks))
+        return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and Ks == 256");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t l0 = g_launches.load();
+    int dev = 0;
+    PQ_TRY_CUDA(cudaGetDevice(&dev));
+    int *err = device_error_word(dev);
+    if (!err) return fail(PQ_ENOMEM, "device error word");
+    Scratch ws(s);
+    const size_t cb_bytes = (size_t)M * Ks * (D / M) * sizeof(float);
+    if (init_codebooks) {
+        if (init_codebooks != codebooks)
+            PQ_TRY_CUDA(cudaMemcpyAsync(codebooks, init_codebooks, cb_bytes, cudaMemcpyDeviceToDevice, s));
+    } else {
+        PQ_TRY(seed_codebooks(X, N, D, M, Ks, seed, codebooks, ws, err, s));
+    }
+    double *sse = stats ? ws.get<double>(PQ_STATS_MAX_ITERS, true) : nullptr;
+    unsigned long long *counters = ws.get<unsigned long long>(2, true);
+    if (ws.status) return ws.status;
+    PQ_TRY(lloyd(X, N, D, M, Ks, iters, prec, codebooks, sse, counters, ws, s));
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        unsigned long long hc[2];
+        PQ_TRY_CUDA(cudaMemcpyAsync(stats->sse, sse, sizeof(double) * iters, cudaMemcpyDeviceToHost, s));
+        PQ_TRY_CUDA(cudaMemcpyAsync(hc, counters, sizeof(hc), cudaMemcpyDeviceToHost, s));
+        int herr = 0;
+        PQ_TRY(status_from_device(err, s, &herr));
+        stats->iters = iters;
+        stats->fp64_rechecks = (int64_t)hc[0];
+        stats->empty_clusters = (int64_t)hc[1];
+        stats->kernel_launches = g_launches.load() - l0;
+        if (herr) {
+            cudaMemsetAsync(err, 0, sizeof(int), s);
+            return fail(herr, "device-side failure %d during pq_fit", herr);
+        }
+    }
+    return ws.status;
+}
+
+int pq_encode(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, const float *codebooks, int32_t prec,
+              uint8_t *codes, double *sse, pq_stats *stats, void *stream)
+{
+    g_msg[0] = 0;
+    PQ_TRY(check_pq_shape(N, D, M, Ks, false));
+    PQ_TRY(check_prec(prec));
+    if (!X || !codebooks || !codes) return fail(PQ_EINVAL, "null pointer");
+    if (!aligned16(X)) return fail(PQ_EINVAL, "X must be 16-byte aligned");
+    if (prec == PQ_PREC_BF16 && !tc_pass_supported(D, M, Ks))
+        return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and Ks == 256");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t l0 = g_launches.load();
+    if (sse) PQ_TRY_CUDA(cudaMemsetAsync(sse, 0, sizeof(double), s));
+    if (N == 0) return PQ_OK;
+    Scratch ws(s);
+    unsigned long long *counters = stats ? ws.get<unsigned long long>(1, true) : nullptr;
+    if (ws.status) return ws.status;
+    PqPass p;
+    p.X = X;
+    p.N = N;
+    p.D = D;
+    p.M = M;
+    p.Ks = Ks;
+    p.ds = D / M;
+    p.C = codebooks;
+    p.codes = codes;
+    p.sse = sse;
+    p.rechecks = counters;
+    PQ_TRY(run_pass(p, prec, s));
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        unsigned long long hc = 0;
+        PQ_TRY_CUDA(cudaMemcpyAsync(&hc, counters, sizeof(hc), cudaMemcpyDeviceToHost, s));
+        PQ_TRY_CUDA(cudaStreamSynchronize(s));
+        stats->fp64_rechecks = (int64_t)hc;
+        stats->kernel_launches = g_launches.load() - l0;
+    }
+    return ws.status;
+}
+
+int pq_decode_rmse(const uint8_t *codes, const float *codebooks, const float *X, int64_t N, int32_t D, int32_t M,
+                   int32_t Ks, float *Xhat, double *rmse, void *stream)
+{
+    g_msg[0] = 0;
+    PQ_TRY(check_pq_shape(N, D, M, Ks, false));
+    if (!codes || !codebooks) return fail(PQ_EINVAL, "null pointer");
+    if (!Xhat && !(X && rmse)) return fail(PQ_EINVAL, "nothing to compute: give Xhat and/or X with rmse");
+    if (X && !rmse) return fail(PQ_EINVAL, "X given without rmse");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Scratch ws(s);
+    double *sse = X ? ws.get<double>(1, true) : nullptr;
+    if (ws.status) return ws.status;
+    if (N > 0) PQ_TRY(launch_decode_rmse(codes, codebooks, X, N, D, M, Ks, Xhat, sse, s));
+    if (X) {
+        double h = 0.0;
+        PQ_TRY_CUDA(cudaMemcpyAsync(&h, sse, sizeof(double), cudaMemcpyDeviceToHost, s));
+        PQ_TRY_CUDA(cudaStreamSynchronize(s));
+        *rmse = N > 0 ? sqrt(h / ((double)N * (double)D)) : 0.0;
+    }
+    return ws.status;
+}
+
+int ivf_build(const float *X, const uint8_t *codes, int64_t N, int32_t D, int32_t M, int32_t nlist, int32_t iters,
+              uint64_t seed, int32_t prec, ivf_index **out, void *stream)
+{
+    g_msg[0] = 0;
+    if (!out) return fail(PQ_EINVAL, "null output handle");
+    *out = nullptr;
+    if (!X || !codes) return fail(PQ_EINVAL, "null pointer");
+    if (N < 1 || N >= (1LL << 31)) return fail(PQ_EINVAL, "N=%lld must be in [1, 2^31)", (long long)N);
+    if (D <= 0 || M <= 0 || D % M != 0) return fail(PQ_EINVAL, "D=%d must be a positive multiple of M=%d", D, M);
+    if (nlist < 1 || nlist > N) return fail(PQ_EINVAL, "nlist=%d must be in [1, N]", nlist);
+    if (nlist > 16384) return fail(PQ_ENOTSUP, "nlist=%d exceeds 16384", nlist);
+    if (D > 256) return fail(PQ_ENOTSUP, "ivf_build supports D <= 256");
+    if (iters < 0) return fail(PQ_EINVAL, "iters=%d must be >= 0", iters);
+    PQ_TRY(check_prec(prec));
+    if (!aligned16(X)) return fail(PQ_EINVAL, "X must be 16-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    PQ_TRY_CUDA(cudaGetDevice(&dev));
+    int *err = device_error_word(dev);
+    if (!err) return fail(PQ_ENOMEM, "device error word");
+
+    ivf_index *idx = new ivf_index();
+    idx->device = dev;
+    idx->N = N;
+    idx->D = D;
+    idx->M = M;
+    idx->nlist = nlist;
+    auto cleanup = [&](int st) {
+        ivf_free(idx);
+        return st;
+    };
+    if (cudaMalloc(&idx->coarse, (size_t)nlist * D * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&idx->half_norm, (size_t)nlist * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&idx->maxes, 2 * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&idx->offsets, (size_t)(nlist + 1) * sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc(&idx->ids, (size_t)N * sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc(&idx->codes, (size_t)N * M) != cudaSuccess)
+        return cleanup(fail(PQ_ENOMEM, "index allocation"));
+    int st = PQ_OK;
+    {
+        Scratch ws(s);
+        int32_t *lst = ws.get<int32_t>((size_t)N);
+        if (ws.status) return cleanup(ws.status);
+        CoarseBound b{idx->half_norm, idx->maxes};
+        st = seed_codebooks(X, N, D, 1, nlist, seed, idx->coarse, ws, err, s);
+        for (int t = 0; st == PQ_OK && t < iters; ++t) {
+            st = launch_coarse_norms(idx->coarse, nlist, D, b, s);
+            if (!st) st = coarse_assign(X, N, D, idx->coarse, nlist, b, lst, ws, nullptr, s);
+            if (!st) st = bucket_rows(lst, N, nlist, nullptr, M, idx->offsets, idx->ids, nullptr, ws, s);
+            if (!st) st = launch_list_mean(X, D, idx->offsets, idx->ids, nlist, idx->coarse, s);
+        }
+        if (!st) st = launch_coarse_norms(idx->coarse, nlist, D, b, s);
+        if (!st) st = coarse_assign(X, N, D, idx->coarse, nlist, b, lst, ws, nullptr, s);
+        if (!st) st = bucket_rows(lst, N, nlist, codes, M, idx->offsets, idx->ids, idx->codes, ws, s);
+        if (!st) st = ws.status;
+    }
+    if (st) return cleanup(st);
+    int herr = 0;
+    st = status_from_device(err, s, &herr);
+    if (st) return cleanup(st);
+    if (herr) {
+        cudaMemsetAsync(err, 0, sizeof(int), s);
+        return cleanup(fail(herr, "device-side failure %d during ivf_build", herr));
+    }
+    *out = idx;
+    return PQ_OK;
+}
+
+int ivf_search(const ivf_index *index, const float *codebooks, int32_t Ks, const float *Q, int64_t nq,
+               int32_t nprobe, int32_t k, int64_t *ids, float *dists, void *stream)
+{
+    g_msg[0] = 0;
+    if (!index || !codebooks || !Q || !ids || !dists) return fail(PQ_EINVAL, "null pointer");
+    if (Ks < 1 || Ks > 256) return fail(PQ_EINVAL, "Ks=%d must be in [1, 256]", Ks);
+    if (nq < 0) return fail(PQ_EINVAL, "nq must be >= 0");
+    if (nprobe < 1 || nprobe > index->nlist)
+        return fail(PQ_EINVAL, "nprobe=%d must be in [1, nlist=%d]", nprobe, index->nlist);
+    if (k < 1 || k > 1024) return fail(PQ_EINVAL, "k=%d must be in [1, 1024]", k);
+    if (nq == 0) return PQ_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Scratch ws(s);
+    CoarseBound b{index->half_norm, index->maxes};
+    SearchArgs a;
+    a.Q = Q;
+    a.nq = nq;
+    a.D = index->D;
+    a.M = index->M;
+    a.Ks = Ks;
+    a.nlist = index->nlist;
+    a.nprobe = nprobe;
+    a.k = k;
+    a.coarse = index->coarse;
+    a.cb = &b;
+    a.offsets = index->offsets;
+    a.ids = index->ids;
+    a.list_codes = index->codes;
+    a.codebooks = codebooks;
+    a.out_ids = ids;
+    a.out_d = dists;
+    PQ_TRY(run_search(a, ws, s));
+    return ws.status;
+}
+
+int ivf_get_info(const ivf_index *index, int64_t *N, int32_t *D, int32_t *M, int32_t *nlist)
+{
+    if (!index) return fail(PQ_EINVAL, "null index");
+    if (N) *N = index->N;
+    if (D) *D = index->D;
+    if (M) *M = index->M;
+    if (nlist) *nlist = index->nlist;
+    return PQ_OK;
+}
+
+int ivf_copy_coarse(const ivf_index *index, float *coarse, void *stream)
+{
+    if (!index || !coarse) return fail(PQ_EINVAL, "null pointer");
+    PQ_TRY_CUDA(cudaMemcpyAsync(coarse, index->coarse, (size_t)index->nlist * index->D * sizeof(float),
+                                cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
+    return PQ_OK;
+}
+
+int ivf_copy_lists(const ivf_index *index, int64_t *offsets, int64_t *ids, uint8_t *list_codes, void *stream)
+{
+    if (!index) return fail(PQ_EINVAL, "null index");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (offsets)
+        PQ_TRY_CUDA(cudaMemcpyAsync(offsets, index->offsets, (size_t)(index->nlist + 1) * sizeof(int64_t),
+                                    cudaMemcpyDeviceToDevice, s));
+    if (ids)
+        PQ_TRY_CUDA(cudaMemcpyAsync(ids, index->ids, (size_t)index->N * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    if (list_codes)
+        PQ_TRY_CUDA(cudaMemcpyAsync(list_codes, index->codes, (size_t)index->N * index->M, cudaMemcpyDeviceToDevice,
+                                    s));
+    return PQ_OK;
+}
+
+void ivf_free(ivf_index *index)
+{
+    if (!index) return;
+    cudaFree(index->coarse);
+    cudaFree(index->half_norm);
+    cudaFree(index->maxes);
+    cudaFree(index->offsets);
+    cudaFree(index->ids);
+    cudaFree(index->codes);
+    delete index;
+}
+
+int pq_sync_status(void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_check(e, "cudaStreamSynchronize");
+    int dev = 0;
+    PQ_TRY_CUDA(cudaGetDevice(&dev));
+    int *err = device_error_word(dev);
+    if (!err) return PQ_OK;
+    int h = 0;
+    PQ_TRY_CUDA(cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        cudaMemset(err, 0, sizeof(int));
+        return fail(h, "device-side failure %d", h);
+    }
+    return PQ_OK;
+}
+
+const char *pq_last_error(void) { return g_msg; }
+
+int64_t pq_launch_count(void) { return g_launches.load(); }
+
+int pq_profile_enable(int on)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &r : g_prof) {
+        g_ev_pool.push_back(r.a);
+        g_ev_pool.push_back(r.b);
+    }
+    g_prof.clear();
+    g_prof_on.store(on != 0);
+    return PQ_OK;
+}
+
+int pq_profile_collect(const char *name, int64_t *count, double *total_ms)
+{
+    if (!name || !count || !total_ms) return fail(PQ_EINVAL, "null pointer");
+    PQ_TRY_CUDA(cudaDeviceSynchronize());
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    int64_t c = 0;
+    double t = 0.0;
+    for (auto &r : g_prof) {
+        if (strcmp(r.name, name) != 0) continue;
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) continue;
+        ++c;
+        t += ms;
+    }
+    *count = c;
+    *total_ms = t;
+    return PQ_OK;
+}
+
+int pq_profile_names(char *buf, int len)
+{
+    if (!buf || len <= 0) return fail(PQ_EINVAL, "null buffer");
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    std::string out;
+    std::vector<std::string> seen;
+    for (auto &r : g_prof) {
+        bool dup = false;
+        for (auto &n : seen) dup = dup || n == r.name;
+        if (dup) continue;
+        seen.emplace_back(r.name);
+        if (!out.empty()) out += ",";
+        out += r.name;
+    }
+    snprintf(buf, (size_t)len, "%s", out.c_str());
+    return (int)out.size() < len ? PQ_OK : PQ_EINVAL;
+}
+
+}  // extern "C"

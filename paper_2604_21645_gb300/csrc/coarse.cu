@@ -1,0 +1,421 @@
+// coarse.cu -- coarse quantizer of the inverted index (Sec. 2.2; Rii is an
+// IVFPQ-style index, Sec. 3.1): k-means on the raw D-dimensional rows,
+// nearest-list assignment, and list-contiguous (CSR) bucketing of row ids and
+// PQ codes.
+//
+// Assignment uses the same certified-argmin rule as the PQ pass: FP32 scores
+// s_l = ||c_l||^2/2 - x.c_l from a tiled FFMA kernel, the two best kept per
+// row; a row whose top-two gap does not clear the FP32 error bound is queued
+// and re-decided by a warp in FP64 (direct differences over the candidates
+// within the bound), so the list of every row is exact.
+//
+// The centroid update sums each list's rows in FP64 in ascending row order,
+// one thread per dimension, which is exactly the reference computation.
+#include <algorithm>
+#include <cfloat>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace pqgb {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 32;
+constexpr int kTileRows = 2048;  // rows per bucketing tile
+
+__global__ void coarse_norms_kernel(const float *C, int nlist, int D, float *half_norm, float *maxes)
+{
+    float lmax = 0.0f;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nlist; l += gridDim.x * blockDim.x) {
+        float n = 0.0f;
+        for (int j = 0; j < D; ++j) n = fmaf(C[(size_t)l * D + j], C[(size_t)l * D + j], n);
+        half_norm[l] = 0.5f * n;
+        lmax = fmaxf(lmax, 0.5f * n);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned *>(maxes), __float_as_uint(lmax));
+}
+
+__global__ void coarse_bound_finish(float *maxes, int D)
+{
+    const float nmax = maxes[0] * (1.0f + 4.0f * gamma_f32(D + 1));
+    maxes[0] = nmax;
+    maxes[1] = sqrtf(2.0f * nmax) * (1.0f + 1e-6f);
+}
+
+__device__ __forceinline__ float score_delta(float xn, float nmax, float cmax, int D)
+{
+    const float t = xn + cmax;
+    return 2.2f * gamma_f32(D + 1) * (nmax + xn * cmax) + 1e-13f * t * t;
+}
+
+__device__ __forceinline__ void top2_merge(float &m1, int &i1, float &m2, float o1, int oi, float o2)
+{
+    const bool take = (o1 < m1) || (o1 == m1 && oi < i1);
+    const float rest = take ? fminf(m1, o2) : fminf(m2, o1);
+    if (take) { m1 = o1; i1 = oi; }
+    m2 = rest;
+}
+
+// Tiled scores of rows against centroids.  TOP2: fused certified argmin per
+// row (list id or -1 + queue entry).  !TOP2: write every score S[row][l].
+template <bool TOP2>
+__global__ void __launch_bounds__(256) coarse_scores_kernel(const float *__restrict__ X, int64_t N, int D,
+                                                            const float *__restrict__ C, int nlist,
+                                                            const float *__restrict__ half_norm,
+                                                            const float *__restrict__ maxes,
+                                                            int32_t *__restrict__ list_of_row,
+                                                            int64_t *__restrict__ queue,
+                                                            unsigned long long *__restrict__ queue_len,
+                                                            float *__restrict__ S)
+{
+    __shared__ __align__(16) float As[BK][BM + 4];
+    __shared__ __align__(16) float Bs[BK][BN + 4];
+    __shared__ float s_xn[BM];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t r0 = (int64_t)blockIdx.x * BM;
+
+    if (TOP2) {
+        // row norms: 4 threads per row
+        const int r = tid >> 2, part = tid & 3;
+        float acc = 0.0f;
+        if (r0 + r < N)
+            for (int j = part; j < D; j += 4) {
+                const float v = X[(r0 + r) * D + j];
+                acc = fmaf(v, v, acc);
+            }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (part == 0) s_xn[r] = sqrtf(acc) * (1.0f + 1e-6f);
+    }
+
+    float m1[4], m2[4];
+    int i1[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { m1[i] = FLT_MAX; m2[i] = FLT_MAX; i1[i] = 0; }
+
+    for (int c0 = 0; c0 < nlist; c0 += BN) {
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+        for (int k0 = 0; k0 < D; k0 += BK) {
+            __syncthreads();
+            // 64 x 32 floats of each operand, 8 per thread, stored transposed
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int e = tid + t * 256;
+                const int r = e / BK, kk = e % BK;
+                const int64_t gr = r0 + r;
+                const int gk = k0 + kk;
+                As[kk][r] = (gr < N && gk < D) ? X[gr * D + gk] : 0.0f;
+                const int gc = c0 + r;
+                Bs[kk][r] = (gc < nlist && gk < D) ? C[(size_t)gc * D + gk] : 0.0f;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int kk = 0; kk < BK; ++kk) {
+                const float4 a = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
+                const float4 b = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
+                const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int l = c0 + tx * 4 + j;
+            const float cn = l < nlist ? half_norm[l] : 0.0f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float s = l < nlist ? cn - acc[i][j] : FLT_MAX;
+                if (TOP2) {
+                    const bool lt = s < m1[i];
+                    m2[i] = lt ? m1[i] : fminf(m2[i], s);
+                    i1[i] = lt ? l : i1[i];
+                    m1[i] = fminf(m1[i], s);
+                } else {
+                    const int64_t gr = r0 + ty * 4 + i;
+                    if (gr < N && l < nlist) S[gr * nlist + l] = s;
+                }
+            }
+        }
+    }
+    if (TOP2) {
+        // merge across the 16 threads sharing the rows (one half-warp)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int o = 1; o < 16; o <<= 1) {
+                const float o1 = __shfl_xor_sync(0xffffffffu, m1[i], o);
+                const int oi = __shfl_xor_sync(0xffffffffu, i1[i], o);
+                const float o2 = __shfl_xor_sync(0xffffffffu, m2[i], o);
+                top2_merge(m1[i], i1[i], m2[i], o1, oi, o2);
+            }
+        }
+        if (tx == 0) {
+            const float nmax = maxes[0], cmax = maxes[1];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int64_t gr = r0 + ty * 4 + i;
+                if (gr >= N) continue;
+                const float delta = score_delta(s_xn[ty * 4 + i], nmax, cmax, D);
+                if (m2[i] - m1[i] > 2.0f * delta) {
+                    list_of_row[gr] = i1[i];
+                } else {
+                    list_of_row[gr] = -1;
+                    const unsigned long long slot = atomicAdd(queue_len, 1ull);
+                    queue[slot] = gr;
+                }
+            }
+        }
+    }
+}
+
+// One warp per queued row: FP64 direct differences over the candidate window.
+__global__ void coarse_recheck_kernel(const float *__restrict__ X, int D, const float *__restrict__ C, int nlist,
+                                      const float *__restrict__ half_norm, const float *__restrict__ maxes,
+                                      const int64_t *__restrict__ queue, const unsigned long long *queue_len,
+                                      int32_t *__restrict__ list_of_row)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned long long total = *queue_len;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < (int64_t)total; w += nw) {
+        const int64_t row = queue[w];
+        const float *x = X + row * D;
+        float xx = 0.0f;
+        for (int j = lane; j < D; j += 32) xx = fmaf(x[j], x[j], xx);
+        xx = warp_sum(xx);
+        const float xn = sqrtf(xx) * (1.0f + 1e-6f);
+        float lmin = FLT_MAX;
+        for (int l = lane; l < nlist; l += 32) {
+            float acc = 0.0f;
+            for (int j = 0; j < D; ++j) acc = fmaf(x[j], C[(size_t)l * D + j], acc);
+            lmin = fminf(lmin, half_norm[l] - acc);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lmin = fminf(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+        const float win = 2.0f * score_delta(xn, maxes[0], maxes[1], D);
+        double best = DBL_MAX;
+        int bl = 0x7fffffff;
+        for (int l = lane; l < nlist; l += 32) {
+            float acc = 0.0f;
+            for (int j = 0; j < D; ++j) acc = fmaf(x[j], C[(size_t)l * D + j], acc);
+            if (half_norm[l] - acc <= lmin + win) {
+                const double d = d2_fp64(x, C + (size_t)l * D, D);
+                if (d < best) { best = d; bl = l; }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+            if (ob < best || (ob == best && ol < bl)) { best = ob; bl = ol; }
+        }
+        if (lane == 0) list_of_row[row] = bl;
+    }
+}
+
+__global__ void bucket_hist_kernel(const int32_t *__restrict__ lst, int64_t N, int nlist, int *__restrict__ tile_cnt)
+{
+    extern __shared__ int s_hist[];
+    for (int l = threadIdx.x; l < nlist; l += blockDim.x) s_hist[l] = 0;
+    __syncthreads();
+    const int64_t t0 = (int64_t)blockIdx.x * kTileRows;
+    const int64_t t1 = min(N, t0 + kTileRows);
+    for (int64_t n = t0 + threadIdx.x; n < t1; n += blockDim.x) atomicAdd(s_hist + lst[n], 1);
+    __syncthreads();
+    for (int l = threadIdx.x; l < nlist; l += blockDim.x) tile_cnt[(size_t)blockIdx.x * nlist + l] = s_hist[l];
+}
+
+// Per list: running count over tiles (in place) and the list total.
+__global__ void bucket_column_kernel(int *__restrict__ tile_cnt, int n_tiles, int nlist, int64_t *__restrict__ total)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nlist) return;
+    int64_t run = 0;
+    for (int t = 0; t < n_tiles; ++t) {
+        const int c = tile_cnt[(size_t)t * nlist + l];
+        tile_cnt[(size_t)t * nlist + l] = (int)run;
+        run += c;
+    }
+    total[l] = run;
+}
+
+// Exclusive scan of the list totals into offsets[0..nlist], one block.
+__global__ void bucket_offsets_kernel(const int64_t *__restrict__ total, int nlist, int64_t *__restrict__ offsets)
+{
+    __shared__ int64_t s_carry;
+    __shared__ int64_t s_warp[32];
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int base = 0; base < nlist; base += blockDim.x) {
+        const int l = base + threadIdx.x;
+        int64_t v = l < nlist ? total[l] : 0;
+        int64_t inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) s_warp[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            int64_t w = lane < nw ? s_warp[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t t = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += t;
+            }
+            if (lane < nw) s_warp[lane] = w;
+        }
+        __syncthreads();
+        const int64_t before = (wid > 0 ? s_warp[wid - 1] : 0) + s_carry;
+        if (l < nlist) offsets[l] = before + inc - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry = before + inc;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) offsets[nlist] = s_carry;
+}
+
+// One warp per tile walks its rows in order; rows of one list keep ascending ids.
+__global__ void bucket_scatter_kernel(const int32_t *__restrict__ lst, int64_t N, int nlist,
+                                      const int *__restrict__ tile_base, const int64_t *__restrict__ offsets,
+                                      const uint8_t *__restrict__ codes, int M, int64_t *__restrict__ ids,
+                                      uint8_t *__restrict__ list_codes)
+{
+    extern __shared__ int s_run[];
+    const int lane = threadIdx.x;
+    for (int l = lane; l < nlist; l += 32) s_run[l] = 0;
+    __syncwarp();
+    const int64_t t0 = (int64_t)blockIdx.x * kTileRows;
+    const int64_t t1 = min(N, t0 + kTileRows);
+    const int *base = tile_base + (size_t)blockIdx.x * nlist;
+    const bool vec16 = (M == 16) && codes && ((reinterpret_cast<uintptr_t>(codes) & 15) == 0) &&
+                       ((reinterpret_cast<uintptr_t>(list_codes) & 15) == 0);
+    for (int64_t c = t0; c < t1; c += 32) {
+        const int64_t n = c + lane;
+        const bool act = n < t1;
+        const unsigned amask = __ballot_sync(0xffffffffu, act);
+        int l = act ? lst[n] : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, l);
+        if (act) {
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            const int64_t pos = offsets[l] + base[l] + s_run[l] + rank;
+            ids[pos] = n;
+            if (codes) {
+                if (vec16) {
+                    *reinterpret_cast<uint4 *>(list_codes + pos * 16) =
+                        *reinterpret_cast<const uint4 *>(codes + n * 16);
+                } else {
+                    for (int j = 0; j < M; ++j) list_codes[pos * M + j] = codes[n * M + j];
+                }
+            }
+        }
+        __syncwarp();
+        if (act && lane == __ffs(peers & amask) - 1) s_run[l] += __popc(peers & amask);
+        __syncwarp();
+    }
+}
+
+__global__ void list_mean_kernel(const float *__restrict__ X, int D, const int64_t *__restrict__ offsets,
+                                 const int64_t *__restrict__ ids, float *__restrict__ C)
+{
+    const int l = blockIdx.x;
+    const int64_t b = offsets[l], e = offsets[l + 1];
+    if (e == b) return;  // empty list keeps its centroid
+    for (int j = threadIdx.x; j < D; j += blockDim.x) {
+        double s = 0.0;
+        for (int64_t p = b; p < e; ++p) s = __dadd_rn(s, (double)X[ids[p] * D + j]);
+        C[(size_t)l * D + j] = __double2float_rn(__ddiv_rn(s, (double)(e - b)));
+    }
+}
+
+}  // namespace
+
+int launch_coarse_norms(const float *C, int nlist, int D, CoarseBound &b, cudaStream_t s)
+{
+    PQ_TRY_CUDA(cudaMemsetAsync(b.maxes, 0, 2 * sizeof(float), s));
+    const int blocks = std::max(1, std::min((nlist + 255) / 256, 152));
+    ProfScope ps("coarse_norms", s);
+    coarse_norms_kernel<<<blocks, 256, 0, s>>>(C, nlist, D, b.half_norm, b.maxes);
+    coarse_bound_finish<<<1, 1, 0, s>>>(b.maxes, D);
+    count_launch(2);
+    PQ_TRY_CUDA(cudaGetLastError());
+    return PQ_OK;
+}
+
+int coarse_assign(const float *X, int64_t N, int D, const float *C, int nlist, const CoarseBound &b,
+                  int32_t *list_of_row, Scratch &ws, unsigned long long *rechecks, cudaStream_t s)
+{
+    int64_t *queue = ws.get<int64_t>((size_t)N);
+    unsigned long long *qlen = ws.get<unsigned long long>(1, true);
+    if (ws.status) return ws.status;
+    const int64_t blocks = (N + BM - 1) / BM;
+    {
+        ProfScope ps("coarse_assign", s);
+        coarse_scores_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(X, N, D, C, nlist, b.half_norm, b.maxes,
+                                                                   list_of_row, queue, qlen, nullptr);
+    }
+    {
+        ProfScope ps("coarse_recheck", s);
+        coarse_recheck_kernel<<<152 * 4, 256, 0, s>>>(X, D, C, nlist, b.half_norm, b.maxes, queue, qlen,
+                                                      list_of_row);
+    }
+    count_launch(2);
+    PQ_TRY_CUDA(cudaGetLastError());
+    return PQ_OK;
+}
+
+int launch_coarse_all_scores(const float *Q, int64_t nq, int D, const float *C, int nlist, const CoarseBound &b,
+                             float *S, cudaStream_t s)
+{
+    const int64_t blocks = (nq + BM - 1) / BM;
+    ProfScope ps("probe_scores", s);
+    coarse_scores_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(Q, nq, D, C, nlist, b.half_norm, b.maxes, nullptr,
+                                                                nullptr, nullptr, S);
+    count_launch();
+    PQ_TRY_CUDA(cudaGetLastError());
+    return PQ_OK;
+}
+
+int bucket_rows(const int32_t *list_of_row, int64_t N, int nlist, const uint8_t *codes, int M, int64_t *offsets,
+                int64_t *ids, uint8_t *list_codes, Scratch &ws, cudaStream_t s)
+{
+    const int64_t n_tiles = (N + kTileRows - 1) / kTileRows;
+    int *tile_cnt = ws.get<int>((size_t)n_tiles * nlist);
+    int64_t *total = ws.get<int64_t>((size_t)nlist);
+    if (ws.status) return ws.status;
+    const size_t hsm = (size_t)nlist * sizeof(int);
+    if (hsm > 200 * 1024) return fail(PQ_ENOTSUP, "nlist=%d too large for bucketing", nlist);
+    PQ_TRY_CUDA(cudaFuncSetAttribute(bucket_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
+    PQ_TRY_CUDA(cudaFuncSetAttribute(bucket_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
+    ProfScope ps("bucket", s);
+    bucket_hist_kernel<<<(unsigned)n_tiles, 256, hsm, s>>>(list_of_row, N, nlist, tile_cnt);
+    bucket_column_kernel<<<(nlist + 255) / 256, 256, 0, s>>>(tile_cnt, (int)n_tiles, nlist, total);
+    bucket_offsets_kernel<<<1, 1024, 0, s>>>(total, nlist, offsets);
+    bucket_scatter_kernel<<<(unsigned)n_tiles, 32, hsm, s>>>(list_of_row, N, nlist, tile_cnt, offsets, codes, M, ids,
+                                                              list_codes);
+    count_launch(4);
+    PQ_TRY_CUDA(cudaGetLastError());
+    return PQ_OK;
+}
+
+int launch_list_mean(const float *X, int D, const int64_t *offsets, const int64_t *ids, int nlist, float *C,
+                     cudaStream_t s)
+{
+    ProfScope ps("list_mean", s);
+    list_mean_kernel<<<nlist, std::min(256, ((D + 31) / 32) * 32), 0, s>>>(X, D, offsets, ids, C);
+    count_launch();
+    PQ_TRY_CUDA(cudaGetLastError());
+    return PQ_OK;
+}
+
+}  // namespace pqgb

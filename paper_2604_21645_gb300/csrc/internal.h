@@ -1,0 +1,92 @@
+// internal.h -- host-side launchers shared between the libpqgb translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <vector>
+
+namespace pqgb {
+
+// Stream-ordered scratch owned by one API call (freed, stream-ordered, when
+// the call returns).
+struct Scratch {
+    cudaStream_t s = nullptr;
+    std::vector<void *> ptrs;
+    int status = 0;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    ~Scratch();
+    template <typename T>
+    T *get(size_t count, bool zero = false)
+    {
+        return static_cast<T *>(raw(count * sizeof(T), zero));
+    }
+    void *raw(size_t bytes, bool zero);
+};
+
+// ---- k-means++ seeding (kmeanspp.cu) --------------------------------------
+// Seeds Ks codewords in each of M subspaces of width ds from the n rows of P
+// (row stride ld floats; subspace m starts at column m*ds).
+int launch_kmeanspp(const float *P, int64_t ld, int64_t n, int ds, int M, int Ks, uint64_t seed, float *C,
+                    Scratch &ws, int *err, cudaStream_t s);
+// Gathers the seeding subsample (n_s rows drawn with replacement from N) into P.
+int launch_gather_subsample(const float *X, int64_t N, int D, int64_t n_s, uint64_t seed, float *P,
+                            cudaStream_t s);
+
+// ---- PQ Lloyd pass, FP32 SIMT form (lloyd_simt.cu) ------------------------
+struct PqPass {
+    const float *X = nullptr;
+    int64_t N = 0;
+    int D = 0, M = 0, Ks = 0, ds = 0;
+    const float *C = nullptr;      // [M][Ks][ds]
+    uint8_t *codes = nullptr;      // [N][M] or null
+    double *part = nullptr;        // [gx][M][Ks][ds] per-block member sums, or null (no update)
+    int *part_cnt = nullptr;       // [gx][M][Ks]
+    double *sse = nullptr;         // device scalar accumulator or null
+    unsigned long long *rechecks = nullptr;
+    int gx = 0;                    // blocks per subspace (set by the launcher)
+};
+int pq_pass_blocks_per_subspace(const PqPass &p);
+int launch_pq_pass_f32(PqPass &p, cudaStream_t s);
+int launch_pq_finalize(const double *part, const int *part_cnt, int gx, int M, int Ks, int ds, float *C,
+                       unsigned long long *empties, cudaStream_t s);
+int launch_decode_rmse(const uint8_t *codes, const float *C, const float *X, int64_t N, int D, int M, int Ks,
+                       float *Xhat, double *sse, cudaStream_t s);
+
+// ---- PQ Lloyd pass, BF16 tcgen05 form (lloyd_tc.cu) ------------------------
+bool tc_pass_supported(int D, int M, int Ks);
+int launch_pq_pass_tc(PqPass &p, cudaStream_t s);
+
+// ---- coarse quantizer and inverted lists (coarse.cu) ----------------------
+struct CoarseBound {
+    float *half_norm = nullptr;    // [nlist] 0.5*||c||^2
+    float *maxes = nullptr;        // [2]: max half norm, max norm
+};
+int launch_coarse_norms(const float *C, int nlist, int D, CoarseBound &b, cudaStream_t s);
+// Nearest coarse centroid of every row (exact: FP32 bound + FP64 re-check).
+int coarse_assign(const float *X, int64_t N, int D, const float *C, int nlist, const CoarseBound &b,
+                  int32_t *list_of_row, Scratch &ws, unsigned long long *rechecks, cudaStream_t s);
+// Stable bucketing of rows by list: offsets[nlist+1], ids[N] ascending within a list,
+// and, if codes != null, list_codes[N][M] in list order.
+int bucket_rows(const int32_t *list_of_row, int64_t N, int nlist, const uint8_t *codes, int M, int64_t *offsets,
+                int64_t *ids, uint8_t *list_codes, Scratch &ws, cudaStream_t s);
+// Coarse centroid update: FP64 sums of each list's rows in ascending row order.
+int launch_list_mean(const float *X, int D, const int64_t *offsets, const int64_t *ids, int nlist, float *C,
+                     cudaStream_t s);
+
+// ---- query path (ivf_search.cu) --------------------------------------------
+struct SearchArgs {
+    const float *Q = nullptr;
+    int64_t nq = 0;
+    int D = 0, M = 0, Ks = 0, nlist = 0, nprobe = 0, k = 0;
+    const float *coarse = nullptr;
+    const CoarseBound *cb = nullptr;
+    const int64_t *offsets = nullptr;
+    const int64_t *ids = nullptr;
+    const uint8_t *list_codes = nullptr;
+    const float *codebooks = nullptr;
+    int64_t *out_ids = nullptr;
+    float *out_d = nullptr;
+};
+int run_search(const SearchArgs &a, Scratch &ws, cudaStream_t s);
+
+}  // namespace pqgb

@@ -1,0 +1,322 @@
+// lloyd_simt.cu -- PQ Lloyd pass in the plain FP32 form (Sec. 2.1: k-means
+// in every subspace; encode = nearest codeword per subspace), the centroid
+// finalisation, and decode + reconstruction error (Sec. 2.1, Sec. 3).
+//
+// Assignment.  For row x and codeword c_k of subspace m the kernel scores
+//     s_k = ||c_k||^2 / 2 - x . c_k        (argmin s_k == argmin ||x - c_k||^2)
+// with FP32 fused multiply-adds and keeps the two smallest scores.  The
+// rounding error of every score is below
+//     delta = 2.2 gamma_{Ds+1} (max_k ||c_k||^2/2 + ||x|| max_k ||c_k||)
+//             + 1e-13 (||x|| + max_k ||c_k||)^2
+// (the last term covers FP64 rounding of the reference distances).  If the
+// second-best score exceeds the best by more than 2 delta the best index is
+// the exact argmin.  Otherwise every codeword whose score is within 2 delta
+// of the best is re-scored in FP64 by direct differences (the rule of the
+// CPU reference) and the lowest-index minimum wins.  Codes are therefore
+// exact, not approximate.
+//
+// Update.  Members are added into per-block FP64 shared-memory sums (the
+// FP64 adds are a rounding error next to the FP32 distance work of this
+// form); each block writes its sums once, and the finalise kernel adds the
+// blocks in a fixed order in FP64 and divides by the member count.
+#include <algorithm>
+#include <cfloat>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace pqgb {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <int DS>
+struct SmemLayout {
+    static size_t bytes(int Ks, bool fit)
+    {
+        size_t b = (size_t)Ks * DS * sizeof(double);  // sums first: 8-byte aligned
+        b += (size_t)Ks * DS * sizeof(float) + (size_t)Ks * sizeof(float);
+        if (fit) b += (size_t)Ks * sizeof(int);
+        return b;
+    }
+};
+
+template <int DS>
+__device__ __forceinline__ void load_row(const float *__restrict__ src, float (&x)[DS], bool vec)
+{
+    if constexpr (DS % 4 == 0) {
+        if (vec) {
+#pragma unroll
+            for (int j = 0; j < DS; j += 4) {
+                float4 v = __ldg(reinterpret_cast<const float4 *>(src + j));
+                x[j] = v.x; x[j + 1] = v.y; x[j + 2] = v.z; x[j + 3] = v.w;
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < DS; ++j) x[j] = __ldg(src + j);
+}
+
+// Scores of every codeword (same rounding as the main loop).
+template <int DS>
+__device__ __forceinline__ float score(const float (&x)[DS], const float *cb, const float *cn, int k)
+{
+    float s = cn[k];
+#pragma unroll
+    for (int j = 0; j < DS; ++j) s = fmaf(-x[j], cb[k * DS + j], s);
+    return s;
+}
+
+// Uncertain case: FP64 direct-difference distances over the candidate window.
+template <int DS>
+__device__ __noinline__ int fp64_recheck(const float (&x)[DS], const float *cb, const float *cn, int Ks, float m1,
+                                         float win)
+{
+    double best = DBL_MAX;
+    int bk = 0;
+    for (int k = 0; k < Ks; ++k) {
+        if (score<DS>(x, cb, cn, k) <= m1 + win) {
+            double d = d2_fp64(x, cb + k * DS, DS);
+            if (d < best) { best = d; bk = k; }
+        }
+    }
+    return bk;
+}
+
+template <int DS>
+__global__ void __launch_bounds__(kThreads) pq_pass_f32_kernel(const PqPass a, const bool vec)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int m = blockIdx.y, Ks = a.Ks, tid = threadIdx.x;
+    const bool fit = a.part != nullptr;
+    double *acc = reinterpret_cast<double *>(smem_raw);
+    float *cb = reinterpret_cast<float *>(acc + Ks * DS);
+    float *cn = cb + Ks * DS;
+    int *cnt = reinterpret_cast<int *>(cn + Ks);
+    __shared__ float s_red[kThreads / 32];
+    __shared__ double s_sse[kThreads / 32];
+
+    const float *Cm = a.C + (size_t)m * Ks * DS;
+    for (int e = tid; e < Ks * DS; e += kThreads) {
+        cb[e] = Cm[e];
+        if (fit) acc[e] = 0.0;
+    }
+    if (fit)
+        for (int k = tid; k < Ks; k += kThreads) cnt[k] = 0;
+    __syncthreads();
+    float lmax = 0.0f;
+    for (int k = tid; k < Ks; k += kThreads) {
+        float n = 0.0f;
+#pragma unroll
+        for (int j = 0; j < DS; ++j) n = fmaf(cb[k * DS + j], cb[k * DS + j], n);
+        cn[k] = 0.5f * n;
+        lmax = fmaxf(lmax, 0.5f * n);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    if ((tid & 31) == 0) s_red[tid >> 5] = lmax;
+    __syncthreads();
+    float nmax = 0.0f;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) nmax = fmaxf(nmax, s_red[w]);
+    nmax *= 1.0f + 4.0f * gamma_f32(DS + 1);
+    const float cmax = sqrtf(2.0f * nmax) * (1.0f + 1e-6f);
+    const float gam = 2.2f * gamma_f32(DS + 1);
+
+    double sse = 0.0;
+    unsigned rechecks = 0;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int bi = 0;; ++bi) {
+        const int64_t base = (int64_t)bi * stride + (int64_t)blockIdx.x * kThreads;
+        if (base >= a.N) break;
+        const int64_t row = base + tid;
+        if (row < a.N) {
+            float x[DS];
+            load_row<DS>(a.X + row * a.D + (int64_t)m * DS, x, vec);
+            float xx = 0.0f;
+#pragma unroll
+            for (int j = 0; j < DS; ++j) xx = fmaf(x[j], x[j], xx);
+            const float xn = sqrtf(xx) * (1.0f + 1e-6f);
+            float m1 = FLT_MAX, m2 = FLT_MAX;
+            int i1 = 0;
+#pragma unroll 4
+            for (int k = 0; k < Ks; ++k) {
+                const float s = score<DS>(x, cb, cn, k);
+                const bool lt = s < m1;
+                m2 = lt ? m1 : fminf(m2, s);
+                i1 = lt ? k : i1;
+                m1 = fminf(m1, s);
+            }
+            const float t = xn + cmax;
+            const float delta = gam * (nmax + xn * cmax) + 1e-13f * t * t;
+            int code = i1;
+            if (!(m2 - m1 > 2.0f * delta)) {
+                code = fp64_recheck<DS>(x, cb, cn, Ks, m1, 2.0f * delta);
+                ++rechecks;
+            }
+            float e = 0.0f;
+#pragma unroll
+            for (int j = 0; j < DS; ++j) {
+                const float d = x[j] - cb[code * DS + j];
+                e = fmaf(d, d, e);
+            }
+            sse += (double)e;
+            if (a.codes) a.codes[row * a.M + m] = (uint8_t)code;
+            if (fit) {
+#pragma unroll
+                for (int j = 0; j < DS; ++j) atomicAdd(acc + code * DS + j, (double)x[j]);
+                atomicAdd(cnt + code, 1);
+            }
+        }
+    }
+    if (fit) {
+        __syncthreads();
+        double *dst = a.part + ((size_t)blockIdx.x * a.M + m) * Ks * DS;
+        for (int e = tid; e < Ks * DS; e += kThreads) dst[e] = acc[e];
+        int *dc = a.part_cnt + ((size_t)blockIdx.x * a.M + m) * Ks;
+        for (int k = tid; k < Ks; k += kThreads) dc[k] = cnt[k];
+    }
+    if (a.sse) {
+        sse = warp_sum(sse);
+        if ((tid & 31) == 0) s_sse[tid >> 5] = sse;
+        __syncthreads();
+        if (tid == 0) {
+            double v = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) v += s_sse[w];
+            atomicAdd(a.sse, v);
+        }
+    }
+    if (a.rechecks) {
+        unsigned r = warp_sum(rechecks);
+        if ((tid & 31) == 0 && r) atomicAdd(a.rechecks, (unsigned long long)r);
+    }
+}
+
+__global__ void pq_finalize_kernel(const double *__restrict__ part, const int *__restrict__ part_cnt, int gx, int M,
+                                   int Ks, int ds, float *C, unsigned long long *empties)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= M * Ks) return;
+    const int m = idx / Ks, k = idx % Ks;
+    long long cnt = 0;
+    for (int b = 0; b < gx; ++b) cnt += part_cnt[((size_t)b * M + m) * Ks + k];
+    if (cnt == 0) {
+        if (empties) atomicAdd(empties, 1ull);
+        return;
+    }
+    for (int j = 0; j < ds; ++j) {
+        double s = 0.0;
+        for (int b = 0; b < gx; ++b) {
+            s = __dadd_rn(s, part[(((size_t)b * M + m) * Ks + k) * ds + j]);
+        }
+        C[((size_t)m * Ks + k) * ds + j] = __double2float_rn(__ddiv_rn(s, (double)cnt));
+    }
+}
+
+// One thread per (row, subspace): reconstruction and/or squared error.
+__global__ void decode_rmse_kernel(const uint8_t *__restrict__ codes, const float *__restrict__ C,
+                                   const float *__restrict__ X, int64_t N, int D, int M, int Ks, int ds,
+                                   float *__restrict__ Xhat, double *sse)
+{
+    __shared__ double s_sse[8];
+    double acc = 0.0;
+    const int64_t total = N * M;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = i / M;
+        const int m = (int)(i - n * M);
+        const int code = codes[i];
+        if (code >= Ks) continue;  // not a codeword index: contributes nothing
+        const float *c = C + ((size_t)m * Ks + code) * ds;
+        const int64_t off = n * D + (int64_t)m * ds;
+        float e = 0.0f;
+        for (int j = 0; j < ds; ++j) {
+            const float v = c[j];
+            if (Xhat) Xhat[off + j] = v;
+            if (X) {
+                const float d = X[off + j] - v;
+                e = fmaf(d, d, e);
+            }
+        }
+        acc += (double)e;
+    }
+    if (sse) {
+        acc = warp_sum(acc);
+        if ((threadIdx.x & 31) == 0) s_sse[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double v = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s_sse[w];
+            atomicAdd(sse, v);
+        }
+    }
+}
+
+template <int DS>
+int launch_ds(PqPass &p, cudaStream_t s)
+{
+    const bool fit = p.part != nullptr;
+    const size_t smem = SmemLayout<DS>::bytes(p.Ks, fit);
+    PQ_TRY_CUDA(cudaFuncSetAttribute(pq_pass_f32_kernel<DS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const bool vec = (p.D % 4 == 0) && ((reinterpret_cast<uintptr_t>(p.X) & 15) == 0);
+    dim3 grid(p.gx, p.M);
+    ProfScope ps("pq_pass_f32", s);
+    pq_pass_f32_kernel<DS><<<grid, kThreads, smem, s>>>(p, vec);
+    count_launch();
+    PQ_TRY_CUDA(cudaGetLastError());
+    return PQ_OK;
+}
+
+}  // namespace
+
+int pq_pass_blocks_per_subspace(const PqPass &p)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+    // about four resident blocks per SM over all subspaces, never more than the rows need
+    const int64_t want = std::max<int64_t>(1, (4LL * sms + p.M - 1) / p.M);
+    const int64_t need = (p.N + kThreads - 1) / kThreads;
+    return (int)std::max<int64_t>(1, std::min(want, need));
+}
+
+int launch_pq_pass_f32(PqPass &p, cudaStream_t s)
+{
+    if (p.gx <= 0) p.gx = pq_pass_blocks_per_subspace(p);
+    switch (p.ds) {
+    case 1: return launch_ds<1>(p, s);
+    case 2: return launch_ds<2>(p, s);
+    case 4: return launch_ds<4>(p, s);
+    case 8: return launch_ds<8>(p, s);
+    case 16: return launch_ds<16>(p, s);
+    case 32: return launch_ds<32>(p, s);
+    default: return fail(PQ_ENOTSUP, "subspace width Ds=%d not supported (1, 2, 4, 8, 16 or 32)", p.ds);
+    }
+}
+
+int launch_pq_finalize(const double *part, const int *part_cnt, int gx, int M, int Ks, int ds, float *C,
+                       unsigned long long *empties, cudaStream_t s)
+{
+    const int n = M * Ks;
+    ProfScope ps("pq_finalize", s);
+    pq_finalize_kernel<<<(n + 127) / 128, 128, 0, s>>>(part, part_cnt, gx, M, Ks, ds, C, empties);
+    count_launch();
+    PQ_TRY_CUDA(cudaGetLastError());
+    return PQ_OK;
+}
+
+int launch_decode_rmse(const uint8_t *codes, const float *C, const float *X, int64_t N, int D, int M, int Ks,
+                       float *Xhat, double *sse, cudaStream_t s)
+{
+    const int64_t total = N * M;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 8));
+    ProfScope ps("decode_rmse", s);
+    decode_rmse_kernel<<<blocks, 256, 0, s>>>(codes, C, X, N, D, M, Ks, D / M, Xhat, sse);
+    count_launch();
+    PQ_TRY_CUDA(cudaGetLastError());
+    return PQ_OK;
+}
+
+}  // namespace pqgb

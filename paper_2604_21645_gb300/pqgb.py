@@ -1,0 +1,252 @@
+"""ctypes binding of ``libpqgb.so`` (C ABI in ``include/pqgb.h``).
+
+Argument marshalling only: tensors are checked for device, dtype, shape and
+contiguity and their device pointers are passed with the current CUDA stream.
+Every step of the computation runs in the library's kernels; there is no CPU
+or PyTorch fallback, and importing this module raises if the library has not
+been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpqgb.so")
+
+PQ_OK, PQ_EINVAL, PQ_ENOMEM, PQ_ECUDA, PQ_ETIMEOUT, PQ_ENOTSUP = 0, -1, -2, -3, -4, -5
+PQ_PREC_FP32, PQ_PREC_BF16 = 0, 1
+PREC = {"fp32": PQ_PREC_FP32, "bf16": PQ_PREC_BF16}
+STATS_MAX_ITERS = 64
+EXPORTS = ("pq_fit", "pq_init_kmeanspp", "pq_encode", "pq_decode_rmse", "ivf_build", "ivf_search", "ivf_get_info",
+           "ivf_copy_coarse", "ivf_copy_lists", "ivf_free", "pq_sync_status", "pq_last_error", "pq_launch_count",
+           "pq_profile_enable", "pq_profile_collect", "pq_profile_names")
+
+
+class PqStats(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("reserved", C.c_int32), ("fp64_rechecks", C.c_int64),
+                ("empty_clusters", C.c_int64), ("kernel_launches", C.c_int64),
+                ("sse", C.c_double * STATS_MAX_ITERS)]
+
+    def as_dict(self):
+        return {"iters": self.iters, "fp64_rechecks": self.fp64_rechecks, "empty_clusters": self.empty_clusters,
+                "kernel_launches": self.kernel_launches, "sse": list(self.sse[:self.iters])}
+
+
+class PqError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libpqgb status {status}: {msg}")
+        self.status = status
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    p, i64, i32, u64, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_uint64, C.c_double
+    sigs = {
+        "pq_fit": (i32, [p, i64, i32, i32, i32, i32, u64, i32, p, p, C.POINTER(PqStats), p]),
+        "pq_init_kmeanspp": (i32, [p, i64, i32, i32, i32, u64, p, p]),
+        "pq_encode": (i32, [p, i64, i32, i32, i32, p, i32, p, p, C.POINTER(PqStats), p]),
+        "pq_decode_rmse": (i32, [p, p, p, i64, i32, i32, i32, p, C.POINTER(dbl), p]),
+        "ivf_build": (i32, [p, p, i64, i32, i32, i32, i32, u64, i32, C.POINTER(p), p]),
+        "ivf_search": (i32, [p, p, i32, p, i64, i32, i32, p, p, p]),
+        "ivf_get_info": (i32, [p, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
+        "ivf_copy_coarse": (i32, [p, p, p]),
+        "ivf_copy_lists": (i32, [p, p, p, p, p]),
+        "ivf_free": (None, [p]),
+        "pq_sync_status": (i32, [p]),
+        "pq_last_error": (C.c_char_p, []),
+        "pq_launch_count": (i64, []),
+        "pq_profile_enable": (i32, [i32]),
+        "pq_profile_collect": (i32, [C.c_char_p, C.POINTER(i64), C.POINTER(dbl)]),
+        "pq_profile_names": (i32, [C.c_char_p, i32]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = load_library()
+
+
+def lib() -> C.CDLL:
+    return _lib
+
+
+def _check(status):
+    if status != PQ_OK:
+        raise PqError(status, _lib.pq_last_error().decode(errors="replace"))
+
+
+def _stream(t: torch.Tensor | None = None):
+    dev = t.device if t is not None else torch.device("cuda", torch.cuda.current_device())
+    return C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _need(t, dtype, ndim, name):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.dim() != ndim:
+        raise ValueError(f"{name} must have {ndim} dims, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def launch_count() -> int:
+    return _lib.pq_launch_count()
+
+
+def profile_enable(on: bool = True):
+    """Start (clearing old records) or stop per-kernel CUDA-event timing inside the library."""
+    _check(_lib.pq_profile_enable(1 if on else 0))
+
+
+def profile_collect() -> dict:
+    """{kernel name: {"launches": n, "ms": summed device time}} of the recorded launches (synchronizes)."""
+    buf = C.create_string_buffer(8192)
+    _check(_lib.pq_profile_names(buf, len(buf)))
+    out = {}
+    for name in filter(None, buf.value.decode().split(",")):
+        cnt, ms = C.c_int64(), C.c_double()
+        _check(_lib.pq_profile_collect(name.encode(), C.byref(cnt), C.byref(ms)))
+        out[name] = {"launches": cnt.value, "ms": ms.value}
+    return out
+
+
+def sync_status(stream=None):
+    _check(_lib.pq_sync_status(stream if stream is not None else _stream()))
+
+
+def init_kmeanspp(X: torch.Tensor, M: int, Ks: int, seed: int) -> torch.Tensor:
+    """k-means++ seeding of the M subspace codebooks (the first step of ``fit``)."""
+    px = _need(X, torch.float32, 2, "X")
+    N, D = X.shape
+    cb = torch.empty((M, Ks, D // M), dtype=torch.float32, device=X.device)
+    with torch.cuda.device(X.device):
+        _check(_lib.pq_init_kmeanspp(px, N, D, M, Ks, seed & (2**64 - 1), C.c_void_p(cb.data_ptr()), _stream(X)))
+    return cb
+
+
+def fit(X: torch.Tensor, M: int, Ks: int = 256, iters: int = 20, seed: int = 0, prec: str = "fp32",
+        init: torch.Tensor | None = None, out: torch.Tensor | None = None, stats: bool = False):
+    """PQ fit (Sec. 2.1): returns codebooks [M][Ks][D/M] (and a stats dict if ``stats``)."""
+    px = _need(X, torch.float32, 2, "X")
+    N, D = X.shape
+    if out is None:
+        out = torch.empty((M, Ks, D // M), dtype=torch.float32, device=X.device)
+    po = _need(out, torch.float32, 3, "out")
+    pi = _need(init, torch.float32, 3, "init") if init is not None else None
+    st = PqStats() if stats else None
+    with torch.cuda.device(X.device):
+        _check(_lib.pq_fit(px, N, D, M, Ks, iters, seed & (2**64 - 1), PREC[prec], pi, po,
+                           C.byref(st) if st is not None else None, _stream(X)))
+    return (out, st.as_dict()) if stats else out
+
+
+def encode(X: torch.Tensor, codebooks: torch.Tensor, prec: str = "fp32", out: torch.Tensor | None = None,
+           sse: torch.Tensor | None = None, stats: bool = False):
+    """PQ encode (Sec. 2.1): uint8 codes [N][M]; ``sse`` (device float64 [1]) receives sum (x - xhat)^2."""
+    px = _need(X, torch.float32, 2, "X")
+    pc = _need(codebooks, torch.float32, 3, "codebooks")
+    N, D = X.shape
+    M, Ks, _ = codebooks.shape
+    if out is None:
+        out = torch.empty((N, M), dtype=torch.uint8, device=X.device)
+    po = _need(out, torch.uint8, 2, "codes")
+    ps = _need(sse, torch.float64, 1, "sse") if sse is not None else None
+    st = PqStats() if stats else None
+    with torch.cuda.device(X.device):
+        _check(_lib.pq_encode(px, N, D, M, Ks, pc, PREC[prec], po, ps, C.byref(st) if st is not None else None,
+                              _stream(X)))
+    return (out, st.as_dict()) if stats else out
+
+
+def decode_rmse(codes: torch.Tensor, codebooks: torch.Tensor, X: torch.Tensor | None = None,
+                want_xhat: bool = False):
+    """Decode and RMSE (Sec. 2.1, Sec. 3): returns (xhat or None, rmse or None)."""
+    pcodes = _need(codes, torch.uint8, 2, "codes")
+    pc = _need(codebooks, torch.float32, 3, "codebooks")
+    N, M = codes.shape
+    _, Ks, ds = codebooks.shape
+    D = M * ds
+    px = _need(X, torch.float32, 2, "X") if X is not None else None
+    xhat = torch.empty((N, D), dtype=torch.float32, device=codes.device) if want_xhat else None
+    r = C.c_double(0.0)
+    with torch.cuda.device(codes.device):
+        _check(_lib.pq_decode_rmse(pcodes, pc, px, N, D, M, Ks, C.c_void_p(xhat.data_ptr()) if xhat is not None
+                                   else None, C.byref(r) if X is not None else None, _stream(codes)))
+    return xhat, (r.value if X is not None else None)
+
+
+class IVFIndex:
+    """Inverted-file index over PQ codes (Sec. 2.2, Sec. 3.1); owns a library handle."""
+
+    def __init__(self, handle: int, device: torch.device):
+        self._h = C.c_void_p(handle)
+        self.device = device
+        N, D, M, nl = C.c_int64(), C.c_int32(), C.c_int32(), C.c_int32()
+        _check(_lib.ivf_get_info(self._h, C.byref(N), C.byref(D), C.byref(M), C.byref(nl)))
+        self.N, self.D, self.M, self.nlist = N.value, D.value, M.value, nl.value
+
+    @classmethod
+    def build(cls, X: torch.Tensor, codes: torch.Tensor, nlist: int, iters: int = 25, seed: int = 0,
+              prec: str = "fp32") -> "IVFIndex":
+        px = _need(X, torch.float32, 2, "X")
+        pc = _need(codes, torch.uint8, 2, "codes")
+        N, D = X.shape
+        M = codes.shape[1]
+        h = C.c_void_p()
+        with torch.cuda.device(X.device):
+            _check(_lib.ivf_build(px, pc, N, D, M, nlist, iters, seed & (2**64 - 1), PREC[prec], C.byref(h),
+                                  _stream(X)))
+        return cls(h.value, X.device)
+
+    def search(self, codebooks: torch.Tensor, Q: torch.Tensor, nprobe: int, k: int, out_ids=None, out_d=None):
+        pc = _need(codebooks, torch.float32, 3, "codebooks")
+        pq = _need(Q, torch.float32, 2, "Q")
+        nq = Q.shape[0]
+        if out_ids is None:
+            out_ids = torch.empty((nq, k), dtype=torch.int64, device=Q.device)
+        if out_d is None:
+            out_d = torch.empty((nq, k), dtype=torch.float32, device=Q.device)
+        pi = _need(out_ids, torch.int64, 2, "ids")
+        pd = _need(out_d, torch.float32, 2, "dists")
+        with torch.cuda.device(Q.device):
+            _check(_lib.ivf_search(self._h, pc, codebooks.shape[1], pq, nq, nprobe, k, pi, pd, _stream(Q)))
+        return out_ids, out_d
+
+    def coarse(self) -> torch.Tensor:
+        out = torch.empty((self.nlist, self.D), dtype=torch.float32, device=self.device)
+        with torch.cuda.device(self.device):
+            _check(_lib.ivf_copy_coarse(self._h, C.c_void_p(out.data_ptr()), _stream(out)))
+        return out
+
+    def lists(self):
+        off = torch.empty(self.nlist + 1, dtype=torch.int64, device=self.device)
+        ids = torch.empty(self.N, dtype=torch.int64, device=self.device)
+        codes = torch.empty((self.N, self.M), dtype=torch.uint8, device=self.device)
+        with torch.cuda.device(self.device):
+            _check(_lib.ivf_copy_lists(self._h, C.c_void_p(off.data_ptr()), C.c_void_p(ids.data_ptr()),
+                                       C.c_void_p(codes.data_ptr()), _stream(off)))
+        return off, ids, codes
+
+    def close(self):
+        if self._h:
+            _lib.ivf_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,106 @@
+"""GPU parity for the inverted index (Sec. 2.2, Sec. 3.1) against the FP64 oracle.
+
+Build: coarse centroids, list offsets, ids and list-ordered codes bit-exact
+(exact nearest-list decisions, FP64 list means in row order, identical
+seeding).  Query: ranked distances within 1e-5 relative and ids equal except
+where the oracle's own distances tie within 1e-5 relative (counted).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from paper_2604_21645_gb300 import datagen
+from tests.parity import check_topk
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pq():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_21645_gb300 import pqgb
+    return pqgb
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.fixture(scope="module")
+def setup(pq):
+    N, D, M, Ks, nlist = 60_037, 32, 8, 64, 48
+    X = datagen.mixture(N, D, 40, "int255", 4242)
+    cb, _ = orc.pq_fit(X[:20_000], M, Ks, 4, 17)
+    codes = orc.pq_encode(X, cb)
+    ref = orc.ivf_build(X, codes, nlist, 4, 99)
+    idx = pq.IVFIndex.build(dev(X), dev(codes), nlist, iters=4, seed=99)
+    Q = datagen.queries(300, D, 40, "int255", 4242)
+    return dict(X=X, cb=cb, codes=codes, ref=ref, idx=idx, Q=Q, nlist=nlist)
+
+
+def test_build_matches_oracle(setup):
+    ref, idx = setup["ref"], setup["idx"]
+    assert np.array_equal(idx.coarse().cpu().numpy(), ref["coarse"])
+    off, ids, codes = (t.cpu().numpy() for t in idx.lists())
+    assert np.array_equal(off, ref["offsets"])
+    assert np.array_equal(ids, ref["ids"])
+    assert np.array_equal(codes, ref["list_codes"])
+
+
+@pytest.mark.parametrize("nprobe,k", [(1, 1), (4, 10), (8, 100), (48, 50)])
+def test_search_matches_oracle(pq, setup, nprobe, k):
+    ref_ids, ref_d, _ = orc.ivf_search(setup["ref"], setup["cb"], setup["Q"], nprobe, k)
+    ids, d = setup["idx"].search(dev(setup["cb"]), dev(setup["Q"]), nprobe, k)
+    ties = check_topk(ids.cpu().numpy(), d.cpu().numpy(), ref_ids, ref_d)
+    assert ties <= 0.01 * ref_ids.size
+
+
+def test_search_pads_missing_results(pq):
+    N, D, M, Ks, nlist = 2_000, 16, 4, 16, 40
+    X = datagen.mixture(N, D, 8, "cont", 5)
+    cb, _ = orc.pq_fit(X, M, Ks, 3, 2)
+    codes = orc.pq_encode(X, cb)
+    ref = orc.ivf_build(X, codes, nlist, 3, 7)
+    idx = pq.IVFIndex.build(dev(X), dev(codes), nlist, iters=3, seed=7)
+    Q = datagen.queries(20, D, 8, "cont", 5)
+    k = 600  # more than the candidates of two lists
+    ref_ids, ref_d, _ = orc.ivf_search(ref, cb, Q, 2, k)
+    ids, d = idx.search(dev(cb), dev(Q), 2, k)
+    ids, d = ids.cpu().numpy(), d.cpu().numpy()
+    assert np.array_equal(ids < 0, ref_ids < 0)
+    assert np.all(np.isinf(d[ids < 0]))
+    check_topk(ids, d, ref_ids, ref_d)
+
+
+def test_search_argument_errors(pq, setup):
+    idx, cb, Q = setup["idx"], dev(setup["cb"]), dev(setup["Q"])
+    for nprobe, k in [(0, 10), (setup["nlist"] + 1, 10), (4, 0), (4, 1025)]:
+        with pytest.raises(pq.PqError) as e:
+            idx.search(cb, Q, nprobe, k)
+        assert e.value.status == pq.PQ_EINVAL
+
+
+@pytest.mark.slow
+def test_full_size_medium_config_recall(pq):
+    """1M x 128, M=16, Ks=256, nlist=1024, nprobe=16, top-100: the benchmarked pipeline.
+    Recall@R of the exact FP64 1-NN among the ADC top-100 on 500 sampled queries."""
+    w = datagen.IVF_MEDIUM
+    X = w.data()
+    Xd = dev(X)
+    cbs = pq.fit(Xd, w.m, w.ks, iters=w.iters, seed=w.init_seed)
+    codes = pq.encode(Xd, cbs)
+    idx = pq.IVFIndex.build(Xd, codes, w.nlist, iters=w.ivf_iters, seed=w.coarse_seed)
+    off, ids, _ = idx.lists()
+    off = off.cpu().numpy()
+    assert off[0] == 0 and off[-1] == w.n and np.all(np.diff(off) >= 0)
+    Q = w.queries()
+    got_ids, got_d = idx.search(cbs, dev(Q), w.nprobe, w.topk)
+    got_ids, got_d = got_ids.cpu().numpy(), got_d.cpu().numpy()
+    assert np.all(np.diff(got_d, axis=1) >= 0)
+    sample = np.random.default_rng(0).choice(w.nq, 500, replace=False)
+    nn, _ = orc.exact_knn(X, Q[sample], 1)
+    rec = {r: float(np.mean([nn[i, 0] in got_ids[q, :r] for i, q in enumerate(sample)])) for r in (1, 10, 100)}
+    print("recall", rec)
+    assert rec[100] >= 0.9 and rec[10] >= 0.6
