@@ -280,8 +280,8 @@ int pq_encode(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, const
     g_msg[0] = 0;
     PQ_TRY(check_pq_shape(N, D, M, Ks, false));
     PQ_TRY(check_prec(prec));
-    if (!X || !codebooks || !codes) return fail(PQ_EINVAL, "null pointer");
-    if (!aligned16(X)) return fail(PQ_EINVAL, "X must be 16-byte aligned");
+    if (!codebooks || (N > 0 && (!X || !codes))) return fail(PQ_EINVAL, "null pointer");
+    if (N > 0 && !aligned16(X)) return fail(PQ_EINVAL, "X must be 16-byte aligned");
     if (prec == PQ_PREC_BF16 && !tc_pass_supported(D, M, Ks))
         return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and Ks == 256");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -319,7 +319,11 @@ int pq_decode_rmse(const uint8_t *codes, const float *codebooks, const float *X,
 {
     g_msg[0] = 0;
     PQ_TRY(check_pq_shape(N, D, M, Ks, false));
-    if (!codes || !codebooks) return fail(PQ_EINVAL, "null pointer");
+    if (!codebooks || (N > 0 && !codes)) return fail(PQ_EINVAL, "null pointer");
+    if (N == 0 && rmse) {
+        *rmse = 0.0;
+        return PQ_OK;
+    }
     if (!Xhat && !(X && rmse)) return fail(PQ_EINVAL, "nothing to compute: give Xhat and/or X with rmse");
     if (X && !rmse) return fail(PQ_EINVAL, "X given without rmse");
     cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -196,6 +196,8 @@ __global__ void __launch_bounds__(kThreads) kmeanspp_kernel(KppArgs a)
             float d = d2_f32_exact(Pm + (i0 + i) * a.ld, s_center, ds);
             if (d < s_d2[i]) s_d2[i] = d;
         }
+        // The update is strided over threads, the next round's sums walk contiguous segments.
+        __syncthreads();
         // s_pick is rewritten by thread 0 only after the next barrier, which every thread passes first.
     }
 }
@@ -234,6 +236,9 @@ int launch_kmeanspp(const float *P, int64_t ld, int64_t n, int ds, int M, int Ks
     PQ_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int smem_cap = 0;
     PQ_TRY_CUDA(cudaDeviceGetAttribute(&smem_cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    PQ_TRY_CUDA(cudaFuncGetAttributes(&fa, kmeanspp_kernel));
+    smem_cap -= (int)fa.sharedSizeBytes;  // the opt-in limit covers static + dynamic shared memory
 
     // Blocks per subspace: enough that each block's D2 slice fits shared
     // memory, at most one point in 64 per block, and the whole grid co-resident.
