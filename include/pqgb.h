@@ -123,6 +123,27 @@ int pq_encode(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, const
 int pq_decode_rmse(const uint8_t *codes, const float *codebooks, const float *X, int64_t N, int32_t D, int32_t M,
                    int32_t Ks, float *Xhat, double *rmse, void *stream);
 
+/*
+ * pq_lloyd_noalloc -- the Lloyd iterations of pq_fit (FP32 form) from given
+ * initial codebooks, without allocating any device memory.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate while
+ * they run (a process whose GPU memory is reserved up front by its own
+ * allocator, or a latency-bound loop where cudaMalloc could block or fail).
+ *   X               [N][D] float32, 16-byte aligned, N >= Ks >= 1, Ks <= 256.
+ *   init_codebooks  [M][Ks][Ds] (required: no k-means++ seeding here).
+ *   codebooks       [M][Ks][Ds] output (may alias init_codebooks).
+ * Results equal pq_fit(..., PQ_PREC_FP32, init_codebooks, ...) up to the FP64
+ * summation order of the member sums.  Scratch is a fixed 8 MiB array inside
+ * the library that every GPU loading it keeps until exit; shapes needing more
+ * than that for one block per subspace, M*Ks*(8*D/M + 4) > 8 MiB, are rejected
+ * with PQ_EINVAL.  The first call on each device looks up the array's device
+ * address (make that first call before any stream capture).  All calls share
+ * the array: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and must be serialized by the caller.
+ */
+int pq_lloyd_noalloc(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, int32_t iters,
+                     const float *init_codebooks, float *codebooks, void *stream);
+
 /* Opaque inverted-file index, allocated by ivf_build and owned by the library until ivf_free. */
 typedef struct ivf_index ivf_index;
 

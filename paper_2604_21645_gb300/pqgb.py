@@ -22,7 +22,7 @@ PREC = {"fp32": PQ_PREC_FP32, "bf16": PQ_PREC_BF16}
 STATS_MAX_ITERS = 64
 EXPORTS = ("pq_fit", "pq_init_kmeanspp", "pq_encode", "pq_decode_rmse", "ivf_build", "ivf_search", "ivf_get_info",
            "ivf_copy_coarse", "ivf_copy_lists", "ivf_free", "pq_sync_status", "pq_last_error", "pq_launch_count",
-           "pq_profile_enable", "pq_profile_collect", "pq_profile_names")
+           "pq_profile_enable", "pq_profile_collect", "pq_profile_names", "pq_lloyd_noalloc")
 
 
 class PqStats(C.Structure):
@@ -63,6 +63,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "pq_profile_enable": (i32, [i32]),
         "pq_profile_collect": (i32, [C.c_char_p, C.POINTER(i64), C.POINTER(dbl)]),
         "pq_profile_names": (i32, [C.c_char_p, i32]),
+        "pq_lloyd_noalloc": (i32, [p, i64, i32, i32, i32, i32, p, p, p]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -151,6 +152,26 @@ def fit(X: torch.Tensor, M: int, Ks: int = 256, iters: int = 20, seed: int = 0, 
         _check(_lib.pq_fit(px, N, D, M, Ks, iters, seed & (2**64 - 1), PREC[prec], pi, po,
                            C.byref(st) if st is not None else None, _stream(X)))
     return (out, st.as_dict()) if stats else out
+
+
+def lloyd_noalloc(X: torch.Tensor, init: torch.Tensor, iters: int, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Lloyd iterations from ``init`` without any device allocation inside the library.
+
+    For callers that must not allocate device memory during the call (memory reserved up
+    front by their own allocator, or a latency-bound loop): the scratch is a fixed array
+    inside the library.  ``out`` (allocate it beforehand) receives the codebooks.
+    Concurrent calls that overlap on the GPU share that array and must be serialized.
+    """
+    px = _need(X, torch.float32, 2, "X")
+    pi = _need(init, torch.float32, 3, "init")
+    N, D = X.shape
+    M, Ks, _ = init.shape
+    if out is None:
+        out = torch.empty_like(init)
+    po = _need(out, torch.float32, 3, "out")
+    with torch.cuda.device(X.device):
+        _check(_lib.pq_lloyd_noalloc(px, N, D, M, Ks, iters, pi, po, _stream(X)))
+    return out
 
 
 def encode(X: torch.Tensor, codebooks: torch.Tensor, prec: str = "fp32", out: torch.Tensor | None = None,
