@@ -150,7 +150,7 @@ int run_pass(PqPass &p, int prec, cudaStream_t s)
 {
     if (prec == PQ_PREC_BF16) {
         if (!tc_pass_supported(p.D, p.M, p.Ks))
-            return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and Ks == 256");
+            return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and M a multiple of 4");
         return launch_pq_pass_tc(p, s);
     }
     return launch_pq_pass_f32(p, s);
@@ -192,7 +192,8 @@ int lloyd(const float *X, int64_t N, int D, int M, int Ks, int iters, int prec, 
     p.Ks = Ks;
     p.ds = D / M;
     p.C = C;
-    p.gx = pq_pass_blocks_per_subspace(p);
+    const bool tc = prec == PQ_PREC_BF16;
+    p.gx = tc ? pq_pass_tc_blocks(p) : pq_pass_blocks_per_subspace(p);
     p.part = ws.get<double>((size_t)p.gx * M * Ks * p.ds);
     p.part_cnt = ws.get<int>((size_t)p.gx * M * Ks);
     if (ws.status) return ws.status;
@@ -200,7 +201,10 @@ int lloyd(const float *X, int64_t N, int D, int M, int Ks, int iters, int prec, 
     for (int t = 0; t < iters; ++t) {
         p.sse = sse_dev ? sse_dev + t : nullptr;
         PQ_TRY(run_pass(p, prec, s));
-        PQ_TRY(launch_pq_finalize(p.part, p.part_cnt, p.gx, M, Ks, p.ds, C, counters + 1, s));
+        if (tc)
+            PQ_TRY(launch_pq_finalize_residual(p.part, p.part_cnt, p.gx, M, Ks, p.ds, C, counters + 1, s));
+        else
+            PQ_TRY(launch_pq_finalize(p.part, p.part_cnt, p.gx, M, Ks, p.ds, C, counters + 1, s));
     }
     return PQ_OK;
 }
@@ -236,7 +240,7 @@ int pq_fit(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, int32_t 
     if (iters < 0 || iters > PQ_STATS_MAX_ITERS) return fail(PQ_EINVAL, "iters=%d must be in [0, %d]", iters,
                                                              PQ_STATS_MAX_ITERS);
     if (prec == PQ_PREC_BF16 && !tc_pass_supported(D, M, Ks))
-        return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and Ks == 256");
+        return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and M a multiple of 4");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t l0 = g_launches.load();
     int dev = 0;
@@ -283,7 +287,7 @@ int pq_encode(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, const
     if (!codebooks || (N > 0 && (!X || !codes))) return fail(PQ_EINVAL, "null pointer");
     if (N > 0 && !aligned16(X)) return fail(PQ_EINVAL, "X must be 16-byte aligned");
     if (prec == PQ_PREC_BF16 && !tc_pass_supported(D, M, Ks))
-        return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and Ks == 256");
+        return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and M a multiple of 4");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t l0 = g_launches.load();
     if (sse) PQ_TRY_CUDA(cudaMemsetAsync(sse, 0, sizeof(double), s));

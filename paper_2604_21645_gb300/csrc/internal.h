@@ -54,7 +54,11 @@ int launch_decode_rmse(const uint8_t *codes, const float *C, const float *X, int
 
 // ---- PQ Lloyd pass, BF16 tcgen05 form (lloyd_tc.cu) ------------------------
 bool tc_pass_supported(int D, int M, int Ks);
+int pq_pass_tc_blocks(const PqPass &p);
+// writes per-CTA residual sums (x - c_code) into p.part; finalise with the residual kernel
 int launch_pq_pass_tc(PqPass &p, cudaStream_t s);
+int launch_pq_finalize_residual(const double *part, const int *part_cnt, int gx, int M, int Ks, int ds, float *C,
+                                unsigned long long *empties, cudaStream_t s);
 
 // ---- coarse quantizer and inverted lists (coarse.cu) ----------------------
 struct CoarseBound {

@@ -12,9 +12,14 @@
 //          smallest i whose inclusive prefix sum exceeds floor(r * W / 2^53),
 //          r the 53-bit draw t of stream m; W == 0 falls back to floor(u*n).
 //
-// One cooperative launch seeds all M subspaces: blocks (b, m) own a slice of
-// the points of subspace m and keep its D2 values in shared memory; each
-// round costs two barriers among the blocks of subspace m (bounded spins).
+// One cooperative launch seeds all M subspaces.  Block b of subspace m owns
+// points [b*nb, (b+1)*nb).  Per round it folds the newest seed into its D2
+// values, publishes the sum of its weights and meets the other blocks of
+// subspace m at one bounded barrier; then every block finds, by itself, the
+// block whose weights hold the threshold and walks that block's D2 values to
+// the picked point.  D2 and the block sums are double-buffered in global
+// memory (round t reads buffer t&1 and writes buffer (t+1)&1), so a block
+// running ahead never overwrites what a slower block still reads.
 #include <algorithm>
 
 #include "common.cuh"
@@ -23,7 +28,8 @@
 namespace pqgb {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
+constexpr int kWarps = kThreads / 32;
 
 struct KppArgs {
     const float *P;
@@ -33,9 +39,9 @@ struct KppArgs {
     uint64_t seed;
     float *C;                     // [M][Ks][ds]
     unsigned *bars;               // [M][2]
-    unsigned long long *bsum;     // [M][bps]
+    unsigned long long *bsum;     // [2][M][bps]
+    float *d2;                    // [2][M][n]
     unsigned *dmax_bits;          // [M]
-    long long *sel;               // [M]
     int *err;
     int bps;
     int64_t nb;                   // points per block
@@ -44,8 +50,36 @@ struct KppArgs {
 __device__ __forceinline__ float d2_f32_exact(const float *x, const float *c, int ds)
 {
     float acc = 0.0f;
-    for (int j = 0; j < ds; ++j) {
-        float t = __fsub_rn(x[j], c[j]);
+    int j = 0;
+    if ((ds & 3) == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+        // Loads are issued 32 floats ahead; the sum itself stays in dimension order.
+        for (; j + 32 <= ds; j += 32) {
+            float4 v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = __ldg(reinterpret_cast<const float4 *>(x + j) + q);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float e[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const float t = __fsub_rn(e[r], c[j + 4 * q + r]);
+                    acc = __fadd_rn(acc, __fmul_rn(t, t));
+                }
+            }
+        }
+        for (; j < ds; j += 4) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(x + j));
+            const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float t = __fsub_rn(e[r], c[j + r]);
+                acc = __fadd_rn(acc, __fmul_rn(t, t));
+            }
+        }
+        return acc;
+    }
+    for (; j < ds; ++j) {
+        const float t = __fsub_rn(x[j], c[j]);
         acc = __fadd_rn(acc, __fmul_rn(t, t));
     }
     return acc;
@@ -56,61 +90,68 @@ __device__ __forceinline__ uint64_t weight(float d2, double scale, bool any)
     return any ? (uint64_t)__double2ull_rz(__dmul_rn((double)d2, scale)) : 0ull;
 }
 
-// Block-wide inclusive scan of one uint64 per thread; returns the inclusive value.
-__device__ __forceinline__ uint64_t block_scan_u64(uint64_t v, uint64_t *sh_warp)
+__device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v)
 {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         uint64_t t = __shfl_up_sync(0xffffffffu, v, o);
         if (lane >= o) v += t;
     }
+    return v;
+}
+
+// Block-wide inclusive scan of one uint64 per thread.
+__device__ __forceinline__ uint64_t block_scan_u64(uint64_t v, uint64_t *sh_warp)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_incl_scan(v);
     if (lane == 31) sh_warp[wid] = v;
     __syncthreads();
     if (wid == 0) {
-        uint64_t w = (lane < kThreads / 32) ? sh_warp[lane] : 0ull;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint64_t t = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += t;
-        }
-        if (lane < kThreads / 32) sh_warp[lane] = w;
+        uint64_t w = lane < kWarps ? sh_warp[lane] : 0ull;
+        w = warp_incl_scan(w);
+        if (lane < kWarps) sh_warp[lane] = w;
     }
     __syncthreads();
-    uint64_t add = wid > 0 ? sh_warp[wid - 1] : 0ull;
+    const uint64_t add = wid > 0 ? sh_warp[wid - 1] : 0ull;
     __syncthreads();
     return v + add;
 }
 
 __global__ void __launch_bounds__(kThreads) kmeanspp_kernel(KppArgs a)
 {
-    extern __shared__ float s_d2[];  // [nb]
     __shared__ float s_center[256];  // ds <= 256
-    __shared__ uint64_t s_warp[kThreads / 32];
-    __shared__ float s_fmax[kThreads / 32];
+    __shared__ uint64_t s_warp[kWarps];
+    __shared__ float s_fmax[kWarps];
     __shared__ long long s_pick;
+    __shared__ int s_owner;
+    __shared__ unsigned long long s_thr;
 
     const int m = blockIdx.y, b = blockIdx.x, tid = threadIdx.x;
     const int ds = a.ds;
     const int64_t i0 = (int64_t)b * a.nb;
-    const int64_t i1 = min(a.n, i0 + a.nb);
-    const int64_t cnt = i1 > i0 ? i1 - i0 : 0;
+    const int64_t cnt = max((int64_t)0, min(a.n, i0 + a.nb) - i0);
     const float *Pm = a.P + (int64_t)m * ds;
     unsigned *bar = a.bars + 2 * m;
     float *Cm = a.C + (size_t)m * a.Ks * ds;
+    const size_t plane = (size_t)a.M * a.n;      // one D2 buffer
+    float *d2m = a.d2 + (size_t)m * a.n;         // + buffer * plane
+    unsigned long long *bs = a.bsum + (size_t)m * a.bps;
+    const size_t bplane = (size_t)a.M * a.bps;
 
     // ---- round 0 -----------------------------------------------------------
     long long pick = scale_index(rng_draw(a.seed, (uint64_t)m, 0) >> 11, (uint64_t)a.n);
     for (int j = tid; j < ds; j += kThreads) {
-        float v = Pm[pick * a.ld + j];
+        const float v = Pm[pick * a.ld + j];
         s_center[j] = v;
         if (b == 0) Cm[j] = v;
     }
     __syncthreads();
     float lmax = 0.0f;
     for (int64_t i = tid; i < cnt; i += kThreads) {
-        float d = d2_f32_exact(Pm + (i0 + i) * a.ld, s_center, ds);
-        s_d2[i] = d;
+        const float d = d2_f32_exact(Pm + (i0 + i) * a.ld, s_center, ds);
+        d2m[plane + i0 + i] = d;  // buffer 1 holds D2 for round 1
         lmax = fmaxf(lmax, d);
     }
 #pragma unroll
@@ -119,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) kmeanspp_kernel(KppArgs a)
     __syncthreads();
     if (tid == 0) {
         float v = 0.0f;
-        for (int w = 0; w < kThreads / 32; ++w) v = fmaxf(v, s_fmax[w]);
+        for (int w = 0; w < kWarps; ++w) v = fmaxf(v, s_fmax[w]);
         atomicMax(a.dmax_bits + m, __float_as_uint(v));  // non-negative floats order as integers
     }
     if (!block_group_barrier(bar, a.bps, a.err)) return;
@@ -128,77 +169,104 @@ __global__ void __launch_bounds__(kThreads) kmeanspp_kernel(KppArgs a)
     int L = 0;
     while (((int64_t)1 << L) < a.n) ++L;
     int E = 0;
-    if (any) E = ((__float_as_uint(dmax) >> 23) & 0xff) - 126;  // dmax in [2^(E-1), 2^E) (dmax normal)
-    if (any && ((__float_as_uint(dmax) >> 23) & 0xff) == 0) {  // subnormal maximum
-        unsigned mant = __float_as_uint(dmax) & 0x7fffff;
-        E = -126 - (__clz(mant) - 9) ;
+    if (any) {
+        const unsigned bits = __float_as_uint(dmax);
+        const int be = (bits >> 23) & 0xff;
+        if (be != 0) E = be - 126;                       // dmax in [2^(E-1), 2^E)
+        else E = -117 - __clz(bits & 0x7fffff);           // subnormal maximum
     }
     const int sh = 62 - L - E;
     const double scale = __longlong_as_double((long long)(sh + 1023) << 52);
 
-    // Each thread owns a contiguous segment of the block's points for the scan.
-    const int64_t seg = (cnt + kThreads - 1) / kThreads;
-    const int64_t s0 = min(cnt, (int64_t)tid * seg), s1 = min(cnt, s0 + seg);
-
     for (int t = 1; t < a.Ks; ++t) {
-        const uint64_t r = rng_draw(a.seed, (uint64_t)m, (uint64_t)t) >> 11;
+        const int cur = t & 1;
+        float *D2c = d2m + (size_t)cur * plane;
+        const float *D2p = d2m + (size_t)(cur ^ 1) * plane;
+        // fold seed t-1 into this block's D2 (round 1 uses round 0's values) and sum the weights
         uint64_t part = 0;
-        for (int64_t i = s0; i < s1; ++i) part += weight(s_d2[i], scale, any);
-        const uint64_t incl = block_scan_u64(part, s_warp);
-        if (tid == kThreads - 1) a.bsum[(size_t)m * a.bps + b] = incl;
+        for (int64_t i = tid; i < cnt; i += kThreads) {
+            float d;
+            if (t == 1) {
+                d = D2c[i0 + i];
+            } else {
+                d = d2_f32_exact(Pm + (i0 + i) * a.ld, s_center, ds);
+                d = fminf(d, D2p[i0 + i]);
+                D2c[i0 + i] = d;
+            }
+            part += weight(d, scale, any);
+        }
+        part = warp_sum(part);
+        if ((tid & 31) == 0) s_warp[tid >> 5] = part;
+        __syncthreads();
+        if (tid == 0) {
+            uint64_t tot = 0;
+            for (int w = 0; w < kWarps; ++w) tot += s_warp[w];
+            bs[(size_t)cur * bplane + b] = tot;
+        }
         if (!block_group_barrier(bar, a.bps, a.err)) return;
 
-        if (tid == 0) {
+        // every block: owner block and threshold
+        const uint64_t r = rng_draw(a.seed, (uint64_t)m, (uint64_t)t) >> 11;
+        if (tid < 32) {
+            const volatile unsigned long long *bv = bs + (size_t)cur * bplane;
             uint64_t W = 0;
-            for (int q = 0; q < a.bps; ++q) W += *(volatile unsigned long long *)(a.bsum + (size_t)m * a.bps + q);
-            long long p = -1;
+            for (int q = tid; q < a.bps; q += 32) W += bv[q];
+            W = warp_sum(W);
             int owner = -1;
             uint64_t thr_local = 0;
+            long long p = -1;
             if (W == 0) {
                 p = scale_index(r, (uint64_t)a.n);
             } else {
                 const uint64_t thr = (__umul64hi(r, W) << 11) | ((r * W) >> 53);
                 uint64_t acc = 0;
-                for (int q = 0; q < a.bps; ++q) {
-                    uint64_t v = *(volatile unsigned long long *)(a.bsum + (size_t)m * a.bps + q);
-                    if (acc + v > thr) { owner = q; thr_local = thr - acc; break; }
-                    acc += v;
+                for (int base = 0; base < a.bps && owner < 0; base += 32) {
+                    const uint64_t v = (base + tid < a.bps) ? bv[base + tid] : 0ull;
+                    const uint64_t incl = warp_incl_scan(v) + acc;
+                    const unsigned hit = __ballot_sync(0xffffffffu, incl > thr && v > 0);
+                    if (hit) {
+                        const int l = __ffs(hit) - 1;
+                        owner = base + l;
+                        thr_local = thr - (__shfl_sync(0xffffffffu, incl, l) - __shfl_sync(0xffffffffu, v, l));
+                    }
+                    acc = __shfl_sync(0xffffffffu, incl, 31);
                 }
             }
-            s_pick = p;
-            s_warp[0] = thr_local;
-            s_fmax[0] = __int_as_float(owner);
+            if (tid == 0) {
+                s_pick = p;
+                s_owner = owner;
+                s_thr = thr_local;
+            }
         }
         __syncthreads();
-        const int owner = __float_as_int(s_fmax[0]);
-        const uint64_t thr_local = s_warp[0];
-        __syncthreads();
-        if (owner == b) {
-            // inclusive prefix (exclusive of this thread's segment) then a sequential walk
-            const uint64_t excl = incl - part;
+        if (s_pick < 0) {
+            // walk the owner's D2 values in order to the threshold
+            const int owner = s_owner;
+            const uint64_t thr_local = s_thr;
+            const int64_t o0 = (int64_t)owner * a.nb;
+            const int64_t ocnt = min(a.n, o0 + a.nb) - o0;
+            const int64_t seg = (ocnt + kThreads - 1) / kThreads;
+            const int64_t s0 = min(ocnt, (int64_t)tid * seg), s1 = min(ocnt, s0 + seg);
+            uint64_t w = 0;
+            for (int64_t i = s0; i < s1; ++i) w += weight(D2c[o0 + i], scale, any);
+            const uint64_t incl = block_scan_u64(w, s_warp);
+            const uint64_t excl = incl - w;
             if (excl <= thr_local && thr_local < incl) {
                 uint64_t acc = excl;
                 for (int64_t i = s0; i < s1; ++i) {
-                    acc += weight(s_d2[i], scale, any);
-                    if (acc > thr_local) { a.sel[m] = i0 + i; break; }
+                    acc += weight(D2c[o0 + i], scale, any);
+                    if (acc > thr_local) { s_pick = o0 + i; break; }
                 }
             }
+            __syncthreads();
         }
-        if (!block_group_barrier(bar, a.bps, a.err)) return;
-        pick = (s_pick >= 0) ? s_pick : *(volatile long long *)(a.sel + m);
+        pick = s_pick;
         for (int j = tid; j < ds; j += kThreads) {
-            float v = Pm[pick * a.ld + j];
+            const float v = Pm[pick * a.ld + j];
             s_center[j] = v;
             if (b == 0) Cm[(size_t)t * ds + j] = v;
         }
         __syncthreads();
-        for (int64_t i = tid; i < cnt; i += kThreads) {
-            float d = d2_f32_exact(Pm + (i0 + i) * a.ld, s_center, ds);
-            if (d < s_d2[i]) s_d2[i] = d;
-        }
-        // The update is strided over threads, the next round's sums walk contiguous segments.
-        __syncthreads();
-        // s_pick is rewritten by thread 0 only after the next barrier, which every thread passes first.
     }
 }
 
@@ -234,33 +302,15 @@ int launch_kmeanspp(const float *P, int64_t ld, int64_t n, int ds, int M, int Ks
     int dev = 0, sms = 0;
     PQ_TRY_CUDA(cudaGetDevice(&dev));
     PQ_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    int smem_cap = 0;
-    PQ_TRY_CUDA(cudaDeviceGetAttribute(&smem_cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    cudaFuncAttributes fa;
-    PQ_TRY_CUDA(cudaFuncGetAttributes(&fa, kmeanspp_kernel));
-    smem_cap -= (int)fa.sharedSizeBytes;  // the opt-in limit covers static + dynamic shared memory
-
-    // Blocks per subspace: enough that each block's D2 slice fits shared
-    // memory, at most one point in 64 per block, and the whole grid co-resident.
-    PQ_TRY_CUDA(cudaFuncSetAttribute(kmeanspp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap));
-    const int64_t bps_min = std::max<int64_t>(1, ((int64_t)n * 4 + smem_cap - 1) / smem_cap);
-    int64_t want = std::max<int64_t>(bps_min, std::min<int64_t>((n + 63) / 64, 4096));
-    int64_t nb = 0;
-    size_t smem = 0;
-    bool ok = false;
-    for (int iter = 0; iter < 16 && want >= bps_min; ++iter) {
-        nb = (n + want - 1) / want;
-        smem = (size_t)nb * sizeof(float);
-        int per_sm = 0;
-        PQ_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kmeanspp_kernel, kThreads, smem));
-        const int64_t capacity = (int64_t)per_sm * sms;
-        if (want * M <= capacity) { ok = true; break; }
-        want = std::min<int64_t>(want - 1, capacity / M);
-    }
-    if (!ok)
-        return fail(PQ_ENOTSUP, "k-means++ seeding: %lld points x %d subspaces do not fit one cooperative wave",
-                    (long long)n, M);
+    int per_sm = 0;
+    PQ_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kmeanspp_kernel, kThreads, 0));
+    const int64_t capacity = (int64_t)per_sm * sms;
+    // About one block per SM over all subspaces, at least 256 points per block.
+    const int64_t want = std::max<int64_t>(1, std::min<int64_t>(sms / std::max(1, M), (n + 255) / 256));
+    if (want * M > capacity)
+        return fail(PQ_ENOTSUP, "k-means++ seeding: %d subspaces do not fit one cooperative wave", M);
     const int bps = (int)want;
+    const int64_t nb = (n + bps - 1) / bps;
 
     KppArgs a;
     a.P = P;
@@ -272,9 +322,9 @@ int launch_kmeanspp(const float *P, int64_t ld, int64_t n, int ds, int M, int Ks
     a.seed = seed;
     a.C = C;
     a.bars = ws.get<unsigned>(2 * (size_t)M, true);
-    a.bsum = ws.get<unsigned long long>((size_t)M * bps, true);
+    a.bsum = ws.get<unsigned long long>(2 * (size_t)M * bps, true);
+    a.d2 = ws.get<float>(2 * (size_t)M * n);
     a.dmax_bits = ws.get<unsigned>((size_t)M, true);
-    a.sel = ws.get<long long>((size_t)M, true);
     if (ws.status) return ws.status;
     a.err = err;
     a.bps = bps;
@@ -282,7 +332,7 @@ int launch_kmeanspp(const float *P, int64_t ld, int64_t n, int ds, int M, int Ks
     void *args[] = {&a};
     dim3 grid(bps, M);
     ProfScope ps("kmeanspp", s);
-    PQ_TRY_CUDA(cudaLaunchCooperativeKernel((void *)kmeanspp_kernel, grid, dim3(kThreads), args, smem, s));
+    PQ_TRY_CUDA(cudaLaunchCooperativeKernel((void *)kmeanspp_kernel, grid, dim3(kThreads), args, 0, s));
     count_launch();
     return PQ_OK;
 }
