@@ -144,6 +144,29 @@ int pq_decode_rmse(const uint8_t *codes, const float *codebooks, const float *X,
 int pq_lloyd_noalloc(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, int32_t iters,
                      const float *init_codebooks, float *codebooks, void *stream);
 
+/*
+ * pq_fit_chunked -- the paper's divide-and-conquer PQ (Sec. 3, "Methodology").
+ *   X              [N][D] float32 rows, 16-byte aligned.
+ *   chunk_offsets  HOST array [n_chunks + 1]: chunk c is rows
+ *                  [chunk_offsets[c], chunk_offsets[c+1]); chunk_offsets[0] = 0,
+ *                  every chunk has at least Ks rows, N = chunk_offsets[n_chunks],
+ *                  1 <= n_chunks <= 512.
+ *   codebooks      [M][Ks][Ds] output: the global model.
+ *   codes          [N][M] output: every row encoded with the global model.
+ *   rmse           host double or NULL; non-NULL makes the call synchronize and
+ *                  receive sqrt(sum (x - xhat)^2 / (N*D)) of the global model.
+ * Chunk c gets a PQ fit (k-means++ seeding from draw c of the chunk stream of
+ * `seed`, then `iters` Lloyd iterations); the codewords of all chunks form the
+ * centroid dataset (row c*Ks + k = concatenation over m of codeword k of
+ * subspace m of chunk c), on which the global PQ is fitted with `seed`.  All
+ * chunks are fitted together: one launch seeds every (chunk, subspace) pair and
+ * each Lloyd iteration is one launch over all chunks.  With rmse == NULL the
+ * call never synchronizes and can be captured in a CUDA graph.
+ */
+int pq_fit_chunked(const float *X, const int64_t *chunk_offsets, int32_t n_chunks, int32_t D, int32_t M, int32_t Ks,
+                   int32_t iters, uint64_t seed, int32_t prec, float *codebooks, uint8_t *codes, double *rmse,
+                   void *stream);
+
 /* Opaque inverted-file index, allocated by ivf_build and owned by the library until ivf_free. */
 typedef struct ivf_index ivf_index;
 

@@ -163,21 +163,11 @@ int status_from_device(int *err_word, cudaStream_t s, int *host_err)
     return PQ_OK;
 }
 
-// Seeding rows: all rows, or 100*Ks drawn with replacement (gathered).
+// Seeding rows: all rows, or 100*Ks drawn with replacement.
 int seed_codebooks(const float *X, int64_t N, int D, int M, int Ks, uint64_t seed, float *C, Scratch &ws, int *err,
-                   cudaStream_t s)
+                   cudaStream_t s, const char *tag = "kmeanspp")
 {
-    const int64_t cap = 100LL * Ks;
-    const float *P = X;
-    int64_t n = N;
-    if (N > cap) {
-        float *G = ws.get<float>((size_t)cap * D);
-        if (ws.status) return ws.status;
-        PQ_TRY(launch_gather_subsample(X, N, D, cap, seed, G, s));
-        P = G;
-        n = cap;
-    }
-    return launch_kmeanspp(P, D, n, D / M, M, Ks, seed, C, ws, err, s);
+    return launch_kmeanspp(X, N, D, M, Ks, seed, C, ws, err, s, tag);
 }
 
 // Lloyd iterations over PQ codebooks C (in place).
@@ -344,6 +334,32 @@ int pq_decode_rmse(const uint8_t *codes, const float *codebooks, const float *X,
     return ws.status;
 }
 
+int pq_fit_chunked(const float *X, const int64_t *chunk_offsets, int32_t n_chunks, int32_t D, int32_t M, int32_t Ks,
+                   int32_t iters, uint64_t seed, int32_t prec, float *codebooks, uint8_t *codes, double *rmse,
+                   void *stream)
+{
+    g_msg[0] = 0;
+    if (!X || !chunk_offsets || !codebooks || !codes) return fail(PQ_EINVAL, "null pointer");
+    if (n_chunks < 1 || n_chunks > kMaxSeedChunks) return fail(PQ_EINVAL, "n_chunks=%d must be in [1, %d]", n_chunks,
+                                                               kMaxSeedChunks);
+    if (chunk_offsets[0] != 0) return fail(PQ_EINVAL, "chunk_offsets[0] must be 0");
+    for (int c = 0; c < n_chunks; ++c)
+        if (chunk_offsets[c + 1] - chunk_offsets[c] < Ks)
+            return fail(PQ_EINVAL, "chunk %d has %lld rows, fewer than Ks=%d", c,
+                        (long long)(chunk_offsets[c + 1] - chunk_offsets[c]), Ks);
+    const int64_t N = chunk_offsets[n_chunks];
+    PQ_TRY(check_pq_shape(N, D, M, Ks, true));
+    PQ_TRY(check_prec(prec));
+    if (!aligned16(X)) return fail(PQ_EINVAL, "X must be 16-byte aligned");
+    if (iters < 0 || iters > PQ_STATS_MAX_ITERS) return fail(PQ_EINVAL, "iters=%d must be in [0, %d]", iters,
+                                                             PQ_STATS_MAX_ITERS);
+    if (prec == PQ_PREC_BF16 && !tc_pass_supported(D, M, Ks))
+        return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and M a multiple of 4");
+    if ((int64_t)n_chunks * Ks < Ks) return fail(PQ_EINVAL, "empty centroid dataset");
+    return run_pq_fit_chunked(X, chunk_offsets, n_chunks, D, M, Ks, iters, seed, prec, codebooks, codes, rmse,
+                              static_cast<cudaStream_t>(stream));
+}
+
 int ivf_build(const float *X, const uint8_t *codes, int64_t N, int32_t D, int32_t M, int32_t nlist, int32_t iters,
               uint64_t seed, int32_t prec, ivf_index **out, void *stream)
 {
@@ -388,15 +404,15 @@ int ivf_build(const float *X, const uint8_t *codes, int64_t N, int32_t D, int32_
         int32_t *lst = ws.get<int32_t>((size_t)N);
         if (ws.status) return cleanup(ws.status);
         CoarseBound b{idx->half_norm, idx->maxes};
-        st = seed_codebooks(X, N, D, 1, nlist, seed, idx->coarse, ws, err, s);
+        st = seed_codebooks(X, N, D, 1, nlist, seed, idx->coarse, ws, err, s, "kmeanspp_coarse");
         for (int t = 0; st == PQ_OK && t < iters; ++t) {
             st = launch_coarse_norms(idx->coarse, nlist, D, b, s);
-            if (!st) st = coarse_assign(X, N, D, idx->coarse, nlist, b, lst, ws, nullptr, s);
+            if (!st) st = coarse_assign(X, N, D, idx->coarse, nlist, b, lst, ws, prec, s);
             if (!st) st = bucket_rows(lst, N, nlist, nullptr, M, idx->offsets, idx->ids, nullptr, ws, s);
             if (!st) st = launch_list_mean(X, D, idx->offsets, idx->ids, nlist, idx->coarse, s);
         }
         if (!st) st = launch_coarse_norms(idx->coarse, nlist, D, b, s);
-        if (!st) st = coarse_assign(X, N, D, idx->coarse, nlist, b, lst, ws, nullptr, s);
+        if (!st) st = coarse_assign(X, N, D, idx->coarse, nlist, b, lst, ws, prec, s);
         if (!st) st = bucket_rows(lst, N, nlist, codes, M, idx->offsets, idx->ids, idx->codes, ws, s);
         if (!st) st = ws.status;
     }

@@ -221,6 +221,82 @@ __global__ void coarse_recheck_kernel(const float *__restrict__ X, int D, const 
     }
 }
 
+// One warp per queued row whose candidates are confined to the 32-centroid chunks of
+// its mask (as found by the tensor-core kernel): FP32 direct differences over those
+// chunks, then FP64 among the FP32 near-ties.  A zero mask means every chunk.
+__global__ void coarse_recheck_masked_kernel(const float *__restrict__ X, int D, const float *__restrict__ C,
+                                             int nlist, const int64_t *__restrict__ queue,
+                                             const uint32_t *__restrict__ qmask,
+                                             const unsigned long long *queue_len, int32_t *__restrict__ list_of_row)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned long long total = *queue_len;
+    const int nchunks = (nlist + 31) / 32;
+    // relative error of an FP32 direct-difference distance over D dimensions, with margin
+    const float rel = 2.5f * (2.0f * 5.9604645e-8f + gamma_f32(D));
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < (int64_t)total; w += nw) {
+        const int64_t row = queue[w];
+        const uint32_t m = qmask[w];
+        const float *x = X + row * D;
+        float d1 = FLT_MAX, d2 = FLT_MAX;
+        int i1 = 0x7fffffff;
+        for (int c = 0; c < nchunks; ++c) {
+            if (m != 0u && c < 32 && !((m >> c) & 1u)) continue;
+            const int l = c * 32 + lane;
+            if (l >= nlist) continue;
+            const float *cl = C + (size_t)l * D;
+            float d = 0.0f;
+            for (int j = 0; j < D; ++j) {
+                const float t = x[j] - cl[j];
+                d = fmaf(t, t, d);
+            }
+            if (d < d1) { d2 = d1; d1 = d; i1 = l; }
+            else if (d < d2) { d2 = d; }
+        }
+        // warp top-2
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float od1 = __shfl_xor_sync(0xffffffffu, d1, o);
+            const float od2 = __shfl_xor_sync(0xffffffffu, d2, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, i1, o);
+            const bool take = od1 < d1 || (od1 == d1 && oi < i1);
+            const float rest = take ? fminf(d1, od2) : fminf(d2, od1);
+            if (take) { d1 = od1; i1 = oi; }
+            d2 = rest;
+        }
+        const float margin = rel * d2 + 1e-30f;
+        int res = i1;
+        if (!(d2 - d1 > margin)) {
+            double best = DBL_MAX;
+            int bl = 0x7fffffff;
+            for (int c = 0; c < nchunks; ++c) {
+                if (m != 0u && c < 32 && !((m >> c) & 1u)) continue;
+                const int l = c * 32 + lane;
+                if (l >= nlist) continue;
+                const float *cl = C + (size_t)l * D;
+                float d = 0.0f;
+                for (int j = 0; j < D; ++j) {
+                    const float t = x[j] - cl[j];
+                    d = fmaf(t, t, d);
+                }
+                if (d <= d1 + margin) {
+                    const double e = d2_fp64(x, cl, D);
+                    if (e < best || (e == best && l < bl)) { best = e; bl = l; }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+                if (ob < best || (ob == best && ol < bl)) { best = ob; bl = ol; }
+            }
+            res = bl;
+        }
+        if (lane == 0) list_of_row[row] = res;
+    }
+}
+
 __global__ void bucket_hist_kernel(const int32_t *__restrict__ lst, int64_t N, int nlist, int *__restrict__ tile_cnt)
 {
     extern __shared__ int s_hist[];
@@ -333,7 +409,16 @@ __global__ void list_mean_kernel(const float *__restrict__ X, int D, const int64
     if (e == b) return;  // empty list keeps its centroid
     for (int j = threadIdx.x; j < D; j += blockDim.x) {
         double s = 0.0;
-        for (int64_t p = b; p < e; ++p) s = __dadd_rn(s, (double)X[ids[p] * D + j]);
+        int64_t p = b;
+        // loads issued eight rows ahead; the additions stay in ascending row order
+        for (; p + 8 <= e; p += 8) {
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = X[ids[p + q] * D + j];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) s = __dadd_rn(s, (double)v[q]);
+        }
+        for (; p < e; ++p) s = __dadd_rn(s, (double)X[ids[p] * D + j]);
         C[(size_t)l * D + j] = __double2float_rn(__ddiv_rn(s, (double)(e - b)));
     }
 }
@@ -353,13 +438,22 @@ int launch_coarse_norms(const float *C, int nlist, int D, CoarseBound &b, cudaSt
 }
 
 int coarse_assign(const float *X, int64_t N, int D, const float *C, int nlist, const CoarseBound &b,
-                  int32_t *list_of_row, Scratch &ws, unsigned long long *rechecks, cudaStream_t s)
+                  int32_t *list_of_row, Scratch &ws, int prec, cudaStream_t s)
 {
     int64_t *queue = ws.get<int64_t>((size_t)N);
     unsigned long long *qlen = ws.get<unsigned long long>(1, true);
     if (ws.status) return ws.status;
-    const int64_t blocks = (N + BM - 1) / BM;
-    {
+    if (prec == PQ_PREC_BF16 && coarse_tc_supported(D, nlist)) {
+        uint32_t *qmask = ws.get<uint32_t>((size_t)N);
+        if (ws.status) return ws.status;
+        PQ_TRY(launch_coarse_tc(X, N, D, C, nlist, list_of_row, queue, qmask, qlen, ws, s));
+        ProfScope ps("coarse_recheck", s);
+        coarse_recheck_masked_kernel<<<152 * 4, 256, 0, s>>>(X, D, C, nlist, queue, qmask, qlen, list_of_row);
+        count_launch();
+        PQ_TRY_CUDA(cudaGetLastError());
+        return PQ_OK;
+    } else {
+        const int64_t blocks = (N + BM - 1) / BM;
         ProfScope ps("coarse_assign", s);
         coarse_scores_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(X, N, D, C, nlist, b.half_norm, b.maxes,
                                                                    list_of_row, queue, qlen, nullptr);

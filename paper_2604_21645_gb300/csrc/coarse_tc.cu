@@ -1,0 +1,534 @@
+// coarse_tc.cu -- nearest coarse centroid of every row on the tcgen05 tensor
+// cores (the coarse quantizer of the inverted index, Sec. 2.2 / Sec. 3.1).
+//
+// Scores S_l = x'.c'_l - ||c'_l||^2/2 with x' = x - mu, c' = c - mu (mu = mean
+// of the centroids) are accumulated in TMEM over K = 3D + 16 bf16 lanes, the
+// three-term split of the contraction
+//     x'.c' ~ xh.ch + xl.ch + xh.cl        (x' = xh + xl, c' = ch + cl)
+// plus the folded half norm (-nh - nl against a constant 1).  The error of S
+// is below C1 ||x'|| max||c'|| + C2 max n' with C1 = 1.5 (3.1 u^2 + (3D+2) 2^-24),
+// C2 = 1.5 (u^2 + (3D+2) 2^-24), u = 2^-8: bf16 split residuals plus a bound
+// on the FP32 accumulation that is linear in the number of products.
+//
+// The epilogue keeps, per row over all centroid blocks, the chunk maxima and
+// the best chunk of 32 scores, and accepts the argmax when no other score is
+// within twice the bound; every other row goes to the FP64 re-check queue
+// (coarse.cu), so the list of every row is exact.
+//
+// Pipeline, one CTA (192 threads) per SM, persistent over 128-row tiles:
+// lane 0 of warp 0 loads the X tile by TMA (128B-swizzled 32-column boxes),
+// lane 1 of warp 0 streams the pre-tiled B operand (8 KB tiles, bulk copies)
+// through a 4-slot ring, lane 0 of warp 1 issues M=128 N=256 K=16 MMAs into two
+// TMEM accumulators (256 centroids each), warps 2-5 build the A operand and run
+// the epilogue.  Every wait is bounded.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cfloat>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace pqgb {
+namespace {
+
+constexpr int TM = 128;
+constexpr int NBLK = 256;            // centroids per MMA / TMEM accumulator
+constexpr int DMAX = 128;
+constexpr int KDMAX = DMAX / 16;     // K steps of one term
+constexpr int kThreads = 64 + 128;
+constexpr int A_TILE = TM * 16 * 2;  // 4 KB
+constexpr int B_TILE = NBLK * 16 * 2;  // 8 KB
+constexpr int RING = 4;
+constexpr int XBOX = TM * 32 * 4;    // 16 KB, one 32-column box
+constexpr int OFF_X = 0;                                  // 4 boxes
+constexpr int OFF_A = OFF_X + (DMAX / 32) * XBOX;        // (2*KD + 1) tiles
+constexpr int OFF_RING = OFF_A + (2 * KDMAX + 1) * A_TILE;
+constexpr int OFF_MISC = OFF_RING + RING * B_TILE;
+constexpr int OFF_CMX = OFF_MISC + 1024;                  // [32 chunks][128 rows] chunk maxima
+constexpr int SMEM_BYTES = OFF_CMX + 32 * TM * 4 + 1024;
+
+// mbarrier slots
+constexpr int MB_XFULL = 0, MB_XEMPTY = 1, MB_AREADY = 2, MB_AFREE = 3, MB_MMA = 4 /*2*/, MB_TFREE = 6 /*2*/,
+              MB_RFULL = 8 /*RING*/, MB_REMPTY = 8 + RING /*RING*/, MB_COUNT = 8 + 2 * RING;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t c)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(c) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int *err)
+{
+    for (unsigned it = 0;; ++it) {
+        if (mbar_try(a, parity)) return true;
+        if (it > kSpinLimit) {
+            atomicCAS(err, 0, PQ_ETIMEOUT);
+            return false;
+        }
+        if ((it & 255) == 255 && *(volatile int *)err != 0) return false;
+    }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(map), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
+{
+    uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)(128 >> 4) << 16;
+    d |= (uint64_t)(256 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+__host__ __device__ __forceinline__ uint32_t core_off(int r, int k)
+{
+    return (r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NBLK >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t da, uint64_t db, uint32_t acc)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(da), "l"(db), "r"(kIdesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+#define TC_LD32(base, v)                                                                                            \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16," \
+                 "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                             \
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]),   \
+                   "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]),         \
+                   "=f"(v[15]), "=f"(v[16]), "=f"(v[17]), "=f"(v[18]), "=f"(v[19]), "=f"(v[20]), "=f"(v[21]),       \
+                   "=f"(v[22]), "=f"(v[23]), "=f"(v[24]), "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]),       \
+                   "=f"(v[29]), "=f"(v[30]), "=f"(v[31])                                                            \
+                 : "r"(base))
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+__device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// ---- preparation: centring mean, bounds, tiled B operand -------------------
+// Bp layout: [blk][tile][256 rows][16 bf16] core-matrix tiles; tile 2k = ch of K step k,
+// 2k+1 = cl of K step k, 2*KD = the half-norm tile.
+__global__ void coarse_mu_kernel(const float *C, int nlist, int D, float *mu)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= D) return;
+    float s = 0.0f;
+    for (int l = 0; l < nlist; ++l) s += C[(size_t)l * D + j];
+    mu[j] = s / (float)nlist;
+}
+
+__global__ void coarse_prep_kernel(const float *C, int nlist, int nlist_pad, int D, const float *mu,
+                                   unsigned char *Bp, unsigned *maxbits)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nlist_pad) return;
+    const int KD = D / 16, T = 2 * KD + 1;
+    const int blk = l / NBLK, row = l % NBLK;
+    unsigned char *base = Bp + (size_t)blk * T * B_TILE;
+    float nc = 0.0f;
+    for (int k = 0; k < KD; ++k) {
+        float hi[16], lo[16];
+        for (int q = 0; q < 16; ++q) {
+            const float c = l < nlist ? C[(size_t)l * D + 16 * k + q] - mu[16 * k + q] : 0.0f;
+            nc = fmaf(c, c, nc);
+            hi[q] = bf16_round(c);
+            lo[q] = c - hi[q];
+        }
+        unsigned char *th = base + (size_t)(2 * k) * B_TILE, *tl = base + (size_t)(2 * k + 1) * B_TILE;
+        *reinterpret_cast<uint4 *>(th + core_off(row, 0)) =
+            make_uint4(pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]), pack_bf16(hi[4], hi[5]), pack_bf16(hi[6], hi[7]));
+        *reinterpret_cast<uint4 *>(th + core_off(row, 8)) = make_uint4(pack_bf16(hi[8], hi[9]), pack_bf16(hi[10], hi[11]),
+                                                                       pack_bf16(hi[12], hi[13]), pack_bf16(hi[14], hi[15]));
+        *reinterpret_cast<uint4 *>(tl + core_off(row, 0)) =
+            make_uint4(pack_bf16(lo[0], lo[1]), pack_bf16(lo[2], lo[3]), pack_bf16(lo[4], lo[5]), pack_bf16(lo[6], lo[7]));
+        *reinterpret_cast<uint4 *>(tl + core_off(row, 8)) = make_uint4(pack_bf16(lo[8], lo[9]), pack_bf16(lo[10], lo[11]),
+                                                                       pack_bf16(lo[12], lo[13]), pack_bf16(lo[14], lo[15]));
+    }
+    const float n = 0.5f * nc;
+    float nh, nl;
+    if (l < nlist) {
+        nh = bf16_round(n);
+        nl = n - nh;
+        atomicMax(maxbits + 0, __float_as_uint(n));
+        atomicMax(maxbits + 1, __float_as_uint(sqrtf(nc)));
+    } else {
+        nh = 3.0e38f;
+        nl = 0.0f;
+    }
+    unsigned char *tn = base + (size_t)(2 * KD) * B_TILE;
+    *reinterpret_cast<uint4 *>(tn + core_off(row, 0)) = make_uint4(pack_bf16(-nh, -nl), 0u, 0u, 0u);
+    *reinterpret_cast<uint4 *>(tn + core_off(row, 8)) = make_uint4(0u, 0u, 0u, 0u);
+}
+
+struct CoarseTcArgs {
+    int64_t N;
+    int D, nlist_pad, tiles;
+    const unsigned char *Bp;
+    const float *mu;
+    const unsigned *maxbits;
+    int32_t *list_of_row;
+    int64_t *queue;
+    uint32_t *qmask;
+    unsigned long long *qlen;
+    int *err;
+};
+
+// NBT > 0: at most NBT centroid blocks (NBT * 8 chunks of 32 <= 32); the chunk maxima are kept
+// and an uncertain row is queued with the mask of chunks that can hold its nearest centroid.
+template <int NBT>
+__global__ void __launch_bounds__(kThreads, 1) coarse_tc_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                 const CoarseTcArgs a)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int D = a.D, KD = D / 16, T = 2 * KD + 1, NB = a.nlist_pad / NBLK, NBOX = D / 32;
+    uint64_t *mb = reinterpret_cast<uint64_t *>(sm + OFF_MISC);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + OFF_MISC + 8 * MB_COUNT);
+    float *smu = reinterpret_cast<float *>(sm + OFF_MISC + 256);
+    unsigned char *xs = sm + OFF_X;
+    unsigned char *aop = sm + OFF_A;
+    unsigned char *ring = sm + OFF_RING;
+
+    for (int j = tid; j < D; j += kThreads) smu[j] = a.mu[j];
+    if (tid == 0) {
+        for (int i = 0; i < MB_COUNT; ++i) {
+            uint32_t c = 1;
+            if (i == MB_XEMPTY || i == MB_AREADY || i == MB_TFREE || i == MB_TFREE + 1) c = 4;
+            mbar_init(smem_u32(mb + i), c);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tslot)) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = *tslot;
+    const int n_my = (a.tiles > (int)blockIdx.x) ? (a.tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // X tiles: NBOX TMA boxes of 128 rows x 32 floats
+            int issued = 0;
+            for (int i = 0; i < n_my; ++i) {
+                if (i >= 1 && !mbar_wait(smem_u32(mb + MB_XEMPTY), (i - 1) & 1, a.err)) break;
+                mbar_expect_tx(smem_u32(mb + MB_XFULL), NBOX * XBOX);
+                const int y = ((int)blockIdx.x + i * (int)gridDim.x) * TM;
+                for (int bx = 0; bx < NBOX; ++bx)
+                    tma_load_2d(smem_u32(xs + bx * XBOX), &tmap, bx * 32, y, smem_u32(mb + MB_XFULL));
+                ++issued;
+            }
+            if (issued) mbar_wait(smem_u32(mb + MB_XFULL), (issued - 1) & 1, a.err);
+        } else if (lane == 1) {
+            // B tiles in MMA order through the ring
+            int z = 0;
+            bool ok = true;
+            for (int i = 0; i < n_my && ok; ++i)
+                for (int b = 0; b < NB && ok; ++b)
+                    for (int t = 0; t < T; ++t, ++z) {
+                        const int slot = z % RING, use = z / RING;
+                        if (use >= 1 && !mbar_wait(smem_u32(mb + MB_REMPTY + slot), (use - 1) & 1, a.err)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_expect_tx(smem_u32(mb + MB_RFULL + slot), B_TILE);
+                        bulk_load(smem_u32(ring + slot * B_TILE), a.Bp + ((size_t)b * T + t) * B_TILE, B_TILE,
+                                  smem_u32(mb + MB_RFULL + slot));
+                    }
+            for (int q = (z > RING ? z - RING : 0); q < z; ++q)
+                mbar_wait(smem_u32(mb + MB_RFULL + q % RING), (q / RING) & 1, a.err);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int z = 0;
+            bool ok = true;
+            for (int i = 0; i < n_my && ok; ++i) {
+                if (!mbar_wait(smem_u32(mb + MB_AREADY), i & 1, a.err)) break;
+                tc_after_sync();
+                for (int b = 0; b < NB && ok; ++b) {
+                    const int v = i * NB + b, buf = v & 1, u = v >> 1;
+                    if (u >= 1 && !mbar_wait(smem_u32(mb + MB_TFREE + buf), (u - 1) & 1, a.err)) { ok = false; break; }
+                    tc_after_sync();
+                    const uint32_t d = tmem + (uint32_t)(buf * NBLK);
+                    for (int t = 0; t < T; ++t, ++z) {
+                        const int slot = z % RING, use = z / RING;
+                        if (!mbar_wait(smem_u32(mb + MB_RFULL + slot), use & 1, a.err)) { ok = false; break; }
+                        tc_after_sync();
+                        const uint64_t db = smem_desc(smem_u32(ring + slot * B_TILE));
+                        if (t == 2 * KD) {
+                            mma_bf16(d, smem_desc(smem_u32(aop + 2 * KD * A_TILE)), db, 1u);  // half norm
+                        } else if ((t & 1) == 0) {
+                            const int k = t >> 1;  // ch: against xh and xl
+                            mma_bf16(d, smem_desc(smem_u32(aop + k * A_TILE)), db, t == 0 ? 0u : 1u);
+                            mma_bf16(d, smem_desc(smem_u32(aop + (KD + k) * A_TILE)), db, 1u);
+                        } else {
+                            const int k = t >> 1;  // cl: against xh
+                            mma_bf16(d, smem_desc(smem_u32(aop + k * A_TILE)), db, 1u);
+                        }
+                        mma_commit(smem_u32(mb + MB_REMPTY + slot));
+                    }
+                    if (!ok) break;
+                    mma_commit(smem_u32(mb + MB_MMA + buf));
+                }
+                if (!ok) break;
+                mma_commit(smem_u32(mb + MB_AFREE));
+            }
+        }
+    } else {
+        const int q = warp & 3;
+        const int r = q * 32 + lane;
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+        const float nmax = __uint_as_float(a.maxbits[0]) * (1.0f + 1e-5f);
+        const float cmax = __uint_as_float(a.maxbits[1]) * (1.0f + 1e-5f);
+        const float u2 = 1.52587890625e-05f;  // 2^-16
+        const float acc_b = (float)(3 * D + 2) * 5.9604645e-8f;
+        const float C1 = 1.5f * (3.1f * u2 + acc_b), C2 = 1.5f * (u2 + acc_b);
+        for (int i = 0; i < n_my; ++i) {
+            const int64_t row = (int64_t)((int)blockIdx.x + i * (int)gridDim.x) * TM + r;
+            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(mb + MB_XFULL), i & 1, a.err))) break;
+            if (i >= 1 && !__all_sync(0xffffffffu, mbar_wait(smem_u32(mb + MB_AFREE), (i - 1) & 1, a.err))) break;
+            // A operand: xh tiles [0, KD), xl tiles [KD, 2KD), constant tile 2KD
+            float xx = 0.0f;
+            for (int k = 0; k < KD; ++k) {
+                const float *box = reinterpret_cast<const float *>(xs + (k >> 1) * XBOX);
+                float hi[16], lo[16];
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    const int chunk = ((k & 1) << 2) + c4;
+                    const float4 v = *reinterpret_cast<const float4 *>(box + r * 32 + ((chunk ^ (r & 7)) << 2));
+                    const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        const float xc = e[w] - smu[16 * k + 4 * c4 + w];
+                        xx = fmaf(xc, xc, xx);
+                        hi[4 * c4 + w] = bf16_round(xc);
+                        lo[4 * c4 + w] = xc - hi[4 * c4 + w];
+                    }
+                }
+                unsigned char *th = aop + k * A_TILE, *tlo = aop + (KD + k) * A_TILE;
+                *reinterpret_cast<uint4 *>(th + core_off(r, 0)) = make_uint4(pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]),
+                                                                             pack_bf16(hi[4], hi[5]), pack_bf16(hi[6], hi[7]));
+                *reinterpret_cast<uint4 *>(th + core_off(r, 8)) = make_uint4(pack_bf16(hi[8], hi[9]), pack_bf16(hi[10], hi[11]),
+                                                                             pack_bf16(hi[12], hi[13]), pack_bf16(hi[14], hi[15]));
+                *reinterpret_cast<uint4 *>(tlo + core_off(r, 0)) = make_uint4(pack_bf16(lo[0], lo[1]), pack_bf16(lo[2], lo[3]),
+                                                                              pack_bf16(lo[4], lo[5]), pack_bf16(lo[6], lo[7]));
+                *reinterpret_cast<uint4 *>(tlo + core_off(r, 8)) = make_uint4(pack_bf16(lo[8], lo[9]), pack_bf16(lo[10], lo[11]),
+                                                                              pack_bf16(lo[12], lo[13]), pack_bf16(lo[14], lo[15]));
+            }
+            {
+                unsigned char *tn = aop + 2 * KD * A_TILE;
+                *reinterpret_cast<uint4 *>(tn + core_off(r, 0)) = make_uint4(pack_bf16(1.0f, 1.0f), 0u, 0u, 0u);
+                *reinterpret_cast<uint4 *>(tn + core_off(r, 8)) = make_uint4(0u, 0u, 0u, 0u);
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(smem_u32(mb + MB_AREADY));
+                mbar_arrive(smem_u32(mb + MB_XEMPTY));
+            }
+            const float xn = sqrtf(xx) * (1.0f + 1e-5f);
+            const float tt = xn + cmax;
+            const float win = 2.0f * (C1 * xn * cmax + C2 * nmax + 1e-13f * tt * tt);
+
+            float best = -FLT_MAX, cm2 = -FLT_MAX;
+            int bestj = 0;
+            float sv[32];
+            float *cmx = reinterpret_cast<float *>(sm + OFF_CMX);
+#pragma unroll
+            for (int q2 = 0; q2 < 32; ++q2) sv[q2] = -FLT_MAX;
+            bool ok = true;
+            for (int b = 0; b < NB; ++b) {
+                const int v = i * NB + b, buf = v & 1, u = v >> 1;
+                if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(mb + MB_MMA + buf), u & 1, a.err))) { ok = false; break; }
+                tc_after_sync();
+                const uint32_t tb = tl + (uint32_t)(buf * NBLK);
+#pragma unroll 1
+                for (int cp = 0; cp < NBLK / 64; ++cp) {
+                    float v2[2][32];
+                    TC_LD32(tb + (uint32_t)(cp * 64), v2[0]);
+                    TC_LD32(tb + (uint32_t)(cp * 64 + 32), v2[1]);
+                    tc_wait_ld();
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const float *vv = v2[hh];
+                        float m16[16];
+#pragma unroll
+                        for (int q2 = 0; q2 < 16; ++q2) m16[q2] = fmaxf(vv[2 * q2], vv[2 * q2 + 1]);
+#pragma unroll
+                        for (int q2 = 0; q2 < 8; ++q2) m16[q2] = fmaxf(m16[2 * q2], m16[2 * q2 + 1]);
+#pragma unroll
+                        for (int q2 = 0; q2 < 4; ++q2) m16[q2] = fmaxf(m16[2 * q2], m16[2 * q2 + 1]);
+                        const float cm = fmaxf(fmaxf(m16[0], m16[1]), fmaxf(m16[2], m16[3]));
+                        if (NBT > 0) cmx[((b * NBLK + cp * 64 + hh * 32) / 32) * TM + r] = cm;
+                        const bool better = cm > best;
+                        cm2 = better ? best : fmaxf(cm2, cm);
+                        best = better ? cm : best;
+                        bestj = better ? (b * NBLK + cp * 64 + hh * 32) / 32 : bestj;
+#pragma unroll
+                        for (int q2 = 0; q2 < 32; ++q2) sv[q2] = better ? vv[q2] : sv[q2];
+                    }
+                }
+                tc_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(mb + MB_TFREE + buf));
+            }
+            if (!ok) break;
+            const float theta = best - win;
+            int ib = 0, nin = 0;
+#pragma unroll
+            for (int q2 = 31; q2 >= 0; --q2) {
+                ib = (sv[q2] == best) ? q2 : ib;
+                nin += (sv[q2] >= theta) ? 1 : 0;
+            }
+            if (row < a.N) {
+                if (nin == 1 && cm2 < theta) {
+                    a.list_of_row[row] = bestj * 32 + ib;
+                } else {
+                    uint32_t mask = 0;
+                    if (NBT > 0) {
+#pragma unroll
+                        for (int c = 0; c < NB * 8; ++c) mask |= (cmx[c * TM + r] >= theta ? 1u : 0u) << c;
+                    }
+                    a.list_of_row[row] = -1;
+                    const unsigned long long slot = atomicAdd(a.qlen, 1ull);
+                    a.queue[slot] = row;
+                    a.qmask[slot] = mask;  // 0: every centroid is a candidate
+                }
+            }
+        }
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (warp == 1) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+bool coarse_tc_supported(int D, int nlist) { return D % 32 == 0 && D >= 32 && D <= DMAX && nlist >= 1; }
+
+// Scores on the tensor cores, certified rows written to list_of_row, the others queued
+// (entries of queue, count in *qlen) for the FP64 re-check.
+int launch_coarse_tc(const float *X, int64_t N, int D, const float *C, int nlist, int32_t *list_of_row,
+                     int64_t *queue, uint32_t *qmask, unsigned long long *qlen, Scratch &ws, cudaStream_t s)
+{
+    if (!coarse_tc_supported(D, nlist)) return fail(PQ_ENOTSUP, "tensor-core coarse assignment needs D % 32 == 0, D <= 128");
+    if (N >= (1LL << 31) - TM) return fail(PQ_ENOTSUP, "tensor-core coarse assignment supports N < 2^31");
+    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+    if (!enc) return fail(PQ_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    const int nlist_pad = (nlist + NBLK - 1) / NBLK * NBLK;
+    const int KD = D / 16, T = 2 * KD + 1;
+    float *mu = ws.get<float>((size_t)D);
+    unsigned *maxbits = ws.get<unsigned>(2, true);
+    unsigned char *Bp = ws.get<unsigned char>((size_t)(nlist_pad / NBLK) * T * B_TILE);
+    if (ws.status) return ws.status;
+    int dev = 0, sms = 0;
+    PQ_TRY_CUDA(cudaGetDevice(&dev));
+    PQ_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int *err = device_error_word(dev);
+    if (!err) return fail(PQ_ENOMEM, "device error word");
+    {
+        ProfScope ps("coarse_prep", s);
+        coarse_mu_kernel<<<(D + 127) / 128, 128, 0, s>>>(C, nlist, D, mu);
+        coarse_prep_kernel<<<(nlist_pad + 127) / 128, 128, 0, s>>>(C, nlist, nlist_pad, D, mu, Bp, maxbits);
+        count_launch(2);
+        PQ_TRY_CUDA(cudaGetLastError());
+    }
+    CUtensorMap map;
+    const cuuint64_t gdim[2] = {(cuuint64_t)D, (cuuint64_t)N};
+    const cuuint64_t gstride[1] = {(cuuint64_t)D * sizeof(float)};
+    const cuuint32_t box[2] = {32u, (cuuint32_t)TM};
+    const cuuint32_t estride[2] = {1, 1};
+    const CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(X), gdim, gstride, box,
+                            estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return fail(PQ_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+    CoarseTcArgs a;
+    a.N = N;
+    a.D = D;
+    a.nlist_pad = nlist_pad;
+    a.tiles = (int)((N + TM - 1) / TM);
+    a.Bp = Bp;
+    a.mu = mu;
+    a.maxbits = maxbits;
+    a.list_of_row = list_of_row;
+    a.queue = queue;
+    a.qmask = qmask;
+    a.qlen = qlen;
+    a.err = err;
+    const int grid = std::max(1, std::min(a.tiles, sms));
+    ProfScope ps("coarse_assign_tc", s);
+    if (nlist_pad <= 4 * NBLK) {
+        PQ_TRY_CUDA(cudaFuncSetAttribute(coarse_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+        coarse_tc_kernel<4><<<grid, kThreads, SMEM_BYTES, s>>>(map, a);
+    } else {
+        PQ_TRY_CUDA(cudaFuncSetAttribute(coarse_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+        coarse_tc_kernel<0><<<grid, kThreads, SMEM_BYTES, s>>>(map, a);
+    }
+    count_launch();
+    PQ_TRY_CUDA(cudaGetLastError());
+    return PQ_OK;
+}
+
+}  // namespace pqgb

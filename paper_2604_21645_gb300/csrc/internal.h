@@ -24,13 +24,20 @@ struct Scratch {
 };
 
 // ---- k-means++ seeding (kmeanspp.cu) --------------------------------------
-// Seeds Ks codewords in each of M subspaces of width ds from the n rows of P
-// (row stride ld floats; subspace m starts at column m*ds).
-int launch_kmeanspp(const float *P, int64_t ld, int64_t n, int ds, int M, int Ks, uint64_t seed, float *C,
-                    Scratch &ws, int *err, cudaStream_t s);
-// Gathers the seeding subsample (n_s rows drawn with replacement from N) into P.
-int launch_gather_subsample(const float *X, int64_t N, int D, int64_t n_s, uint64_t seed, float *P,
-                            cudaStream_t s);
+// A chunk of rows [r0, r0 + rows) seeded with its own seed; chunks with more than
+// 100*Ks rows are seeded on a with-replacement subsample of 100*Ks of them.
+constexpr int kMaxSeedChunks = 512;
+struct SeedChunk {
+    int64_t r0 = 0, rows = 0;
+    int64_t n = 0, sub_off = -1;  // filled in by the launcher
+    uint64_t seed = 0;
+};
+// Ks codewords in each of the M subspaces (width ds) of every chunk; C is [n_chunks][M][Ks][ds].
+int launch_kmeanspp_chunks(const float *X, int64_t ld, const SeedChunk *chunks, int n_chunks, int ds, int M, int Ks,
+                           float *C, Scratch &ws, int *err, cudaStream_t s, const char *tag);
+// One chunk: all N rows of X (row stride D).
+int launch_kmeanspp(const float *X, int64_t N, int D, int M, int Ks, uint64_t seed, float *C, Scratch &ws, int *err,
+                    cudaStream_t s, const char *tag = "kmeanspp");
 
 // ---- PQ Lloyd pass, FP32 SIMT form (lloyd_simt.cu) ------------------------
 struct PqPass {
@@ -44,11 +51,19 @@ struct PqPass {
     double *sse = nullptr;         // device scalar accumulator or null
     unsigned long long *rechecks = nullptr;
     int gx = 0;                    // blocks per subspace (set by the launcher)
+    // Optional chunk table (batched form): grid block b belongs to chunk blk_chunk[b]; chunk c
+    // owns rows [chunk_off[c], chunk_off[c+1]), grid blocks [chunk_blk[c], chunk_blk[c+1]) and
+    // codebooks C + c*M*Ks*ds.  All null: one chunk, all rows, all blocks.
+    const int *blk_chunk = nullptr;
+    const int64_t *chunk_off = nullptr;
+    const int *chunk_blk = nullptr;
+    int n_chunks = 1;
 };
 int pq_pass_blocks_per_subspace(const PqPass &p);
 int launch_pq_pass_f32(PqPass &p, cudaStream_t s);
 int launch_pq_finalize(const double *part, const int *part_cnt, int gx, int M, int Ks, int ds, float *C,
-                       unsigned long long *empties, cudaStream_t s);
+                       unsigned long long *empties, cudaStream_t s, int n_chunks = 1,
+                       const int *chunk_blk = nullptr);
 int launch_decode_rmse(const uint8_t *codes, const float *C, const float *X, int64_t N, int D, int M, int Ks,
                        float *Xhat, double *sse, cudaStream_t s);
 
@@ -58,7 +73,8 @@ int pq_pass_tc_blocks(const PqPass &p);
 // writes per-CTA residual sums (x - c_code) into p.part; finalise with the residual kernel
 int launch_pq_pass_tc(PqPass &p, cudaStream_t s);
 int launch_pq_finalize_residual(const double *part, const int *part_cnt, int gx, int M, int Ks, int ds, float *C,
-                                unsigned long long *empties, cudaStream_t s);
+                                unsigned long long *empties, cudaStream_t s, int n_chunks = 1,
+                                const int *chunk_blk = nullptr);
 
 // ---- coarse quantizer and inverted lists (coarse.cu) ----------------------
 struct CoarseBound {
@@ -68,7 +84,11 @@ struct CoarseBound {
 int launch_coarse_norms(const float *C, int nlist, int D, CoarseBound &b, cudaStream_t s);
 // Nearest coarse centroid of every row (exact: FP32 bound + FP64 re-check).
 int coarse_assign(const float *X, int64_t N, int D, const float *C, int nlist, const CoarseBound &b,
-                  int32_t *list_of_row, Scratch &ws, unsigned long long *rechecks, cudaStream_t s);
+                  int32_t *list_of_row, Scratch &ws, int prec, cudaStream_t s);
+// tensor-core scores (coarse_tc.cu): certified rows written, the rest queued for the FP64 re-check
+bool coarse_tc_supported(int D, int nlist);
+int launch_coarse_tc(const float *X, int64_t N, int D, const float *C, int nlist, int32_t *list_of_row,
+                     int64_t *queue, uint32_t *qmask, unsigned long long *qlen, Scratch &ws, cudaStream_t s);
 // Stable bucketing of rows by list: offsets[nlist+1], ids[N] ascending within a list,
 // and, if codes != null, list_codes[N][M] in list order.
 int bucket_rows(const int32_t *list_of_row, int64_t N, int nlist, const uint8_t *codes, int M, int64_t *offsets,
@@ -76,6 +96,10 @@ int bucket_rows(const int32_t *list_of_row, int64_t N, int nlist, const uint8_t 
 // Coarse centroid update: FP64 sums of each list's rows in ascending row order.
 int launch_list_mean(const float *X, int D, const int64_t *offsets, const int64_t *ids, int nlist, float *C,
                      cudaStream_t s);
+
+// ---- chunked divide and conquer (chunked.cu) -------------------------------
+int run_pq_fit_chunked(const float *X, const int64_t *off, int n_chunks, int D, int M, int Ks, int iters,
+                       uint64_t seed, int prec, float *global_cb, uint8_t *codes, double *rmse, cudaStream_t s);
 
 // ---- query path (ivf_search.cu) --------------------------------------------
 struct SearchArgs {

@@ -32,19 +32,20 @@ constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 
 struct KppArgs {
-    const float *P;
+    const float *X;               // rows, stride ld floats
     int64_t ld;
-    int64_t n;
+    const int64_t *sub_rows;      // subsample row indices (chunks with sub_off >= 0)
     int ds, M, Ks;
-    uint64_t seed;
-    float *C;                     // [M][Ks][ds]
-    unsigned *bars;               // [M][2]
-    unsigned long long *bsum;     // [2][M][bps]
-    float *d2;                    // [2][M][n]
-    unsigned *dmax_bits;          // [M]
+    int n_chunks;
+    int64_t nmax;                 // largest point count of a group
+    float *C;                     // [n_chunks][M][Ks][ds]
+    unsigned *bars;               // [groups][2]
+    unsigned long long *bsum;     // [2][groups][bps]
+    float *d2;                    // [2][groups][nmax]
+    unsigned *dmax_bits;          // [groups]
     int *err;
     int bps;
-    int64_t nb;                   // points per block
+    SeedChunk ch[kMaxSeedChunks];
 };
 
 __device__ __forceinline__ float d2_f32_exact(const float *x, const float *c, int ds)
@@ -128,29 +129,38 @@ __global__ void __launch_bounds__(kThreads) kmeanspp_kernel(KppArgs a)
     __shared__ int s_owner;
     __shared__ unsigned long long s_thr;
 
-    const int m = blockIdx.y, b = blockIdx.x, tid = threadIdx.x;
+    // group = (chunk, subspace); its points are the chunk's rows or its subsample
+    const int grp = blockIdx.y, b = blockIdx.x, tid = threadIdx.x;
+    const int chunk = grp / a.M, m = grp % a.M;
+    const SeedChunk ck = a.ch[chunk];
+    const int64_t n = ck.n;
+    const uint64_t seed = ck.seed;
     const int ds = a.ds;
-    const int64_t i0 = (int64_t)b * a.nb;
-    const int64_t cnt = max((int64_t)0, min(a.n, i0 + a.nb) - i0);
-    const float *Pm = a.P + (int64_t)m * ds;
-    unsigned *bar = a.bars + 2 * m;
-    float *Cm = a.C + (size_t)m * a.Ks * ds;
-    const size_t plane = (size_t)a.M * a.n;      // one D2 buffer
-    float *d2m = a.d2 + (size_t)m * a.n;         // + buffer * plane
-    unsigned long long *bs = a.bsum + (size_t)m * a.bps;
-    const size_t bplane = (size_t)a.M * a.bps;
+    const int64_t nb = (n + a.bps - 1) / a.bps;
+    const int64_t i0 = (int64_t)b * nb;
+    const int64_t cnt = max((int64_t)0, min(n, i0 + nb) - i0);
+    const float *Pm = a.X + (int64_t)m * ds;
+    const int64_t *sub = ck.sub_off >= 0 ? a.sub_rows + ck.sub_off : nullptr;
+    auto point = [&](int64_t i) -> const float * { return Pm + (ck.r0 + (sub ? sub[i] : i)) * a.ld; };
+    unsigned *bar = a.bars + 2 * grp;
+    float *Cm = a.C + ((size_t)chunk * a.M + m) * a.Ks * ds;
+    const int groups = a.n_chunks * a.M;
+    const size_t plane = (size_t)groups * a.nmax;  // one D2 buffer
+    float *d2m = a.d2 + (size_t)grp * a.nmax;      // + buffer * plane
+    unsigned long long *bs = a.bsum + (size_t)grp * a.bps;
+    const size_t bplane = (size_t)groups * a.bps;
 
     // ---- round 0 -----------------------------------------------------------
-    long long pick = scale_index(rng_draw(a.seed, (uint64_t)m, 0) >> 11, (uint64_t)a.n);
+    long long pick = scale_index(rng_draw(seed, (uint64_t)m, 0) >> 11, (uint64_t)n);
     for (int j = tid; j < ds; j += kThreads) {
-        const float v = Pm[pick * a.ld + j];
+        const float v = point(pick)[j];
         s_center[j] = v;
         if (b == 0) Cm[j] = v;
     }
     __syncthreads();
     float lmax = 0.0f;
     for (int64_t i = tid; i < cnt; i += kThreads) {
-        const float d = d2_f32_exact(Pm + (i0 + i) * a.ld, s_center, ds);
+        const float d = d2_f32_exact(point(i0 + i), s_center, ds);
         d2m[plane + i0 + i] = d;  // buffer 1 holds D2 for round 1
         lmax = fmaxf(lmax, d);
     }
@@ -161,13 +171,13 @@ __global__ void __launch_bounds__(kThreads) kmeanspp_kernel(KppArgs a)
     if (tid == 0) {
         float v = 0.0f;
         for (int w = 0; w < kWarps; ++w) v = fmaxf(v, s_fmax[w]);
-        atomicMax(a.dmax_bits + m, __float_as_uint(v));  // non-negative floats order as integers
+        atomicMax(a.dmax_bits + grp, __float_as_uint(v));  // non-negative floats order as integers
     }
     if (!block_group_barrier(bar, a.bps, a.err)) return;
-    const float dmax = __uint_as_float(ld_acquire_u32(a.dmax_bits + m));
+    const float dmax = __uint_as_float(ld_acquire_u32(a.dmax_bits + grp));
     const bool any = dmax > 0.0f;
     int L = 0;
-    while (((int64_t)1 << L) < a.n) ++L;
+    while (((int64_t)1 << L) < n) ++L;
     int E = 0;
     if (any) {
         const unsigned bits = __float_as_uint(dmax);
@@ -189,7 +199,7 @@ __global__ void __launch_bounds__(kThreads) kmeanspp_kernel(KppArgs a)
             if (t == 1) {
                 d = D2c[i0 + i];
             } else {
-                d = d2_f32_exact(Pm + (i0 + i) * a.ld, s_center, ds);
+                d = d2_f32_exact(point(i0 + i), s_center, ds);
                 d = fminf(d, D2p[i0 + i]);
                 D2c[i0 + i] = d;
             }
@@ -206,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) kmeanspp_kernel(KppArgs a)
         if (!block_group_barrier(bar, a.bps, a.err)) return;
 
         // every block: owner block and threshold
-        const uint64_t r = rng_draw(a.seed, (uint64_t)m, (uint64_t)t) >> 11;
+        const uint64_t r = rng_draw(seed, (uint64_t)m, (uint64_t)t) >> 11;
         if (tid < 32) {
             const volatile unsigned long long *bv = bs + (size_t)cur * bplane;
             uint64_t W = 0;
@@ -216,7 +226,7 @@ __global__ void __launch_bounds__(kThreads) kmeanspp_kernel(KppArgs a)
             uint64_t thr_local = 0;
             long long p = -1;
             if (W == 0) {
-                p = scale_index(r, (uint64_t)a.n);
+                p = scale_index(r, (uint64_t)n);
             } else {
                 const uint64_t thr = (__umul64hi(r, W) << 11) | ((r * W) >> 53);
                 uint64_t acc = 0;
@@ -243,8 +253,8 @@ __global__ void __launch_bounds__(kThreads) kmeanspp_kernel(KppArgs a)
             // walk the owner's D2 values in order to the threshold
             const int owner = s_owner;
             const uint64_t thr_local = s_thr;
-            const int64_t o0 = (int64_t)owner * a.nb;
-            const int64_t ocnt = min(a.n, o0 + a.nb) - o0;
+            const int64_t o0 = (int64_t)owner * nb;
+            const int64_t ocnt = min(n, o0 + nb) - o0;
             const int64_t seg = (ocnt + kThreads - 1) / kThreads;
             const int64_t s0 = min(ocnt, (int64_t)tid * seg), s1 = min(ocnt, s0 + seg);
             uint64_t w = 0;
@@ -262,7 +272,7 @@ __global__ void __launch_bounds__(kThreads) kmeanspp_kernel(KppArgs a)
         }
         pick = s_pick;
         for (int j = tid; j < ds; j += kThreads) {
-            const float v = Pm[pick * a.ld + j];
+            const float v = point(pick)[j];
             s_center[j] = v;
             if (b == 0) Cm[(size_t)t * ds + j] = v;
         }
@@ -270,71 +280,101 @@ __global__ void __launch_bounds__(kThreads) kmeanspp_kernel(KppArgs a)
     }
 }
 
-__global__ void gather_subsample_kernel(const float *X, int64_t N, int D, int64_t n_s, uint64_t seed, float *P)
+// Row indices of the with-replacement subsample of every chunk that needs one:
+// index l of chunk c is floor(u * rows_c) with u draw l of the subsample stream of seed_c.
+__global__ void subsample_rows_kernel(const KppArgs a, int64_t n_s, int64_t *sub_rows)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t l = warp; l < n_s; l += nw) {
-        const int64_t row = scale_index(rng_draw(seed, kStreamSubsample, (uint64_t)l) >> 11, (uint64_t)N);
-        const float *src = X + row * D;
-        float *dst = P + l * D;
-        for (int j = lane; j < D; j += 32) dst[j] = src[j];
-    }
+    const SeedChunk ck = a.ch[blockIdx.y];
+    if (ck.sub_off < 0) return;
+    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n_s; l += (int64_t)gridDim.x * blockDim.x)
+        sub_rows[ck.sub_off + l] = scale_index(rng_draw(ck.seed, kStreamSubsample, (uint64_t)l) >> 11, (uint64_t)ck.rows);
 }
 
 }  // namespace
 
-int launch_gather_subsample(const float *X, int64_t N, int D, int64_t n_s, uint64_t seed, float *P, cudaStream_t s)
-{
-    int blocks = (int)std::min<int64_t>((n_s + 7) / 8, 152 * 16);
-    ProfScope ps("gather_subsample", s);
-    gather_subsample_kernel<<<blocks, 256, 0, s>>>(X, N, D, n_s, seed, P);
-    count_launch();
-    PQ_TRY_CUDA(cudaGetLastError());
-    return PQ_OK;
-}
-
-int launch_kmeanspp(const float *P, int64_t ld, int64_t n, int ds, int M, int Ks, uint64_t seed, float *C,
-                    Scratch &ws, int *err, cudaStream_t s)
+int launch_kmeanspp_chunks(const float *X, int64_t ld, const SeedChunk *chunks, int n_chunks, int ds, int M, int Ks,
+                           float *C, Scratch &ws, int *err, cudaStream_t s, const char *tag)
 {
     if (ds > 256) return fail(PQ_ENOTSUP, "k-means++ seeding supports subspace width <= 256 (got %d)", ds);
+    if (n_chunks < 1 || n_chunks > kMaxSeedChunks) return fail(PQ_ENOTSUP, "at most %d chunks", kMaxSeedChunks);
     int dev = 0, sms = 0;
     PQ_TRY_CUDA(cudaGetDevice(&dev));
     PQ_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    int per_sm = 0;
-    PQ_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kmeanspp_kernel, kThreads, 0));
-    const int64_t capacity = (int64_t)per_sm * sms;
-    // About one block per SM over all subspaces, at least 256 points per block.
-    const int64_t want = std::max<int64_t>(1, std::min<int64_t>(sms / std::max(1, M), (n + 255) / 256));
-    if (want * M > capacity)
-        return fail(PQ_ENOTSUP, "k-means++ seeding: %d subspaces do not fit one cooperative wave", M);
-    const int bps = (int)want;
-    const int64_t nb = (n + bps - 1) / bps;
-
+    const int64_t cap = 100LL * Ks;
     KppArgs a;
-    a.P = P;
+    a.X = X;
     a.ld = ld;
-    a.n = n;
     a.ds = ds;
     a.M = M;
     a.Ks = Ks;
-    a.seed = seed;
+    a.n_chunks = n_chunks;
+    a.nmax = 0;
+    int64_t n_sub = 0;
+    for (int c = 0; c < n_chunks; ++c) {
+        a.ch[c] = chunks[c];
+        if (chunks[c].rows > cap) {
+            a.ch[c].n = cap;
+            a.ch[c].sub_off = n_sub * cap;
+            ++n_sub;
+        } else {
+            a.ch[c].n = chunks[c].rows;
+            a.ch[c].sub_off = -1;
+        }
+        if (a.ch[c].n < Ks) return fail(PQ_EINVAL, "chunk %d has %lld rows, fewer than Ks=%d", c, (long long)a.ch[c].n, Ks);
+        a.nmax = std::max(a.nmax, a.ch[c].n);
+    }
+    const int groups = n_chunks * M;
+    // One chunk: about one block per SM over its subspaces, cooperative (blocks of a subspace
+    // meet at barriers).  Several chunks: one block per (chunk, subspace), no inter-block waits.
+    int bps = 1;
+    bool coop = false;
+    if (n_chunks == 1) {
+        int per_sm = 0;
+        PQ_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kmeanspp_kernel, kThreads, 0));
+        const int64_t capacity = (int64_t)per_sm * sms;
+        const int64_t want = std::max<int64_t>(1, std::min<int64_t>(sms / std::max(1, M), (a.nmax + 255) / 256));
+        if (want * M > capacity)
+            return fail(PQ_ENOTSUP, "k-means++ seeding: %d subspaces do not fit one cooperative wave", M);
+        bps = (int)want;
+        coop = true;
+    }
+    a.bps = bps;
+    a.sub_rows = n_sub ? ws.get<int64_t>((size_t)n_sub * cap) : nullptr;
     a.C = C;
-    a.bars = ws.get<unsigned>(2 * (size_t)M, true);
-    a.bsum = ws.get<unsigned long long>(2 * (size_t)M * bps, true);
-    a.d2 = ws.get<float>(2 * (size_t)M * n);
-    a.dmax_bits = ws.get<unsigned>((size_t)M, true);
+    a.bars = ws.get<unsigned>(2 * (size_t)groups, true);
+    a.bsum = ws.get<unsigned long long>(2 * (size_t)groups * bps, true);
+    a.d2 = ws.get<float>(2 * (size_t)groups * a.nmax);
+    a.dmax_bits = ws.get<unsigned>((size_t)groups, true);
     if (ws.status) return ws.status;
     a.err = err;
-    a.bps = bps;
-    a.nb = nb;
-    void *args[] = {&a};
-    dim3 grid(bps, M);
-    ProfScope ps("kmeanspp", s);
-    PQ_TRY_CUDA(cudaLaunchCooperativeKernel((void *)kmeanspp_kernel, grid, dim3(kThreads), args, 0, s));
+    if (n_sub) {
+        ProfScope ps("subsample_rows", s);
+        subsample_rows_kernel<<<dim3((unsigned)((cap + 255) / 256), n_chunks), 256, 0, s>>>(a, cap,
+                                                                                       const_cast<int64_t *>(a.sub_rows));
+        count_launch();
+        PQ_TRY_CUDA(cudaGetLastError());
+    }
+    dim3 grid(bps, groups);
+    ProfScope ps(tag, s);
+    if (coop) {
+        void *args[] = {&a};
+        PQ_TRY_CUDA(cudaLaunchCooperativeKernel((void *)kmeanspp_kernel, grid, dim3(kThreads), args, 0, s));
+    } else {
+        kmeanspp_kernel<<<grid, kThreads, 0, s>>>(a);
+        PQ_TRY_CUDA(cudaGetLastError());
+    }
     count_launch();
     return PQ_OK;
+}
+
+int launch_kmeanspp(const float *X, int64_t N, int D, int M, int Ks, uint64_t seed, float *C, Scratch &ws, int *err,
+                    cudaStream_t s, const char *tag)
+{
+    SeedChunk c;
+    c.r0 = 0;
+    c.rows = N;
+    c.seed = seed;
+    return launch_kmeanspp_chunks(X, D, &c, 1, D / M, M, Ks, C, ws, err, s, tag);
 }
 
 }  // namespace pqgb

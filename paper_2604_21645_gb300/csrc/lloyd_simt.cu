@@ -90,6 +90,16 @@ __global__ void __launch_bounds__(kThreads) pq_pass_f32_kernel(const PqPass a, c
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int m = blockIdx.y, Ks = a.Ks, tid = threadIdx.x;
     const bool fit = a.part != nullptr;
+    // chunk of this block (batched form) and its rows
+    int chunk = 0, lb = blockIdx.x, gxc = gridDim.x;
+    int64_t r0 = 0, r1 = a.N;
+    if (a.blk_chunk) {
+        chunk = a.blk_chunk[blockIdx.x];
+        lb = blockIdx.x - a.chunk_blk[chunk];
+        gxc = a.chunk_blk[chunk + 1] - a.chunk_blk[chunk];
+        r0 = a.chunk_off[chunk];
+        r1 = a.chunk_off[chunk + 1];
+    }
     double *acc = reinterpret_cast<double *>(smem_raw);
     float *cb = reinterpret_cast<float *>(acc + Ks * DS);
     float *cn = cb + Ks * DS;
@@ -97,7 +107,7 @@ __global__ void __launch_bounds__(kThreads) pq_pass_f32_kernel(const PqPass a, c
     __shared__ float s_red[kThreads / 32];
     __shared__ double s_sse[kThreads / 32];
 
-    const float *Cm = a.C + (size_t)m * Ks * DS;
+    const float *Cm = a.C + ((size_t)chunk * a.M + m) * Ks * DS;
     for (int e = tid; e < Ks * DS; e += kThreads) {
         cb[e] = Cm[e];
         if (fit) acc[e] = 0.0;
@@ -126,12 +136,12 @@ __global__ void __launch_bounds__(kThreads) pq_pass_f32_kernel(const PqPass a, c
 
     double sse = 0.0;
     unsigned rechecks = 0;
-    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    const int64_t stride = (int64_t)gxc * kThreads;
     for (int bi = 0;; ++bi) {
-        const int64_t base = (int64_t)bi * stride + (int64_t)blockIdx.x * kThreads;
-        if (base >= a.N) break;
+        const int64_t base = r0 + (int64_t)bi * stride + (int64_t)lb * kThreads;
+        if (base >= r1) break;
         const int64_t row = base + tid;
-        if (row < a.N) {
+        if (row < r1) {
             float x[DS];
             load_row<DS>(a.X + row * a.D + (int64_t)m * DS, x, vec);
             float xx = 0.0f;
@@ -194,20 +204,23 @@ __global__ void __launch_bounds__(kThreads) pq_pass_f32_kernel(const PqPass a, c
 }
 
 __global__ void pq_finalize_kernel(const double *__restrict__ part, const int *__restrict__ part_cnt, int gx, int M,
-                                   int Ks, int ds, float *C, unsigned long long *empties)
+                                   int Ks, int ds, float *C, unsigned long long *empties, int n_chunks,
+                                   const int *__restrict__ chunk_blk)
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= M * Ks) return;
-    const int m = idx / Ks, k = idx % Ks;
+    if (idx >= n_chunks * M * Ks) return;
+    const int c = idx / (M * Ks), m = (idx / Ks) % M, k = idx % Ks;
+    const int b0 = chunk_blk ? chunk_blk[c] : 0, b1 = chunk_blk ? chunk_blk[c + 1] : gx;
+    C += (size_t)c * M * Ks * ds;
     long long cnt = 0;
-    for (int b = 0; b < gx; ++b) cnt += part_cnt[((size_t)b * M + m) * Ks + k];
+    for (int b = b0; b < b1; ++b) cnt += part_cnt[((size_t)b * M + m) * Ks + k];
     if (cnt == 0) {
         if (empties) atomicAdd(empties, 1ull);
         return;
     }
     for (int j = 0; j < ds; ++j) {
         double s = 0.0;
-        for (int b = 0; b < gx; ++b) {
+        for (int b = b0; b < b1; ++b) {
             s = __dadd_rn(s, part[(((size_t)b * M + m) * Ks + k) * ds + j]);
         }
         C[((size_t)m * Ks + k) * ds + j] = __double2float_rn(__ddiv_rn(s, (double)cnt));
@@ -297,11 +310,12 @@ int launch_pq_pass_f32(PqPass &p, cudaStream_t s)
 }
 
 int launch_pq_finalize(const double *part, const int *part_cnt, int gx, int M, int Ks, int ds, float *C,
-                       unsigned long long *empties, cudaStream_t s)
+                       unsigned long long *empties, cudaStream_t s, int n_chunks, const int *chunk_blk)
 {
-    const int n = M * Ks;
+    const int n = n_chunks * M * Ks;
     ProfScope ps("pq_finalize", s);
-    pq_finalize_kernel<<<(n + 127) / 128, 128, 0, s>>>(part, part_cnt, gx, M, Ks, ds, C, empties);
+    pq_finalize_kernel<<<(n + 127) / 128, 128, 0, s>>>(part, part_cnt, gx, M, Ks, ds, C, empties, n_chunks,
+                                                       chunk_blk);
     count_launch();
     PQ_TRY_CUDA(cudaGetLastError());
     return PQ_OK;

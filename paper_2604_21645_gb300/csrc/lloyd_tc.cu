@@ -63,10 +63,14 @@ constexpr int B_HALF = KSMAX * 16 * 2;               // 8 KB
 constexpr int OFF_XS = 0;
 constexpr int OFF_A = OFF_XS + 2 * XS_BYTES;                // [wg][buf][half]
 constexpr int OFF_B = OFF_A + 2 * 2 * 2 * A_HALF;           // [g][half]
+// Row strides of the FP32 codeword copy (12 floats: 16-byte aligned rows that fall on different
+// bank groups for random codes) and of the update sums (9 floats: conflict-free scalar atomics).
+constexpr int CB_STRIDE = 12;
+constexpr int ACC_STRIDE = 9;
 constexpr int OFF_CBF = OFF_B + G * 2 * B_HALF;
-constexpr int OFF_CN = OFF_CBF + G * KSMAX * DS * 4;
+constexpr int OFF_CN = OFF_CBF + G * KSMAX * CB_STRIDE * 4;
 constexpr int OFF_ACC = OFF_CN + G * KSMAX * 4;
-constexpr int OFF_CNT = OFF_ACC + G * KSMAX * DS * 4;
+constexpr int OFF_CNT = OFF_ACC + G * KSMAX * ACC_STRIDE * 4;
 constexpr int OFF_MISC = OFF_CNT + G * KSMAX * 4;
 constexpr int MISC_BYTES = 512;
 constexpr int SMEM_BYTES = OFF_MISC + MISC_BYTES + 1024;  // + alignment slack
@@ -94,6 +98,9 @@ struct TcArgs {
     double *sse;
     unsigned long long *rechecks;
     int *err;
+    const int *blk_chunk;      // optional chunk table (batched form)
+    const int64_t *chunk_off;
+    const int *chunk_blk;
 };
 
 // ---- PTX wrappers ----------------------------------------------------------
@@ -213,7 +220,7 @@ __device__ __forceinline__ int exact_code(const float *x, const float *cb, const
     for (int k = 0; k < Ks; ++k) {
         float s = cn[k];
 #pragma unroll
-        for (int j = 0; j < DS; ++j) s = fmaf(-x[j], cb[k * DS + j], s);
+        for (int j = 0; j < DS; ++j) s = fmaf(-x[j], cb[k * CB_STRIDE + j], s);
         const bool lt = s < m1;
         m2 = lt ? m1 : fminf(m2, s);
         i1 = lt ? k : i1;
@@ -227,9 +234,9 @@ __device__ __forceinline__ int exact_code(const float *x, const float *cb, const
     for (int k = 0; k < Ks; ++k) {
         float s = cn[k];
 #pragma unroll
-        for (int j = 0; j < DS; ++j) s = fmaf(-x[j], cb[k * DS + j], s);
+        for (int j = 0; j < DS; ++j) s = fmaf(-x[j], cb[k * CB_STRIDE + j], s);
         if (s <= m1 + win) {
-            const double d = d2_fp64(x, cb + k * DS, DS);
+            const double d = d2_fp64(x, cb + k * CB_STRIDE, DS);
             if (d < best) { best = d; bk = k; }
         }
     }
@@ -243,7 +250,7 @@ __device__ __forceinline__ int rerank(const float *x, const float *cb, const int
     float d1 = FLT_MAX, d2 = FLT_MAX;
     int k1 = 0x7fffffff;
     for (int i = 0; i < nc; ++i) {
-        const float *c = cb + cand[i] * DS;
+        const float *c = cb + cand[i] * CB_STRIDE;
         float d = 0.0f;
 #pragma unroll
         for (int j = 0; j < DS; ++j) {
@@ -258,7 +265,7 @@ __device__ __forceinline__ int rerank(const float *x, const float *cb, const int
     double best = DBL_MAX;
     int bk = 0x7fffffff;
     for (int i = 0; i < nc; ++i) {
-        const float *c = cb + cand[i] * DS;
+        const float *c = cb + cand[i] * CB_STRIDE;
         float d = 0.0f;
 #pragma unroll
         for (int j = 0; j < DS; ++j) {
@@ -282,6 +289,18 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
     const int grp = blockIdx.y, m0 = grp * G;
     const int Ks = a.Ks;
     const bool fit = a.part != nullptr;
+    // chunk of this CTA (batched form): its rows, its share of the CTAs, its codebooks
+    int chunk = 0, lb = blockIdx.x, gxc = gridDim.x;
+    int64_t r0 = 0, r1 = a.N;
+    if (a.blk_chunk) {
+        chunk = a.blk_chunk[blockIdx.x];
+        lb = blockIdx.x - a.chunk_blk[chunk];
+        gxc = a.chunk_blk[chunk + 1] - a.chunk_blk[chunk];
+        r0 = a.chunk_off[chunk];
+        r1 = a.chunk_off[chunk + 1];
+    }
+    const int tiles_c = (int)((r1 - r0 + TM - 1) / TM);
+    const float *Cc = a.C + (size_t)chunk * a.M * Ks * DS;
 
     float *xs = reinterpret_cast<float *>(sm + OFF_XS);
     unsigned char *aop = sm + OFF_A;
@@ -298,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
     // ---- set-up: codeword mean, B operands, FP32 copies, norms, bounds ------
     if (tid < G * DS) {
         const int g = tid / DS, j = tid % DS;
-        const float *Cm = a.C + (size_t)(m0 + g) * Ks * DS;
+        const float *Cm = Cc + (size_t)(m0 + g) * Ks * DS;
         float s = 0.0f;
         for (int k = 0; k < Ks; ++k) s += Cm[k * DS + j];
         mu[tid] = s / (float)Ks;
@@ -310,7 +329,7 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
         float c[DS], cc[DS];
         float nc = 0.0f, n = 0.0f, norm2c = 0.0f;
         if (k < Ks) {
-            const float *src = a.C + ((size_t)(m0 + g) * Ks + k) * DS;
+            const float *src = Cc + ((size_t)(m0 + g) * Ks + k) * DS;
 #pragma unroll
             for (int j = 0; j < DS; ++j) {
                 c[j] = src[j];
@@ -326,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
             for (int j = 0; j < DS; ++j) { c[j] = 0.0f; cc[j] = 0.0f; }
         }
 #pragma unroll
-        for (int j = 0; j < DS; ++j) cbf[(g * KSMAX + k) * DS + j] = c[j];
+        for (int j = 0; j < DS; ++j) cbf[(g * KSMAX + k) * CB_STRIDE + j] = c[j];
         cn[g * KSMAX + k] = n;
         float ch[DS], cl[DS];
 #pragma unroll
@@ -359,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
         }
         if (fit) {
 #pragma unroll
-            for (int j = 0; j < DS; ++j) acc[(g * KSMAX + k) * DS + j] = 0.0f;
+            for (int j = 0; j < DS; ++j) acc[(g * KSMAX + k) * ACC_STRIDE + j] = 0.0f;
             cnt[g * KSMAX + k] = 0;
         }
     }
@@ -385,7 +404,7 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
     tc_after_sync();
     const uint32_t tmem = *tslot;
 
-    const int n_my = (a.tiles > (int)blockIdx.x) ? (a.tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int n_my = (tiles_c > lb) ? (tiles_c - 1 - lb) / gxc + 1 : 0;
     const int wsteps = 2 * n_my;  // steps of each warpgroup
 
     if (warp == 0) {
@@ -397,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
                 if (i >= 2 && !mbar_wait(smem_u32(mb + MB_EMPTY + s), ((i >> 1) - 1) & 1, a.err)) break;
                 mbar_expect_tx(smem_u32(mb + MB_FULL + s), XS_BYTES);
                 tma_load_2d(smem_u32(reinterpret_cast<unsigned char *>(xs) + s * XS_BYTES), &tmap, m0 * DS,
-                            ((int)blockIdx.x + i * (int)gridDim.x) * TM, smem_u32(mb + MB_FULL + s));
+                            (int)(r0 + (int64_t)(lb + i * gxc) * TM), smem_u32(mb + MB_FULL + s));
                 ++issued;
             }
             // our own copies must have landed before the CTA can leave
@@ -440,7 +459,7 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
         uint32_t code_pair = 0;
         for (int u = 0; u < wsteps; ++u) {
             const int i = u >> 1, h = u & 1, g = 2 * w + h, s = i & 1, buf = u & 1;
-            const int64_t row = (int64_t)((int)blockIdx.x + i * (int)gridDim.x) * TM + r;
+            const int64_t row = r0 + (int64_t)(lb + i * gxc) * TM + r;
             const float *stage = xs + s * (XS_BYTES / 4);
             // (a) A operand of this step
             if (h == 0 && !__all_sync(0xffffffffu, mbar_wait(smem_u32(mb + MB_FULL + s), (i >> 1) & 1, a.err))) break;
@@ -521,7 +540,7 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
                 nin += (sv[q2] >= theta) ? 1 : 0;
             }
             int code = bestj * 32 + ib;
-            const bool valid = row < a.N;
+            const bool valid = row < r1;
             const bool unsure = valid && !(nin == 1 && cm2 < theta);
             if (__any_sync(0xffffffffu, unsure)) {
                 // complete candidate set: the saved chunk, plus every other chunk reaching theta
@@ -551,7 +570,7 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
                     }
                 }
                 if (unsure) {
-                    const float *cbg = cbf + g * KSMAX * DS;
+                    const float *cbg = cbf + g * KSMAX * CB_STRIDE;
                     code = over ? exact_code(x, cbg, cn + g * KSMAX, Ks, nb_orig[h], cb_orig[h]) : rerank(x, cbg, cand, nc);
                     ++rechecks;
                 }
@@ -560,12 +579,15 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(mb + MB_TFREE + w));
             if (valid) {
-                const float *c = cbf + (g * KSMAX + code) * DS;
+                const float *c = cbf + (g * KSMAX + code) * CB_STRIDE;
                 float e = 0.0f;
                 float res[DS];
+                const float4 c0 = *reinterpret_cast<const float4 *>(c);
+                const float4 c1 = *reinterpret_cast<const float4 *>(c + 4);
+                const float cv[DS] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
 #pragma unroll
                 for (int d = 0; d < DS; ++d) {
-                    res[d] = x[d] - c[d];
+                    res[d] = x[d] - cv[d];
                     e = fmaf(res[d], res[d], e);
                 }
                 const float y = e - sse_c;  // Kahan accumulation of the squared error
@@ -573,7 +595,7 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
                 sse_c = (t2 - sse_s) - y;
                 sse_s = t2;
                 if (fit) {
-                    float *ac = acc + (g * KSMAX + code) * DS;
+                    float *ac = acc + (g * KSMAX + code) * ACC_STRIDE;
 #pragma unroll
                     for (int d = 0; d < DS; ++d) atomicAdd(ac + d, res[d]);
                     atomicAdd(cnt + g * KSMAX + code, 1);
@@ -596,7 +618,7 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
                 if (k >= Ks) continue;
                 const size_t base = ((size_t)blockIdx.x * a.M + m0 + g) * Ks + k;
 #pragma unroll
-                for (int d = 0; d < DS; ++d) a.part[base * DS + d] = (double)acc[(g * KSMAX + k) * DS + d];
+                for (int d = 0; d < DS; ++d) a.part[base * DS + d] = (double)acc[(g * KSMAX + k) * ACC_STRIDE + d];
                 a.part_cnt[base] = cnt[g * KSMAX + k];
             }
         }
@@ -616,20 +638,23 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
 }
 
 __global__ void pq_finalize_residual_kernel(const double *__restrict__ part, const int *__restrict__ part_cnt, int gx,
-                                            int M, int Ks, int ds, float *C, unsigned long long *empties)
+                                            int M, int Ks, int ds, float *C, unsigned long long *empties, int n_chunks,
+                                            const int *__restrict__ chunk_blk)
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= M * Ks) return;
-    const int m = idx / Ks, k = idx % Ks;
+    if (idx >= n_chunks * M * Ks) return;
+    const int c = idx / (M * Ks), m = (idx / Ks) % M, k = idx % Ks;
+    const int b0 = chunk_blk ? chunk_blk[c] : 0, b1 = chunk_blk ? chunk_blk[c + 1] : gx;
+    C += (size_t)c * M * Ks * ds;
     long long n = 0;
-    for (int b = 0; b < gx; ++b) n += part_cnt[((size_t)b * M + m) * Ks + k];
+    for (int b = b0; b < b1; ++b) n += part_cnt[((size_t)b * M + m) * Ks + k];
     if (n == 0) {
         if (empties) atomicAdd(empties, 1ull);
         return;
     }
     for (int j = 0; j < ds; ++j) {
         double s = 0.0;
-        for (int b = 0; b < gx; ++b) s = __dadd_rn(s, part[(((size_t)b * M + m) * Ks + k) * ds + j]);
+        for (int b = b0; b < b1; ++b) s = __dadd_rn(s, part[(((size_t)b * M + m) * Ks + k) * ds + j]);
         float *c = C + ((size_t)m * Ks + k) * ds + j;
         *c = __double2float_rn(__dadd_rn((double)*c, __ddiv_rn(s, (double)n)));
     }
@@ -699,6 +724,9 @@ int launch_pq_pass_tc(PqPass &p, cudaStream_t s)
     a.sse = p.sse;
     a.rechecks = p.rechecks;
     a.err = err;
+    a.blk_chunk = p.blk_chunk;
+    a.chunk_off = p.chunk_off;
+    a.chunk_blk = p.chunk_blk;
     PQ_TRY_CUDA(cudaFuncSetAttribute(pq_pass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     dim3 grid(p.gx, p.M / G);
     ProfScope ps("pq_pass_tc", s);
@@ -709,11 +737,12 @@ int launch_pq_pass_tc(PqPass &p, cudaStream_t s)
 }
 
 int launch_pq_finalize_residual(const double *part, const int *part_cnt, int gx, int M, int Ks, int ds, float *C,
-                                unsigned long long *empties, cudaStream_t s)
+                                unsigned long long *empties, cudaStream_t s, int n_chunks, const int *chunk_blk)
 {
-    const int n = M * Ks;
+    const int n = n_chunks * M * Ks;
     ProfScope ps("pq_finalize", s);
-    pq_finalize_residual_kernel<<<(n + 127) / 128, 128, 0, s>>>(part, part_cnt, gx, M, Ks, ds, C, empties);
+    pq_finalize_residual_kernel<<<(n + 127) / 128, 128, 0, s>>>(part, part_cnt, gx, M, Ks, ds, C, empties, n_chunks,
+                                                                chunk_blk);
     count_launch();
     PQ_TRY_CUDA(cudaGetLastError());
     return PQ_OK;

@@ -22,7 +22,7 @@ PREC = {"fp32": PQ_PREC_FP32, "bf16": PQ_PREC_BF16}
 STATS_MAX_ITERS = 64
 EXPORTS = ("pq_fit", "pq_init_kmeanspp", "pq_encode", "pq_decode_rmse", "ivf_build", "ivf_search", "ivf_get_info",
            "ivf_copy_coarse", "ivf_copy_lists", "ivf_free", "pq_sync_status", "pq_last_error", "pq_launch_count",
-           "pq_profile_enable", "pq_profile_collect", "pq_profile_names", "pq_lloyd_noalloc")
+           "pq_profile_enable", "pq_profile_collect", "pq_profile_names", "pq_lloyd_noalloc", "pq_fit_chunked")
 
 
 class PqStats(C.Structure):
@@ -64,6 +64,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "pq_profile_collect": (i32, [C.c_char_p, C.POINTER(i64), C.POINTER(dbl)]),
         "pq_profile_names": (i32, [C.c_char_p, i32]),
         "pq_lloyd_noalloc": (i32, [p, i64, i32, i32, i32, i32, p, p, p]),
+        "pq_fit_chunked": (i32, [p, C.POINTER(i64), i32, i32, i32, i32, i32, u64, i32, p, p, C.POINTER(dbl), p]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -172,6 +173,29 @@ def lloyd_noalloc(X: torch.Tensor, init: torch.Tensor, iters: int, out: torch.Te
     with torch.cuda.device(X.device):
         _check(_lib.pq_lloyd_noalloc(px, N, D, M, Ks, iters, pi, po, _stream(X)))
     return out
+
+
+def fit_chunked(X: torch.Tensor, chunk_offsets, M: int, Ks: int = 256, iters: int = 20, seed: int = 0,
+                prec: str = "fp32", want_rmse: bool = True):
+    """Divide-and-conquer PQ (Sec. 3): per-chunk fits, pooled codewords, global refit, global encode.
+
+    ``chunk_offsets`` is a host sequence of n_chunks + 1 row offsets.  Returns
+    (global codebooks [M][Ks][D/M], codes [N][M] uint8, RMSE or None).
+    """
+    px = _need(X, torch.float32, 2, "X")
+    N, D = X.shape
+    off = (C.c_int64 * len(chunk_offsets))(*[int(v) for v in chunk_offsets])
+    n_chunks = len(chunk_offsets) - 1
+    if n_chunks < 1 or off[n_chunks] != N:
+        raise ValueError("chunk_offsets must end at N")
+    cb = torch.empty((M, Ks, D // M), dtype=torch.float32, device=X.device)
+    codes = torch.empty((N, M), dtype=torch.uint8, device=X.device)
+    r = C.c_double(0.0)
+    with torch.cuda.device(X.device):
+        _check(_lib.pq_fit_chunked(px, off, n_chunks, D, M, Ks, iters, seed & (2**64 - 1), PREC[prec],
+                                   C.c_void_p(cb.data_ptr()), C.c_void_p(codes.data_ptr()),
+                                   C.byref(r) if want_rmse else None, _stream(X)))
+    return cb, codes, (r.value if want_rmse else None)
 
 
 def encode(X: torch.Tensor, codebooks: torch.Tensor, prec: str = "fp32", out: torch.Tensor | None = None,

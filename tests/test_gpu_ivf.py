@@ -49,6 +49,31 @@ def test_build_matches_oracle(setup):
     assert np.array_equal(codes, ref["list_codes"])
 
 
+def test_build_bf16_tensor_core_matches_oracle(pq, setup):
+    """The tcgen05 coarse quantizer certifies or re-checks every list decision: same index as the oracle."""
+    ref = setup["ref"]
+    idx = pq.IVFIndex.build(dev(setup["X"]), dev(setup["codes"]), setup["nlist"], iters=4, seed=99, prec="bf16")
+    assert np.array_equal(idx.coarse().cpu().numpy(), ref["coarse"])
+    off, ids, codes = (t.cpu().numpy() for t in idx.lists())
+    assert np.array_equal(off, ref["offsets"])
+    assert np.array_equal(ids, ref["ids"])
+    assert np.array_equal(codes, ref["list_codes"])
+
+
+@pytest.mark.parametrize("D,nlist,kind", [(128, 300, "int255"), (64, 512, "cont"), (96, 257, "cont")])
+def test_build_bf16_shapes(pq, D, nlist, kind):
+    N = 30_011
+    X = datagen.mixture(N, D, 150, kind, 700 + D)
+    M = D // 8
+    cb, _ = orc.pq_fit(X[:8000], M, 16, 2, 3)
+    codes = orc.pq_encode(X, cb)
+    ref = orc.ivf_build(X, codes, nlist, 2, 31)
+    idx = pq.IVFIndex.build(dev(X), dev(codes), nlist, iters=2, seed=31, prec="bf16")
+    assert np.array_equal(idx.coarse().cpu().numpy(), ref["coarse"])
+    off, ids, _ = (t.cpu().numpy() for t in idx.lists())
+    assert np.array_equal(off, ref["offsets"]) and np.array_equal(ids, ref["ids"])
+
+
 @pytest.mark.parametrize("nprobe,k", [(1, 1), (4, 10), (8, 100), (48, 50)])
 def test_search_matches_oracle(pq, setup, nprobe, k):
     ref_ids, ref_d, _ = orc.ivf_search(setup["ref"], setup["cb"], setup["Q"], nprobe, k)
