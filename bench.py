@@ -1,10 +1,12 @@
 """Benchmark of the PQ + IVF-ADC hot path on one GB300 (or N replicas).
 
-One step = the whole path over the medium workload (1M x 128 integer-valued
-mixture, M=16, Ks=256): PQ fit (k-means++ seeding + 25 Lloyd iterations),
-encode with the reconstruction error, inverted-index build (coarse k-means
+Default workload (1M x 128 integer-valued mixture, M=16, Ks=256): one step is
+the whole path -- PQ fit (k-means++ seeding + 25 Lloyd iterations), encode
+with the reconstruction error, inverted-index build (coarse k-means
 nlist=1024, 25 iterations, bucketing) and the IVF-ADC query of 10,000 queries
-(nprobe=16, top-100).
+(nprobe=16, top-100).  `--workload pq_10m_d128_m16` times the precision form
+(10M x 128, 20 iterations; fit + encode per step) and `--compare-fp32` adds
+the plain FP32 form of the same fit + encode beside it.
 
 value        fit+encode throughput, Mvec/s = N / (t_fit + t_encode), inputs
              resident in HBM, device time (CUDA events on the launch stream).
@@ -54,6 +56,11 @@ def load_peaks():
 def fp32_peak_tflops(peaks):
     # 152 SMs x 128 FP32 lanes x 2 flop per FFMA x max SM clock
     return SMS * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+
+
+def compare_peak_t(peaks):
+    # 152 SMs x 128 FP32 lanes x one FMNMX per lane per clock x max SM clock (Tcmp/s)
+    return SMS * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
 
 
 def source_hash(*names):
@@ -121,21 +128,61 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# algorithmic work per launch of each kernel, for the roofline of the dominant one
+# algorithmic work per launch of each kernel, for the roofline of the dominant one:
+# (bound, work, unit, peak kind)
 def kernel_work(name, w, n_launch_rows):
     D, M, Ks = w.d, w.m, w.ks
     if name == "pq_pass_f32":
-        return "alu", 2.0 * n_launch_rows * Ks * D, "TFLOP/s"
+        # the plain form evaluates every (row, subspace, codeword) distance with Ds FFMAs
+        return "alu", 2.0 * n_launch_rows * Ks * D, "TFLOP/s", "fp32"
     if name == "pq_pass_tc":
-        return "hbm", 4.0 * n_launch_rows * D, "GB/s"
+        # the argmin over Ks tensor-core scores needs one FP32 compare per score
+        return "alu", float(n_launch_rows) * M * Ks, "Tcmp/s", "cmp"
+    if name == "coarse_assign_tc":
+        return "tensor", 2.0 * w.n * w.nlist * D, "TFLOP/s", "bf16_sustained"
     if name == "coarse_assign":
-        return "alu", 2.0 * w.n * w.nlist * D, "TFLOP/s"
+        return "alu", 2.0 * w.n * w.nlist * D, "TFLOP/s", "fp32"
+    if name == "list_mean":
+        return "hbm", float(w.n) * (4 * D + 8), "GB/s", "hbm"
     if name == "adc_scan":
-        # codes of the probed lists (uniform-list expectation) + LUT build inputs
-        return "hbm", float(w.nq) * w.nprobe * (w.n / w.nlist) * M, "GB/s"
-    if name == "kmeanspp":
-        return "alu", None, "TFLOP/s"
-    return None, None, None
+        # codes of the probed lists (uniform-list expectation)
+        return "hbm", float(w.nq) * w.nprobe * (w.n / w.nlist) * M, "GB/s", "hbm"
+    return None, None, None, None
+
+
+def roofline(kern, w, peaks, peak_src):
+    """Roofline record of the kernel with the largest share of the timed region."""
+    if not kern:
+        return None
+    dominant = max(kern, key=lambda n: kern[n]["ms"])
+    k = kern[dominant]
+    avg_s = k["ms"] / max(k["launches"], 1) / 1e3
+    bound, work, unit, kind = kernel_work(dominant, w, w.n)
+    share = k["ms"] / max(sum(v["ms"] for v in kern.values()), 1e-9)
+    if work is None:
+        return {"kernel": dominant, "bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None, "avg_launch_ms": avg_s * 1e3, "share": share}
+    if kind == "hbm":
+        achieved, peak, src = work / avg_s / 1e9, peaks["hbm_gbs"], peak_src
+    elif kind == "bf16_sustained":
+        achieved, peak, src = work / avg_s / 1e12, peaks["bf16_tflops_sustained"], peak_src
+    elif kind == "cmp":
+        achieved, peak = work / avg_s / 1e12, compare_peak_t(peaks)
+        src = "152 SMs x 128 FP32 lanes x 1 compare per clock x max SM clock"
+    else:
+        achieved, peak = work / avg_s / 1e12, fp32_peak_tflops(peaks)
+        src = "152 SMs x 128 FP32 lanes x 2 flop per FFMA x max SM clock"
+    traffic = None
+    try:
+        with open(TRAFFIC_PATH) as f:
+            tr = json.load(f).get(dominant)
+        if tr and tr.get("source_hash") == source_hash(*tr["sources"]) and tr.get("workload") == w.name:
+            traffic = tr["bytes_per_launch"]
+    except (OSError, KeyError, ValueError):
+        traffic = None
+    return {"kernel": dominant, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": traffic, "peak_source": src, "avg_launch_ms": avg_s * 1e3,
+            "share": share}
 
 
 def run_gpu(args):
@@ -151,50 +198,61 @@ def run_gpu(args):
     from paper_2604_21645_gb300 import pqgb
 
     w = datagen.WORKLOADS[args.workload]
+    ivf = w.nlist > 0
     prec = args.prec
     X = w.data()
-    Q = w.queries()
     Xd = torch.from_numpy(X).cuda()
-    Qd = torch.from_numpy(Q).cuda()
+    if ivf:
+        Qd = torch.from_numpy(w.queries()).cuda()
+        out_ids = torch.empty((w.nq, w.topk), dtype=torch.int64, device="cuda")
+        out_d = torch.empty((w.nq, w.topk), dtype=torch.float32, device="cuda")
     cbs = torch.empty((w.m, w.ks, w.d // w.m), dtype=torch.float32, device="cuda")
     codes = torch.empty((w.n, w.m), dtype=torch.uint8, device="cuda")
     sse = torch.zeros(1, dtype=torch.float64, device="cuda")
-    out_ids = torch.empty((w.nq, w.topk), dtype=torch.int64, device="cuda")
-    out_d = torch.empty((w.nq, w.topk), dtype=torch.float32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
     stream = torch.cuda.current_stream()
+    names = ["fit", "encode"] + (["ivf_build", "ivf_search"] if ivf else [])
 
-    def step():
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    def step(p=prec, full=True):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
         ev[0].record(stream)
-        pqgb.fit(Xd, w.m, w.ks, iters=w.iters, seed=w.init_seed, prec=prec, out=cbs)
+        pqgb.fit(Xd, w.m, w.ks, iters=w.iters, seed=w.init_seed, prec=p, out=cbs)
         ev[1].record(stream)
-        pqgb.encode(Xd, cbs, prec=prec, out=codes, sse=sse)
+        pqgb.encode(Xd, cbs, prec=p, out=codes, sse=sse)
         ev[2].record(stream)
-        idx = pqgb.IVFIndex.build(Xd, codes, w.nlist, iters=w.ivf_iters, seed=w.coarse_seed, prec=prec)
-        ev[3].record(stream)
-        idx.search(cbs, Qd, w.nprobe, w.topk, out_ids=out_ids, out_d=out_d)
-        ev[4].record(stream)
+        idx = None
+        if ivf and full:
+            idx = pqgb.IVFIndex.build(Xd, codes, w.nlist, iters=w.ivf_iters, seed=w.coarse_seed, prec=p)
+            ev[3].record(stream)
+            idx.search(cbs, Qd, w.nprobe, w.topk, out_ids=out_ids, out_d=out_d)
+            ev[4].record(stream)
         return ev, idx
+
+    def timed(p, full, steps):
+        n = len(names) if full else 2
+        ph = np.zeros(n)
+        for _ in range(steps):
+            flush.zero_()
+            ev, idx = step(p, full)
+            torch.cuda.synchronize()
+            ph += [ev[i].elapsed_time(ev[i + 1]) for i in range(n)]
+            if idx is not None:
+                idx.close()
+        return ph / steps
 
     for _ in range(args.warmup):
         _, idx = step()
-        idx.close()
+        if idx is not None:
+            idx.close()
     torch.cuda.synchronize()
 
-    phases = np.zeros(4)
     launches0 = pqgb.launch_count()
     pqgb.profile_enable(True)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            flush.zero_()
-            ev, idx = step()
-            torch.cuda.synchronize()
-            phases += [ev[i].elapsed_time(ev[i + 1]) for i in range(4)]
-            idx.close()
+        per_step = timed(prec, True, args.steps)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -203,18 +261,27 @@ def run_gpu(args):
     # per-kernel device time inside the timed region (events on the launch stream)
     kern = pqgb.profile_collect()
     pqgb.profile_enable(False)
+    _, rmse = pqgb.decode_rmse(codes, cbs, Xd)
 
-    per_step = phases / args.steps
     t_fe = (per_step[0] + per_step[1]) / 1e3
     t_step = per_step.sum() / 1e3
+    t_search = per_step[3] / 1e3 if ivf else 0.0
     if world > 1:
-        t = torch.tensor([t_fe, t_step, per_step[3] / 1e3], dtype=torch.float64, device="cuda")
+        t = torch.tensor([t_fe, t_step, t_search], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_fe, t_step, t_search = t.tolist()
-    else:
-        t_search = per_step[3] / 1e3
     value = world * w.n / t_fe / 1e6
-    qps = world * w.nq / t_search
+
+    # the plain FP32 form of the same fit + encode, for the precision comparison
+    fp32_form = None
+    if args.compare_fp32 and prec != "fp32":
+        for _ in range(1):
+            step("fp32", False)
+        ph = timed("fp32", False, args.steps)
+        _, rmse32 = pqgb.decode_rmse(codes, cbs, Xd)
+        t32 = (ph[0] + ph[1]) / 1e3
+        fp32_form = {"value": world * w.n / t32 / 1e6, "unit": "Mvec/s", "ms_fit": ph[0], "ms_encode": ph[1],
+                     "rmse": rmse32, "rmse_rel_diff": abs(rmse - rmse32) / rmse32}
 
     # end-to-end through the public API from pinned host buffers (fit + encode)
     Xh = torch.from_numpy(X).pin_memory()
@@ -241,42 +308,14 @@ def run_gpu(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_e2e = t.item()
 
-    _, rmse = pqgb.decode_rmse(codes, cbs, Xd)
-
-    # roofline of the kernel with the largest share of the timed region
     peaks, peak_src = load_peaks()
-    dominant = max(kern, key=lambda n: kern[n]["ms"]) if kern else None
-    roof = None
-    if dominant:
-        k = kern[dominant]
-        avg_s = k["ms"] / max(k["launches"], 1) / 1e3
-        bound, work, unit = kernel_work(dominant, w, w.n)
-        if work is not None:
-            if bound == "hbm":
-                achieved = work / avg_s / 1e9
-                peak = peaks["hbm_gbs"]
-            elif bound == "tensor":
-                achieved = work / avg_s / 1e12
-                peak = peaks["bf16_tflops_sustained"]
-            else:
-                achieved = work / avg_s / 1e12
-                peak = fp32_peak_tflops(peaks)
-            traffic = None
-            try:
-                with open(TRAFFIC_PATH) as f:
-                    tr = json.load(f).get(dominant)
-                if tr and tr.get("source_hash") == source_hash(*tr["sources"]) and tr.get("workload") == w.name:
-                    traffic = tr["bytes_per_launch"]
-            except (OSError, KeyError, ValueError):
-                traffic = None
-            roof = {"kernel": dominant, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                    "frac": achieved / peak, "traffic": traffic,
-                    "peak_source": (peak_src if bound != "alu" else "152 SMs x 128 FP32 lanes x 2 x max SM clock"),
-                    "avg_launch_ms": avg_s * 1e3,
-                    "share": k["ms"] / max(sum(v["ms"] for v in kern.values()), 1e-9)}
-
+    cfg = {"workload": w.name, "N": w.n, "D": w.d, "M": w.m, "Ks": w.ks, "iters": w.iters}
+    if ivf:
+        cfg.update({"nlist": w.nlist, "ivf_iters": w.ivf_iters, "nq": w.nq, "nprobe": w.nprobe, "topk": w.topk})
+    cfg.update({"prec": prec, "parallelism": f"replicas{world}",
+                "l2": f"256 MB buffer written between steps; X ({X.nbytes // 10**6} MB) exceeds L2"})
     line = {
-        "metric": "PQ fit+encode Mvec/s (medium workload; IVF-ADC queries/s reported beside it)",
+        "metric": "PQ fit+encode Mvec/s" + (" (IVF-ADC queries/s reported beside it)" if ivf else ""),
         "value": value,
         "unit": "Mvec/s",
         "n_gpus": world,
@@ -288,20 +327,20 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f32" if prec == "fp32" else "bf16",
         "data": "synthetic (seeded Gaussian mixture standing in for the paper's data)",
-        "config": {"workload": w.name, "N": w.n, "D": w.d, "M": w.m, "Ks": w.ks, "iters": w.iters,
-                   "nlist": w.nlist, "ivf_iters": w.ivf_iters, "nq": w.nq, "nprobe": w.nprobe, "topk": w.topk,
-                   "prec": prec, "parallelism": f"replicas{world}",
-                   "l2": "256 MB buffer written between steps; X (512 MB) exceeds L2"},
-        "phases_ms": {"fit": per_step[0], "encode": per_step[1], "ivf_build": per_step[2], "ivf_search": per_step[3]},
-        "queries_per_s": qps,
+        "config": cfg,
+        "phases_ms": dict(zip(names, per_step.tolist())),
         "rmse": rmse,
         "e2e": {"value": world * w.n / t_e2e / 1e6, "unit": "Mvec/s", "h2d_bytes_per_step": int(X.nbytes),
                 "d2h_bytes_per_step": int(codes.numel() + cbs.numel() * 4)},
         "gpu_launches": int(launches),
         "kernels": kern,
-        "roofline": roof,
+        "roofline": roofline(kern, w, peaks, peak_src),
         "clocks": clk.summary(),
     }
+    if ivf:
+        line["queries_per_s"] = world * w.nq / t_search
+    if fp32_form:
+        line["fp32_form"] = fp32_form
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_rows)
     if rank == 0:
@@ -342,7 +381,7 @@ def run_reference(args):
     v = rows / t / 1e6
     print(json.dumps({
         "impl": "reference",
-        "metric": "PQ fit+encode Mvec/s (medium workload; IVF-ADC queries/s reported beside it)",
+        "metric": "PQ fit+encode Mvec/s" + (" (IVF-ADC queries/s reported beside it)" if w.nlist else ""),
         "value": v, "unit": "Mvec/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded Gaussian mixture standing in for the paper's data)",
@@ -360,8 +399,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default=datagen.IVF_MEDIUM.name, choices=[datagen.IVF_MEDIUM.name])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--workload", default=datagen.IVF_MEDIUM.name, choices=[datagen.IVF_MEDIUM.name,
+                                                                            datagen.PQ_10M.name])
+    ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--compare-fp32", action="store_true", help="also time the plain FP32 form of fit + encode")
     ap.add_argument("--cpu-rows", type=int, default=50_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

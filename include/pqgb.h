@@ -167,6 +167,29 @@ int pq_fit_chunked(const float *X, const int64_t *chunk_offsets, int32_t n_chunk
                    int32_t iters, uint64_t seed, int32_t prec, float *codebooks, uint8_t *codes, double *rmse,
                    void *stream);
 
+/*
+ * softpq_forward / softpq_backward -- soft-assignment reconstruction loss for
+ * codebook refinement, the differentiable relaxation of the hard assignment of
+ * Sec. 2.1:
+ *     p_k = softmax_k(-||x_m - c_{m,k}||^2 / tau),  xh_m = sum_k p_k c_{m,k},
+ *     L   = (1/N) sum_n sum_m ||xh_m - x_m||^2.
+ *   X          [N][D] float32 rows (device, 16-byte aligned), N >= 0.
+ *   codebooks  [M][Ks][Ds] float32 (device), 1 <= Ks <= 256, Ds = D/M in {4, 8, 16}.
+ *   tau        temperature, > 0.
+ *   loss       device float [1] receiving L (0 for N = 0).
+ *   grad_loss  device float [1] holding dOut/dL (the upstream gradient), or NULL for 1.
+ *   dcodebooks [M][Ks][Ds] device output dOut/dC (overwritten).
+ *   dX         [N][D] device output dOut/dX (overwritten, 16-byte aligned), or NULL.
+ * FP32 arithmetic; the backward pass recomputes the soft assignments from X and
+ * the codebooks (nothing is carried over from the forward call).  Neither call
+ * synchronizes.  Errors: PQ_EINVAL for bad shapes, pointers or tau; PQ_ENOTSUP
+ * for an unsupported Ds.
+ */
+int softpq_forward(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, const float *codebooks, float tau,
+                   float *loss, void *stream);
+int softpq_backward(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, const float *codebooks, float tau,
+                    const float *grad_loss, float *dcodebooks, float *dX, void *stream);
+
 /* Opaque inverted-file index, allocated by ivf_build and owned by the library until ivf_free. */
 typedef struct ivf_index ivf_index;
 

@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <cmath>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -358,6 +360,38 @@ int pq_fit_chunked(const float *X, const int64_t *chunk_offsets, int32_t n_chunk
     if ((int64_t)n_chunks * Ks < Ks) return fail(PQ_EINVAL, "empty centroid dataset");
     return run_pq_fit_chunked(X, chunk_offsets, n_chunks, D, M, Ks, iters, seed, prec, codebooks, codes, rmse,
                               static_cast<cudaStream_t>(stream));
+}
+
+static int check_softpq(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, const float *codebooks, float tau)
+{
+    if (!codebooks || (N > 0 && !X)) return fail(PQ_EINVAL, "null pointer");
+    if (N < 0) return fail(PQ_EINVAL, "N=%lld must be >= 0", (long long)N);
+    if (D <= 0 || M <= 0 || D % M != 0) return fail(PQ_EINVAL, "D=%d must be a positive multiple of M=%d", D, M);
+    if (Ks < 1 || Ks > 256) return fail(PQ_EINVAL, "Ks=%d must be in [1, 256]", Ks);
+    if (!(tau > 0.0f) || !std::isfinite(tau)) return fail(PQ_EINVAL, "tau must be positive and finite");
+    if (!softpq_supported(D, M)) return fail(PQ_ENOTSUP, "soft PQ supports D/M in {4, 8, 16}");
+    if (N > 0 && !aligned16(X)) return fail(PQ_EINVAL, "X must be 16-byte aligned");
+    return PQ_OK;
+}
+
+int softpq_forward(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, const float *codebooks, float tau,
+                   float *loss, void *stream)
+{
+    g_msg[0] = 0;
+    PQ_TRY(check_softpq(X, N, D, M, Ks, codebooks, tau));
+    if (!loss) return fail(PQ_EINVAL, "null loss");
+    return run_softpq_forward(X, N, D, M, Ks, codebooks, tau, loss, static_cast<cudaStream_t>(stream));
+}
+
+int softpq_backward(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, const float *codebooks, float tau,
+                    const float *grad_loss, float *dcodebooks, float *dX, void *stream)
+{
+    g_msg[0] = 0;
+    PQ_TRY(check_softpq(X, N, D, M, Ks, codebooks, tau));
+    if (!dcodebooks) return fail(PQ_EINVAL, "null dcodebooks");
+    if (dX && !aligned16(dX)) return fail(PQ_EINVAL, "dX must be 16-byte aligned");
+    return run_softpq_backward(X, N, D, M, Ks, codebooks, tau, grad_loss, dcodebooks, dX,
+                               static_cast<cudaStream_t>(stream));
 }
 
 int ivf_build(const float *X, const uint8_t *codes, int64_t N, int32_t D, int32_t M, int32_t nlist, int32_t iters,

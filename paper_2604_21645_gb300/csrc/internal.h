@@ -117,4 +117,11 @@ struct SearchArgs {
 };
 int run_search(const SearchArgs &a, Scratch &ws, cudaStream_t s);
 
+// ---- soft-assignment PQ loss and gradients (softpq.cu) --------------------
+bool softpq_supported(int D, int M);
+int run_softpq_forward(const float *X, int64_t N, int D, int M, int Ks, const float *C, float tau, float *loss,
+                       cudaStream_t s);
+int run_softpq_backward(const float *X, int64_t N, int D, int M, int Ks, const float *C, float tau,
+                        const float *grad_loss, float *dC, float *dX, cudaStream_t s);
+
 }  // namespace pqgb

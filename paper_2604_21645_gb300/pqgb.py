@@ -22,7 +22,8 @@ PREC = {"fp32": PQ_PREC_FP32, "bf16": PQ_PREC_BF16}
 STATS_MAX_ITERS = 64
 EXPORTS = ("pq_fit", "pq_init_kmeanspp", "pq_encode", "pq_decode_rmse", "ivf_build", "ivf_search", "ivf_get_info",
            "ivf_copy_coarse", "ivf_copy_lists", "ivf_free", "pq_sync_status", "pq_last_error", "pq_launch_count",
-           "pq_profile_enable", "pq_profile_collect", "pq_profile_names", "pq_lloyd_noalloc", "pq_fit_chunked")
+           "pq_profile_enable", "pq_profile_collect", "pq_profile_names", "pq_lloyd_noalloc", "pq_fit_chunked",
+           "softpq_forward", "softpq_backward")
 
 
 class PqStats(C.Structure):
@@ -65,6 +66,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "pq_profile_names": (i32, [C.c_char_p, i32]),
         "pq_lloyd_noalloc": (i32, [p, i64, i32, i32, i32, i32, p, p, p]),
         "pq_fit_chunked": (i32, [p, C.POINTER(i64), i32, i32, i32, i32, i32, u64, i32, p, p, C.POINTER(dbl), p]),
+        "softpq_forward": (i32, [p, i64, i32, i32, i32, p, C.c_float, p, p]),
+        "softpq_backward": (i32, [p, i64, i32, i32, i32, p, C.c_float, p, p, p, p]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -196,6 +199,36 @@ def fit_chunked(X: torch.Tensor, chunk_offsets, M: int, Ks: int = 256, iters: in
                                    C.c_void_p(cb.data_ptr()), C.c_void_p(codes.data_ptr()),
                                    C.byref(r) if want_rmse else None, _stream(X)))
     return cb, codes, (r.value if want_rmse else None)
+
+
+def softpq_forward(X: torch.Tensor, codebooks: torch.Tensor, tau: float, out: torch.Tensor | None = None):
+    """Soft-assignment reconstruction loss L (device float32 scalar); see softpq.SoftPQLoss."""
+    px = _need(X, torch.float32, 2, "X")
+    pc = _need(codebooks, torch.float32, 3, "codebooks")
+    N, D = X.shape
+    M, Ks, _ = codebooks.shape
+    if out is None:
+        out = torch.empty((), dtype=torch.float32, device=X.device)
+    po = _need(out, torch.float32, 0, "loss")
+    with torch.cuda.device(X.device):
+        _check(_lib.softpq_forward(px, N, D, M, Ks, pc, float(tau), po, _stream(X)))
+    return out
+
+
+def softpq_backward(X: torch.Tensor, codebooks: torch.Tensor, tau: float, grad_loss: torch.Tensor | None = None,
+                    need_dx: bool = True):
+    """(dL/dcodebooks, dL/dX or None), scaled by the device scalar ``grad_loss`` when given."""
+    px = _need(X, torch.float32, 2, "X")
+    pc = _need(codebooks, torch.float32, 3, "codebooks")
+    N, D = X.shape
+    M, Ks, _ = codebooks.shape
+    pg = _need(grad_loss, torch.float32, 0, "grad_loss") if grad_loss is not None else None
+    dC = torch.empty_like(codebooks)
+    dX = torch.empty_like(X) if need_dx else None
+    with torch.cuda.device(X.device):
+        _check(_lib.softpq_backward(px, N, D, M, Ks, pc, float(tau), pg, C.c_void_p(dC.data_ptr()),
+                                    C.c_void_p(dX.data_ptr()) if dX is not None else None, _stream(X)))
+    return dC, dX
 
 
 def encode(X: torch.Tensor, codebooks: torch.Tensor, prec: str = "fp32", out: torch.Tensor | None = None,
