@@ -152,7 +152,7 @@ int run_pass(PqPass &p, int prec, cudaStream_t s)
 {
     if (prec == PQ_PREC_BF16) {
         if (!tc_pass_supported(p.D, p.M, p.Ks))
-            return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and M a multiple of 4");
+            return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and M even");
         return launch_pq_pass_tc(p, s);
     }
     return launch_pq_pass_f32(p, s);
@@ -232,7 +232,7 @@ int pq_fit(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, int32_t 
     if (iters < 0 || iters > PQ_STATS_MAX_ITERS) return fail(PQ_EINVAL, "iters=%d must be in [0, %d]", iters,
                                                              PQ_STATS_MAX_ITERS);
     if (prec == PQ_PREC_BF16 && !tc_pass_supported(D, M, Ks))
-        return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and M a multiple of 4");
+        return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and M even");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t l0 = g_launches.load();
     int dev = 0;
@@ -279,7 +279,7 @@ int pq_encode(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, const
     if (!codebooks || (N > 0 && (!X || !codes))) return fail(PQ_EINVAL, "null pointer");
     if (N > 0 && !aligned16(X)) return fail(PQ_EINVAL, "X must be 16-byte aligned");
     if (prec == PQ_PREC_BF16 && !tc_pass_supported(D, M, Ks))
-        return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and M a multiple of 4");
+        return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and M even");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t l0 = g_launches.load();
     if (sse) PQ_TRY_CUDA(cudaMemsetAsync(sse, 0, sizeof(double), s));
@@ -356,7 +356,7 @@ int pq_fit_chunked(const float *X, const int64_t *chunk_offsets, int32_t n_chunk
     if (iters < 0 || iters > PQ_STATS_MAX_ITERS) return fail(PQ_EINVAL, "iters=%d must be in [0, %d]", iters,
                                                              PQ_STATS_MAX_ITERS);
     if (prec == PQ_PREC_BF16 && !tc_pass_supported(D, M, Ks))
-        return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and M a multiple of 4");
+        return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and M even");
     if ((int64_t)n_chunks * Ks < Ks) return fail(PQ_EINVAL, "empty centroid dataset");
     return run_pq_fit_chunked(X, chunk_offsets, n_chunks, D, M, Ks, iters, seed, prec, codebooks, codes, rmse,
                               static_cast<cudaStream_t>(stream));

@@ -93,7 +93,7 @@ int run_pq_fit_chunked(const float *X, const int64_t *off, int n_chunks, int D, 
     PqPass base;
     base.N = N;
     base.M = M;
-    const int per = tc ? std::max(1, sms / std::max(1, M / 4)) : pq_pass_blocks_per_subspace(base);
+    const int per = tc ? std::max(1, sms / std::max(1, M / tc_pass_group())) : pq_pass_blocks_per_subspace(base);
     for (int c = 0; c <= n_chunks; ++c) tp.off[c] = off[c];
     for (int c = 0; c < n_chunks; ++c) {
         const int64_t rows = off[c + 1] - off[c];

@@ -138,7 +138,17 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar)
                    "=f"(v[22]), "=f"(v[23]), "=f"(v[24]), "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]),       \
                    "=f"(v[29]), "=f"(v[30]), "=f"(v[31])                                                            \
                  : "r"(base))
-__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// tcgen05.ld writes its registers asynchronously: the wait names them as in/out operands so that
+// the compiler cannot move a use of the loaded values above it.
+#define TC_WAIT32(v)                                                                                              \
+    asm volatile("tcgen05.wait::ld.sync.aligned;"                                                                 \
+                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]),  \
+                   "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]),         \
+                   "+f"(v[15]), "+f"(v[16]), "+f"(v[17]), "+f"(v[18]), "+f"(v[19]), "+f"(v[20]), "+f"(v[21]),       \
+                   "+f"(v[22]), "+f"(v[23]), "+f"(v[24]), "+f"(v[25]), "+f"(v[26]), "+f"(v[27]), "+f"(v[28]),       \
+                   "+f"(v[29]), "+f"(v[30]), "+f"(v[31])                                                            \
+                 :                                                                                                \
+                 : "memory")
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -391,7 +401,8 @@ __global__ void __launch_bounds__(kThreads, 1) coarse_tc_kernel(const __grid_con
                     float v2[2][32];
                     TC_LD32(tb + (uint32_t)(cp * 64), v2[0]);
                     TC_LD32(tb + (uint32_t)(cp * 64 + 32), v2[1]);
-                    tc_wait_ld();
+                    TC_WAIT32(v2[0]);
+                    TC_WAIT32(v2[1]);
 #pragma unroll
                     for (int hh = 0; hh < 2; ++hh) {
                         const float *vv = v2[hh];

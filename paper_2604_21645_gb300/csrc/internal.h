@@ -69,6 +69,7 @@ int launch_decode_rmse(const uint8_t *codes, const float *C, const float *X, int
 
 // ---- PQ Lloyd pass, BF16 tcgen05 form (lloyd_tc.cu) ------------------------
 bool tc_pass_supported(int D, int M, int Ks);
+int tc_pass_group();  // subspaces per CTA of the tensor-core pass
 int pq_pass_tc_blocks(const PqPass &p);
 // writes per-CTA residual sums (x - c_code) into p.part; finalise with the residual kernel
 int launch_pq_pass_tc(PqPass &p, cudaStream_t s);

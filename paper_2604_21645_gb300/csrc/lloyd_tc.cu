@@ -3,10 +3,11 @@
 // FP32 accumulation in tensor memory.
 //
 // Contraction.  Per subspace the scores S_k = x.c_k - ||c_k||^2/2 (argmax S_k
-// == argmin ||x - c_k||^2) come from one M=128 x N=256 MMA over K=32 bf16
-// lanes.  Both sides are first centred by the subspace's codeword mean mu
-// (distances are translation invariant) and split into bf16 high and low
-// parts, x' = xh + xl, c' = ch + cl, n' = ||c'||^2/2 = nh + nl:
+// == argmin ||x - c_k||^2) come from M=128 x N=128 MMAs over K=32 bf16 lanes,
+// one for each half of the 256 codewords.  Both sides are first centred by the
+// subspace's codeword mean mu (distances are translation invariant) and split
+// into bf16 high and low parts, x' = xh + xl, c' = ch + cl,
+// n' = ||c'||^2/2 = nh + nl:
 //     A row  = [xh(8) xl(8) | xh(8) 1 1 0..]
 //     B row  = [ch(8) ch(8) | cl(8) -nh -nl 0..]
 //     S      = xh.ch + xl.ch + xh.cl - nh - nl
@@ -19,30 +20,35 @@
 // Decision.  The epilogue reads each row's 256 scores from TMEM in chunks of
 // 32, keeps the eight chunk maxima and the values of the best chunk, and
 // accepts the argmax when no other score lies within twice the error bound of
-// it.  For the other rows the complete candidate set -- every score within
-// the bound, from the saved chunk and from any chunk whose maximum reaches the
-// bound (re-read from TMEM) -- is re-ranked exactly: FP32 direct differences,
-// then FP64 among the FP32 near-ties, the decision rule of the CPU reference.
+// it.  For the other rows (about 0.2% on clustered data) every codeword that
+// may be the nearest -- the saved chunk's scores within the bound, and all
+// codewords of any other chunk whose maximum reaches it -- is re-ranked exactly
+// from the FP32 codebook copy in shared memory: FP32 direct differences, then
+// FP64 among the FP32 near-ties, the decision rule of the CPU reference.
 // Codes are exact.
 //
 // Update.  Residuals x - c_code are added with shared-memory FP32 atomics into
 // per-CTA sums; the finalise kernel adds the CTAs in a fixed order in FP64 and
 // moves every codeword by the mean residual of its members.
 //
-// Pipeline (one CTA per SM, one group of 4 subspaces, persistent over row
-// tiles of 128): warp 0 issues TMA loads of 128 x 32 float tiles (128B swizzle)
-// into two stages; two lanes of warp 1 issue the MMAs; warps 2-9 form two
-// warpgroups (thread = row = TMEM lane), warpgroup w handling subspaces 2w and
-// 2w+1 of every tile with its own TMEM accumulator and a double-buffered A
-// operand.  All hand-offs are mbarriers; every wait is bounded, and a
-// timed-out wait records PQ_ETIMEOUT and lets the CTA unwind (its copies
-// waited for, its tensor memory freed).
+// Pipeline (one CTA per SM, a group of 2 subspaces, persistent over row tiles
+// of 128).  Warp 0 issues TMA loads of 128 x 16 float tiles (64B swizzle) into
+// three stages.  Warp 3 (the operand warp) turns each tile into the bf16 A
+// operands of both subspaces (two A stages).  Warps 1 and 2 issue the MMAs of
+// subspace 0 and 1.  Warps 4-7 and 8-11 (the epilogue
+// warpgroups; thread = row = TMEM lane) own subspace 0 and 1 and two 128-column
+// TMEM buffers each, one per codeword half: the MMA of a half is issued as soon
+// as the epilogue has read the same half of the previous tile, so the tensor
+// core works while the epilogue runs.  All hand-offs are mbarriers; every wait
+// is bounded, and a timed-out wait records PQ_ETIMEOUT and lets the CTA unwind
+// (its copies and MMAs waited for, its tensor memory freed).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
 #include <cfloat>
+#include <climits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -50,42 +56,54 @@
 namespace pqgb {
 namespace {
 
-constexpr int G = 4;        // subspaces per CTA
+constexpr int G = 2;        // subspaces per CTA
 constexpr int TM = 128;     // rows per tile
-constexpr int KSMAX = 256;  // codewords (MMA N)
+constexpr int KSMAX = 256;  // codewords
+constexpr int NH = 128;     // codewords per MMA (one TMEM buffer)
 constexpr int DS = 8;       // subspace width
-constexpr int kCompute = 256;              // two warpgroups
-constexpr int kThreads = 64 + kCompute;    // + producer warp + MMA warp
+constexpr int NXS = 3;      // X stages
+constexpr int NAS = 2;      // A stages
+// Warps per block must keep ceil(warps / 4) * 32 * registers within one SM sub-partition's
+// 16K registers: 12 warps leave room for the epilogue's double-buffered TMEM loads.
+constexpr int kOpWarps = 1;                         // operand warps
+constexpr int kOpRows = TM / (32 * kOpWarps);       // rows per operand thread
+constexpr int kThreads = 96 + 32 * kOpWarps + 256;  // TMA warp, two MMA warps, operand warps, two epilogue warpgroups
+constexpr int kOp0 = 96;                            // first operand thread
+constexpr int kEpi0 = kOp0 + 32 * kOpWarps;         // first epilogue thread
 
-constexpr int XS_BYTES = TM * G * DS * 4;            // 16 KB per stage
-constexpr int A_HALF = TM * 16 * 2;                  // 4 KB (K = 16 bf16)
-constexpr int B_HALF = KSMAX * 16 * 2;               // 8 KB
+constexpr int XS_BYTES = TM * G * DS * 4;  // 8 KB per stage (rows of 64 B)
+constexpr int A_K16 = TM * 16 * 2;         // 4 KB: 128 rows x K=16 bf16
+constexpr int A_SUB = 2 * A_K16;           // K = 32
+constexpr int B_K16 = KSMAX * 16 * 2;      // 8 KB: 256 codewords x K=16
+constexpr int B_SUB = 2 * B_K16;
+constexpr int CB_STRIDE = 12;  // FP32 codeword rows: 16-byte aligned, spread over bank groups
+constexpr int ACC_STRIDE = 9;  // update sums: conflict-free scalar atomics
 constexpr int OFF_XS = 0;
-constexpr int OFF_A = OFF_XS + 2 * XS_BYTES;                // [wg][buf][half]
-constexpr int OFF_B = OFF_A + 2 * 2 * 2 * A_HALF;           // [g][half]
-// Row strides of the FP32 codeword copy (12 floats: 16-byte aligned rows that fall on different
-// bank groups for random codes) and of the update sums (9 floats: conflict-free scalar atomics).
-constexpr int CB_STRIDE = 12;
-constexpr int ACC_STRIDE = 9;
-constexpr int OFF_CBF = OFF_B + G * 2 * B_HALF;
-constexpr int OFF_CN = OFF_CBF + G * KSMAX * CB_STRIDE * 4;
-constexpr int OFF_ACC = OFF_CN + G * KSMAX * 4;
+constexpr int OFF_A = OFF_XS + NXS * XS_BYTES;  // [stage][g]
+constexpr int OFF_B = OFF_A + NAS * G * A_SUB;  // [g]
+constexpr int OFF_CBF = OFF_B + G * B_SUB;
+constexpr int OFF_ACC = OFF_CBF + G * KSMAX * CB_STRIDE * 4;
 constexpr int OFF_CNT = OFF_ACC + G * KSMAX * ACC_STRIDE * 4;
-constexpr int OFF_MISC = OFF_CNT + G * KSMAX * 4;
+constexpr int OFF_SV = OFF_CNT + G * KSMAX * 4;        // [256 epilogue threads][32] best-chunk scores
+constexpr int OFF_MISC = OFF_SV + 256 * 32 * 4;
 constexpr int MISC_BYTES = 512;
 constexpr int SMEM_BYTES = OFF_MISC + MISC_BYTES + 1024;  // + alignment slack
 
 // mbarrier slots in the misc area
-constexpr int MB_FULL = 0;      // [2] TMA -> compute
-constexpr int MB_EMPTY = 2;     // [2] compute -> producer (8 warps)
-constexpr int MB_AREADY = 4;    // [2] per warpgroup: compute -> MMA (4 warps)
-constexpr int MB_MMA = 6;       // [2] per warpgroup: MMA -> compute (commit)
-constexpr int MB_TFREE = 8;     // [2] per warpgroup: compute -> MMA (4 warps)
-constexpr int MB_COUNT = 10;
+constexpr int MB_FULL = 0;     // [NXS]  TMA -> operand + epilogue warps
+constexpr int MB_EMPTY = 3;    // [NXS]  12 warps -> TMA
+constexpr int MB_AREADY = 6;   // [NAS][G] operand warpgroup (4 warps) -> MMA lane g
+constexpr int MB_AFREE = 10;   // [NAS][G] MMA completion -> operand warpgroup
+constexpr int MB_MMAF = 14;    // [G][2]  MMA completion of a half -> epilogue warpgroup g
+constexpr int MB_TFREE = 18;   // [G][2]  epilogue warpgroup g (4 warps) -> MMA lane g
+constexpr int MB_DRAIN = 22;   // [G]     final commit of MMA lane g
+constexpr int MB_COUNT = 24;
+constexpr int MISC_TSLOT = 8 * MB_COUNT;  // 192
+constexpr int MISC_MU = 256;              // [G][8] floats
+constexpr int MISC_BND = 320;             // [G][4] float bits
 
 constexpr float kC1 = 7.5e-5f;
 constexpr float kC2 = 2.7e-5f;
-constexpr int kMaxCand = 32;
 
 struct TcArgs {
     int64_t N;
@@ -167,8 +185,8 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
 // byte offset of element (row, k) in a K=16 operand tile
 __device__ __forceinline__ uint32_t core_off(int r, int k) { return (r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
 
-// kind::f16, D = f32, A = B = bf16, both K-major, N = 256, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(KSMAX >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+// kind::f16, D = f32, A = B = bf16, both K-major, N = 128, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NH >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate)
 {
@@ -192,7 +210,17 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar)
                    "=f"(v[22]), "=f"(v[23]), "=f"(v[24]), "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]),       \
                    "=f"(v[29]), "=f"(v[30]), "=f"(v[31])                                                            \
                  : "r"(base))
-__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// tcgen05.ld writes its registers asynchronously: the wait names them as in/out operands so that
+// the compiler cannot move a use of the loaded values above it.
+#define TC_WAIT32(v)                                                                                              \
+    asm volatile("tcgen05.wait::ld.sync.aligned;"                                                                 \
+                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]),  \
+                   "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]),         \
+                   "+f"(v[15]), "+f"(v[16]), "+f"(v[17]), "+f"(v[18]), "+f"(v[19]), "+f"(v[20]), "+f"(v[21]),       \
+                   "+f"(v[22]), "+f"(v[23]), "+f"(v[24]), "+f"(v[25]), "+f"(v[26]), "+f"(v[27]), "+f"(v[28]),       \
+                   "+f"(v[29]), "+f"(v[30]), "+f"(v[31])                                                            \
+                 :                                                                                                \
+                 : "memory")
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
@@ -200,87 +228,80 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
-// float chunk (16 B) of row r in a 128B-swizzled TMA stage (row = 128 bytes)
-__device__ __forceinline__ const float *xs_row_chunk(const float *stage, int r, int chunk)
+// 16-byte chunk c (0..3) of row r in a 64B-swizzled TMA stage (row = 64 bytes)
+__device__ __forceinline__ const float4 *xs_chunk(const float *stage, int r, int c)
 {
-    return stage + r * 32 + ((chunk ^ (r & 7)) << 2);
+    return reinterpret_cast<const float4 *>(stage + r * 16 + ((c ^ ((r >> 1) & 3)) << 2));
 }
 
-// Exact decision over all codewords (used only if a row has more than kMaxCand
-// candidates): FP32 expansion scores with their error bound, then FP64 inside it.
-__device__ __forceinline__ int exact_code(const float *x, const float *cb, const float *cn, int Ks, float nmax,
-                                       float cmax)
-{
-    float xx = 0.0f;
-#pragma unroll
-    for (int j = 0; j < DS; ++j) xx = fmaf(x[j], x[j], xx);
-    const float xn = sqrtf(xx) * (1.0f + 1e-6f);
-    float m1 = FLT_MAX, m2 = FLT_MAX;
-    int i1 = 0;
-    for (int k = 0; k < Ks; ++k) {
-        float s = cn[k];
-#pragma unroll
-        for (int j = 0; j < DS; ++j) s = fmaf(-x[j], cb[k * CB_STRIDE + j], s);
-        const bool lt = s < m1;
-        m2 = lt ? m1 : fminf(m2, s);
-        i1 = lt ? k : i1;
-        m1 = fminf(m1, s);
-    }
-    const float t = xn + cmax;
-    const float win = 2.0f * (2.2f * gamma_f32(DS + 1) * (nmax + xn * cmax) + 1e-13f * t * t);
-    if (m2 - m1 > win) return i1;
-    double best = DBL_MAX;
-    int bk = 0;
-    for (int k = 0; k < Ks; ++k) {
-        float s = cn[k];
-#pragma unroll
-        for (int j = 0; j < DS; ++j) s = fmaf(-x[j], cb[k * CB_STRIDE + j], s);
-        if (s <= m1 + win) {
-            const double d = d2_fp64(x, cb + k * CB_STRIDE, DS);
-            if (d < best) { best = d; bk = k; }
-        }
-    }
-    return bk;
-}
-
-// Exact decision among a complete candidate list: FP32 direct differences (relative error
-// below 1e-6 for Ds = 8), then FP64 among the FP32 near-ties; ties to the lowest index.
-__device__ __forceinline__ int rerank(const float *x, const float *cb, const int *cand, int nc)
-{
+// Running top-2 of FP32 direct distances over candidate codewords (ties to the lowest index).
+struct Top2 {
     float d1 = FLT_MAX, d2 = FLT_MAX;
-    int k1 = 0x7fffffff;
-    for (int i = 0; i < nc; ++i) {
-        const float *c = cb + cand[i] * CB_STRIDE;
-        float d = 0.0f;
-#pragma unroll
-        for (int j = 0; j < DS; ++j) {
-            const float t = x[j] - c[j];
-            d = fmaf(t, t, d);
+    int k1 = INT_MAX;
+    __device__ __forceinline__ void add(float d, int k)
+    {
+        if (d < d1 || (d == d1 && k < k1)) {
+            d2 = d1;
+            d1 = d;
+            k1 = k;
+        } else if (d < d2) {
+            d2 = d;
         }
-        if (d < d1 || (d == d1 && cand[i] < k1)) { d2 = d1; d1 = d; k1 = cand[i]; }
-        else if (d < d2) { d2 = d; }
     }
-    const float margin = 4e-6f * d2 + 1e-30f;
-    if (d2 - d1 > margin) return k1;
-    double best = DBL_MAX;
-    int bk = 0x7fffffff;
-    for (int i = 0; i < nc; ++i) {
-        const float *c = cb + cand[i] * CB_STRIDE;
-        float d = 0.0f;
+};
+__device__ __forceinline__ float d2_fp32(const float *x, const float *c)
+{
+    float d = 0.0f;
 #pragma unroll
-        for (int j = 0; j < DS; ++j) {
-            const float t = x[j] - c[j];
-            d = fmaf(t, t, d);
-        }
-        if (d <= d1 + margin) {
+    for (int j = 0; j < DS; ++j) {
+        const float t = x[j] - c[j];
+        d = fmaf(t, t, d);
+    }
+    return d;
+}
+
+// Exact decision among every codeword that may be the nearest: the codewords of the saved
+// chunk `bestj` whose scores reach the bound (bits of svmask) and all codewords of the
+// chunks in cmask.  FP32 direct differences (relative error below 1e-6 for Ds = 8), then
+// FP64 among the FP32 near-ties; ties to the lowest index -- the decision rule of the CPU
+// reference.  The row comes by value so that the caller's copy stays in registers.
+__device__ __noinline__ int decide_exact(float4 xa, float4 xb, const float *cb, unsigned svmask, int bestj,
+                                         unsigned cmask, int Ks)
+{
+    const float x[DS] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+    Top2 t;
+    for (unsigned m = svmask; m; m &= m - 1) {
+        const int k = bestj * 32 + __ffs(m) - 1;
+        t.add(d2_fp32(x, cb + k * CB_STRIDE), k);
+    }
+    for (unsigned m = cmask; m; m &= m - 1) {
+        const int c = __ffs(m) - 1;
+        for (int k = c * 32; k < c * 32 + 32 && k < Ks; ++k) t.add(d2_fp32(x, cb + k * CB_STRIDE), k);
+    }
+    const float margin = 4e-6f * t.d2 + 1e-30f;
+    if (t.d2 - t.d1 > margin) return t.k1;
+    const float lim = t.d1 + margin;
+    double best = DBL_MAX;
+    int bk = INT_MAX;
+    auto fp64 = [&](int k) {
+        const float *c = cb + k * CB_STRIDE;
+        if (d2_fp32(x, c) <= lim) {
             const double e = d2_fp64(x, c, DS);
-            if (e < best || (e == best && cand[i] < bk)) { best = e; bk = cand[i]; }
+            if (e < best || (e == best && k < bk)) {
+                best = e;
+                bk = k;
+            }
         }
+    };
+    for (unsigned m = svmask; m; m &= m - 1) fp64(bestj * 32 + __ffs(m) - 1);
+    for (unsigned m = cmask; m; m &= m - 1) {
+        const int c = __ffs(m) - 1;
+        for (int k = c * 32; k < c * 32 + 32 && k < Ks; ++k) fp64(k);
     }
     return bk;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_constant__ CUtensorMap tmap,
+__global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                   const TcArgs a)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -306,15 +327,15 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
     unsigned char *aop = sm + OFF_A;
     unsigned char *bop = sm + OFF_B;
     float *cbf = reinterpret_cast<float *>(sm + OFF_CBF);
-    float *cn = reinterpret_cast<float *>(sm + OFF_CN);
     float *acc = reinterpret_cast<float *>(sm + OFF_ACC);
     int *cnt = reinterpret_cast<int *>(sm + OFF_CNT);
     uint64_t *mb = reinterpret_cast<uint64_t *>(sm + OFF_MISC);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + OFF_MISC + 8 * MB_COUNT);
-    float *mu = reinterpret_cast<float *>(sm + OFF_MISC + 128);           // [G][8]
-    unsigned *bnd = reinterpret_cast<unsigned *>(sm + OFF_MISC + 256);    // [G][4] float bits: n', c', n, c maxima
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + OFF_MISC + MISC_TSLOT);
+    float *mu = reinterpret_cast<float *>(sm + OFF_MISC + MISC_MU);
+    unsigned *bnd = reinterpret_cast<unsigned *>(sm + OFF_MISC + MISC_BND);  // [G][2] float bits: n', ||c'|| maxima
+    auto bar = [&](int slot) { return smem_u32(mb + slot); };
 
-    // ---- set-up: codeword mean, B operands, FP32 copies, norms, bounds ------
+    // ---- set-up: codeword mean, B operands, FP32 copies, bounds -------------
     if (tid < G * DS) {
         const int g = tid / DS, j = tid % DS;
         const float *Cm = Cc + (size_t)(m0 + g) * Ks * DS;
@@ -327,7 +348,7 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
     for (int e = tid; e < G * KSMAX; e += kThreads) {
         const int g = e / KSMAX, k = e % KSMAX;
         float c[DS], cc[DS];
-        float nc = 0.0f, n = 0.0f, norm2c = 0.0f;
+        float nc = 0.0f;
         if (k < Ks) {
             const float *src = Cc + ((size_t)(m0 + g) * Ks + k) * DS;
 #pragma unroll
@@ -335,18 +356,15 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
                 c[j] = src[j];
                 cc[j] = c[j] - mu[g * DS + j];
                 nc = fmaf(cc[j], cc[j], nc);
-                n = fmaf(c[j], c[j], n);
             }
-            norm2c = nc;
-            nc *= 0.5f;
-            n *= 0.5f;
         } else {
 #pragma unroll
             for (int j = 0; j < DS; ++j) { c[j] = 0.0f; cc[j] = 0.0f; }
         }
+        const float norm2c = nc;
+        nc *= 0.5f;
 #pragma unroll
         for (int j = 0; j < DS; ++j) cbf[(g * KSMAX + k) * CB_STRIDE + j] = c[j];
-        cn[g * KSMAX + k] = n;
         float ch[DS], cl[DS];
 #pragma unroll
         for (int j = 0; j < DS; ++j) {
@@ -361,8 +379,8 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
             nh = 3.0e38f;  // padding codeword: score -3e38, never the maximum
             nl = 0.0f;
         }
-        unsigned char *b0 = bop + (g * 2 + 0) * B_HALF;
-        unsigned char *b1 = bop + (g * 2 + 1) * B_HALF;
+        unsigned char *b0 = bop + g * B_SUB;
+        unsigned char *b1 = b0 + B_K16;
         const uint4 w = make_uint4(pack_bf16(ch[0], ch[1]), pack_bf16(ch[2], ch[3]), pack_bf16(ch[4], ch[5]),
                                    pack_bf16(ch[6], ch[7]));
         *reinterpret_cast<uint4 *>(b0 + core_off(k, 0)) = w;
@@ -371,10 +389,8 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
             make_uint4(pack_bf16(cl[0], cl[1]), pack_bf16(cl[2], cl[3]), pack_bf16(cl[4], cl[5]), pack_bf16(cl[6], cl[7]));
         *reinterpret_cast<uint4 *>(b1 + core_off(k, 8)) = make_uint4(pack_bf16(-nh, -nl), 0u, 0u, 0u);
         if (k < Ks) {
-            atomicMax(bnd + g * 4 + 0, __float_as_uint(nc));
-            atomicMax(bnd + g * 4 + 1, __float_as_uint(sqrtf(norm2c)));
-            atomicMax(bnd + g * 4 + 2, __float_as_uint(n));
-            atomicMax(bnd + g * 4 + 3, __float_as_uint(sqrtf(2.0f * n)));
+            atomicMax(bnd + g * 2 + 0, __float_as_uint(nc));
+            atomicMax(bnd + g * 2 + 1, __float_as_uint(sqrtf(norm2c)));
         }
         if (fit) {
 #pragma unroll
@@ -382,16 +398,25 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
             cnt[g * KSMAX + k] = 0;
         }
     }
+    // constant K lanes 24..31 of every A stage: [1 1 0 0 0 0 0 0]
+    for (int e = tid; e < NAS * G * TM; e += kThreads) {
+        unsigned char *a1 = aop + (e / TM) * A_SUB + A_K16;
+        *reinterpret_cast<uint4 *>(a1 + core_off(e % TM, 8)) = make_uint4(pack_bf16(1.0f, 1.0f), 0u, 0u, 0u);
+    }
     if (tid == 0) {
-        mbar_init(smem_u32(mb + MB_FULL + 0), 1);
-        mbar_init(smem_u32(mb + MB_FULL + 1), 1);
-        mbar_init(smem_u32(mb + MB_EMPTY + 0), kCompute / 32);
-        mbar_init(smem_u32(mb + MB_EMPTY + 1), kCompute / 32);
-        for (int w = 0; w < 2; ++w) {
-            mbar_init(smem_u32(mb + MB_AREADY + w), 4);
-            mbar_init(smem_u32(mb + MB_MMA + w), 1);
-            mbar_init(smem_u32(mb + MB_TFREE + w), 4);
+        for (int s = 0; s < NXS; ++s) {
+            mbar_init(bar(MB_FULL + s), 1);
+            mbar_init(bar(MB_EMPTY + s), kOpWarps + 8);
         }
+        for (int i = 0; i < NAS * G; ++i) {
+            mbar_init(bar(MB_AREADY + i), kOpWarps);
+            mbar_init(bar(MB_AFREE + i), 1);
+        }
+        for (int i = 0; i < G * 2; ++i) {
+            mbar_init(bar(MB_MMAF + i), 1);
+            mbar_init(bar(MB_TFREE + i), 4);
+        }
+        for (int g = 0; g < G; ++g) mbar_init(bar(MB_DRAIN + g), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -405,91 +430,126 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
     const uint32_t tmem = *tslot;
 
     const int n_my = (tiles_c > lb) ? (tiles_c - 1 - lb) / gxc + 1 : 0;
-    const int wsteps = 2 * n_my;  // steps of each warpgroup
 
     if (warp == 0) {
         // ---- producer: TMA loads of the row tiles -----------------------------
         if (lane == 0) {
             int issued = 0;
             for (int i = 0; i < n_my; ++i) {
-                const int s = i & 1;
-                if (i >= 2 && !mbar_wait(smem_u32(mb + MB_EMPTY + s), ((i >> 1) - 1) & 1, a.err)) break;
-                mbar_expect_tx(smem_u32(mb + MB_FULL + s), XS_BYTES);
+                const int s = i % NXS;
+                if (i >= NXS && !mbar_wait(bar(MB_EMPTY + s), ((i / NXS) - 1) & 1, a.err)) break;
+                mbar_expect_tx(bar(MB_FULL + s), XS_BYTES);
                 tma_load_2d(smem_u32(reinterpret_cast<unsigned char *>(xs) + s * XS_BYTES), &tmap, m0 * DS,
-                            (int)(r0 + (int64_t)(lb + i * gxc) * TM), smem_u32(mb + MB_FULL + s));
+                            (int)(r0 + (int64_t)(lb + i * gxc) * TM), bar(MB_FULL + s));
                 ++issued;
             }
             // our own copies must have landed before the CTA can leave
-            for (int i = (issued > 2 ? issued - 2 : 0); i < issued; ++i)
-                mbar_wait(smem_u32(mb + MB_FULL + (i & 1)), (i >> 1) & 1, a.err);
+            for (int i = (issued > NXS ? issued - NXS : 0); i < issued; ++i)
+                mbar_wait(bar(MB_FULL + i % NXS), (i / NXS) & 1, a.err);
         }
-    } else if (warp == 1) {
-        // ---- MMA issue: lane w serves warpgroup w ------------------------------
-        if (lane < 2) {
-            const int w = lane;
-            for (int u = 0; u < wsteps; ++u) {
-                if (!mbar_wait(smem_u32(mb + MB_AREADY + w), u & 1, a.err)) break;
-                if (u >= 1 && !mbar_wait(smem_u32(mb + MB_TFREE + w), (u - 1) & 1, a.err)) break;
-                tc_after_sync();
-                const int g = 2 * w + (u & 1), buf = u & 1;
-                const uint32_t d = tmem + (uint32_t)(w * KSMAX);
-                const unsigned char *ab = aop + (w * 2 + buf) * 2 * A_HALF;
-                mma_bf16(d, smem_desc(smem_u32(ab)), smem_desc(smem_u32(bop + (g * 2 + 0) * B_HALF)), 0u);
-                mma_bf16(d, smem_desc(smem_u32(ab + A_HALF)), smem_desc(smem_u32(bop + (g * 2 + 1) * B_HALF)), 1u);
-                mma_commit(smem_u32(mb + MB_MMA + w));
-            }
-        }
-    } else {
-        // ---- compute warpgroups: thread = row = TMEM lane --------------------
-        const int w = (warp - 2) >> 2;
-        const int q = warp & 3;
-        const int r = q * 32 + lane;
-        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(w * KSMAX);
-        float nb_prime[2], cb_prime[2], nb_orig[2], cb_orig[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int g = 2 * w + h;
-            nb_prime[h] = __uint_as_float(bnd[g * 4 + 0]) * (1.0f + 1e-5f);
-            cb_prime[h] = __uint_as_float(bnd[g * 4 + 1]) * (1.0f + 1e-5f);
-            nb_orig[h] = __uint_as_float(bnd[g * 4 + 2]) * (1.0f + 4.0f * gamma_f32(DS + 1));
-            cb_orig[h] = __uint_as_float(bnd[g * 4 + 3]) * (1.0f + 1e-5f);
-        }
-        float sse_s = 0.0f, sse_c = 0.0f;  // Kahan pair
-        unsigned rechecks = 0;
-        uint32_t code_pair = 0;
-        for (int u = 0; u < wsteps; ++u) {
-            const int i = u >> 1, h = u & 1, g = 2 * w + h, s = i & 1, buf = u & 1;
-            const int64_t row = r0 + (int64_t)(lb + i * gxc) * TM + r;
-            const float *stage = xs + s * (XS_BYTES / 4);
-            // (a) A operand of this step
-            if (h == 0 && !__all_sync(0xffffffffu, mbar_wait(smem_u32(mb + MB_FULL + s), (i >> 1) & 1, a.err))) break;
-            const float4 v0 = *reinterpret_cast<const float4 *>(xs_row_chunk(stage, r, 2 * g));
-            const float4 v1 = *reinterpret_cast<const float4 *>(xs_row_chunk(stage, r, 2 * g + 1));
-            const float x[DS] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-            {
-                float xh[DS], xl[DS];
-#pragma unroll
-                for (int d = 0; d < DS; ++d) {
-                    const float xc = x[d] - mu[g * DS + d];
-                    xh[d] = __bfloat162float(__float2bfloat16_rn(xc));
-                    xl[d] = xc - xh[d];
+    } else if (warp <= G) {
+        // ---- MMA issue: warp 1 + g serves subspace g (one warp each, so that a wait of
+        // one never holds up the other) --------------------------------------------
+        if (lane == 0) {
+            const int g = warp - 1;
+            for (int i = 0; i < n_my; ++i) {
+                const int as = i & 1;
+                if (!mbar_wait(bar(MB_AREADY + as * G + g), (i >> 1) & 1, a.err)) break;
+                bool ok = true;
+                for (int h = 0; h < 2 && ok; ++h) {
+                    if (i >= 1 && !mbar_wait(bar(MB_TFREE + g * 2 + h), (i - 1) & 1, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_after_sync();
+                    const uint32_t d = tmem + (uint32_t)((g * 2 + h) * NH);
+                    const unsigned char *ab = aop + (as * G + g) * A_SUB;
+                    const unsigned char *bb = bop + g * B_SUB + h * (NH / 8) * 256;
+                    mma_bf16(d, smem_desc(smem_u32(ab)), smem_desc(smem_u32(bb)), 0u);
+                    mma_bf16(d, smem_desc(smem_u32(ab + A_K16)), smem_desc(smem_u32(bb + B_K16)), 1u);
+                    mma_commit(bar(MB_MMAF + g * 2 + h));
                 }
-                unsigned char *a0 = aop + (w * 2 + buf) * 2 * A_HALF;
-                unsigned char *a1 = a0 + A_HALF;
-                const uint4 wh = make_uint4(pack_bf16(xh[0], xh[1]), pack_bf16(xh[2], xh[3]), pack_bf16(xh[4], xh[5]),
-                                            pack_bf16(xh[6], xh[7]));
-                *reinterpret_cast<uint4 *>(a0 + core_off(r, 0)) = wh;
-                *reinterpret_cast<uint4 *>(a0 + core_off(r, 8)) = make_uint4(
-                    pack_bf16(xl[0], xl[1]), pack_bf16(xl[2], xl[3]), pack_bf16(xl[4], xl[5]), pack_bf16(xl[6], xl[7]));
-                *reinterpret_cast<uint4 *>(a1 + core_off(r, 0)) = wh;
-                *reinterpret_cast<uint4 *>(a1 + core_off(r, 8)) = make_uint4(pack_bf16(1.0f, 1.0f), 0u, 0u, 0u);
+                if (!ok) break;
+                mma_commit(bar(MB_AFREE + as * G + g));
             }
+            // every MMA of this lane has completed before the tensor memory is freed
+            mma_commit(bar(MB_DRAIN + g));
+            mbar_wait(bar(MB_DRAIN + g), 0, a.err);
+        }
+    } else if (warp < kEpi0 / 32) {
+        // ---- operand warp: bf16 A operands of both subspaces, rows t + 32 rr
+        const int t = tid - kOp0;
+        for (int i = 0; i < n_my; ++i) {
+            const int s = i % NXS, as = i & 1;
+            if (!__all_sync(0xffffffffu, mbar_wait(bar(MB_FULL + s), (i / NXS) & 1, a.err))) break;
+            const float *stage = xs + s * (XS_BYTES / 4);
+            float4 v[kOpRows][4];
+#pragma unroll
+            for (int rr = 0; rr < kOpRows; ++rr)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) v[rr][c] = *xs_chunk(stage, t + 32 * kOpWarps * rr, c);
             fence_async_smem();
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(mb + MB_AREADY + w));
-            // (b) scores of this step
-            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(mb + MB_MMA + w), u & 1, a.err))) break;
-            tc_after_sync();
+            if (lane == 0) mbar_arrive(bar(MB_EMPTY + s));
+            bool ok = true;
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                if (i >= NAS &&
+                    !__all_sync(0xffffffffu, mbar_wait(bar(MB_AFREE + as * G + g), ((i >> 1) - 1) & 1, a.err))) {
+                    ok = false;
+                    break;
+                }
+                unsigned char *a0 = aop + (as * G + g) * A_SUB;
+#pragma unroll
+                for (int rr = 0; rr < kOpRows; ++rr) {
+                    const int r = t + 32 * kOpWarps * rr;
+                    const float x[DS] = {v[rr][2 * g].x, v[rr][2 * g].y, v[rr][2 * g].z, v[rr][2 * g].w,
+                                         v[rr][2 * g + 1].x, v[rr][2 * g + 1].y, v[rr][2 * g + 1].z, v[rr][2 * g + 1].w};
+                    float xh[DS], xl[DS];
+#pragma unroll
+                    for (int d = 0; d < DS; ++d) {
+                        const float xc = x[d] - mu[g * DS + d];
+                        xh[d] = __bfloat162float(__float2bfloat16_rn(xc));
+                        xl[d] = xc - xh[d];
+                    }
+                    const uint4 wh = make_uint4(pack_bf16(xh[0], xh[1]), pack_bf16(xh[2], xh[3]),
+                                                pack_bf16(xh[4], xh[5]), pack_bf16(xh[6], xh[7]));
+                    *reinterpret_cast<uint4 *>(a0 + core_off(r, 0)) = wh;
+                    *reinterpret_cast<uint4 *>(a0 + core_off(r, 8)) =
+                        make_uint4(pack_bf16(xl[0], xl[1]), pack_bf16(xl[2], xl[3]), pack_bf16(xl[4], xl[5]),
+                                   pack_bf16(xl[6], xl[7]));
+                    *reinterpret_cast<uint4 *>(a0 + A_K16 + core_off(r, 0)) = wh;
+                }
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar(MB_AREADY + as * G + g));
+            }
+            if (!ok) break;
+        }
+    } else {
+        // ---- epilogue warpgroups: thread = row = TMEM lane, warpgroup g = subspace g
+        const int g = (tid - kEpi0) >> 7;
+        const int r = (warp & 3) * 32 + lane;
+        const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(g * 2 * NH);
+        const float nb_prime = __uint_as_float(bnd[g * 2 + 0]) * (1.0f + 1e-5f);
+        const float cb_prime = __uint_as_float(bnd[g * 2 + 1]) * (1.0f + 1e-5f);
+        const float *cbg = cbf + g * KSMAX * CB_STRIDE;
+        const int te = tid - kEpi0;
+        float4 *svs = reinterpret_cast<float4 *>(sm + OFF_SV) + te * 8;  // 16-byte pieces swizzled by te & 7
+        float sse_s = 0.0f, sse_c = 0.0f;  // Kahan pair
+        unsigned rechecks = 0;
+        for (int i = 0; i < n_my; ++i) {
+            const int s = i % NXS;
+            const int64_t row = r0 + (int64_t)(lb + i * gxc) * TM + r;
+            if (!__all_sync(0xffffffffu, mbar_wait(bar(MB_FULL + s), (i / NXS) & 1, a.err))) break;
+            const float *stage = xs + s * (XS_BYTES / 4);
+            const float4 v0 = *xs_chunk(stage, r, 2 * g);
+            const float4 v1 = *xs_chunk(stage, r, 2 * g + 1);
+            // the stage is not read again: order the reads before the TMA that will refill it
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar(MB_EMPTY + s));
+            const float x[DS] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
             float xx = 0.0f;
 #pragma unroll
             for (int d = 0; d < DS; ++d) {
@@ -497,89 +557,89 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
                 xx = fmaf(xc, xc, xx);
             }
             const float xn = sqrtf(xx) * (1.0f + 1e-5f);
-            const float tt = xn + cb_prime[h];
-            const float win = 2.0f * (kC1 * xn * cb_prime[h] + kC2 * nb_prime[h] + 1e-13f * tt * tt);
+            const float tt = xn + cb_prime;
+            const float win = 2.0f * (kC1 * xn * cb_prime + kC2 * nb_prime + 1e-13f * tt * tt);
 
+            // scores, two halves of 128 codewords, each in its own TMEM buffer
             float best = -FLT_MAX, cm2 = -FLT_MAX;
             int bestj = 0;
             float cmx[KSMAX / 32];
-            float sv[32];
+            // chunk j+1 is loaded from TMEM while chunk j is reduced (tcgen05.wait::ld waits for
+            // every outstanding load, so each wait sits after the reduction it overlaps)
+            bool ok = __all_sync(0xffffffffu, mbar_wait(bar(MB_MMAF + g * 2 + 0), i & 1, a.err));
+            if (!ok) break;
+            tc_after_sync();
+            float vb[2][32];
+            TC_LD32(tl, vb[0]);
+            TC_WAIT32(vb[0]);
 #pragma unroll
-            for (int q2 = 0; q2 < 32; ++q2) sv[q2] = -FLT_MAX;
-#pragma unroll 1
-            for (int cp = 0; cp < KSMAX / 64; ++cp) {
-                float v2[2][32];
-                TC_LD32(tl + (uint32_t)(cp * 64), v2[0]);
-                TC_LD32(tl + (uint32_t)(cp * 64 + 32), v2[1]);
-                tc_wait_ld();
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    const float *v = v2[hh];
-                    float m16[16];
-#pragma unroll
-                    for (int q2 = 0; q2 < 16; ++q2) m16[q2] = fmaxf(v[2 * q2], v[2 * q2 + 1]);
-#pragma unroll
-                    for (int q2 = 0; q2 < 8; ++q2) m16[q2] = fmaxf(m16[2 * q2], m16[2 * q2 + 1]);
-#pragma unroll
-                    for (int q2 = 0; q2 < 4; ++q2) m16[q2] = fmaxf(m16[2 * q2], m16[2 * q2 + 1]);
-                    const float cm = fmaxf(fmaxf(m16[0], m16[1]), fmaxf(m16[2], m16[3]));
-                    cmx[2 * cp + hh] = cm;
-                    const bool better = cm > best;
-                    cm2 = better ? best : fmaxf(cm2, cm);
-                    best = better ? cm : best;
-                    bestj = better ? 2 * cp + hh : bestj;
-#pragma unroll
-                    for (int q2 = 0; q2 < 32; ++q2) sv[q2] = better ? v[q2] : sv[q2];
+            for (int j = 0; j < KSMAX / 32; ++j) {
+                if (j + 1 == NH / 32) {
+                    ok = __all_sync(0xffffffffu, mbar_wait(bar(MB_MMAF + g * 2 + 1), i & 1, a.err));
+                    if (!ok) break;
+                    tc_after_sync();
                 }
+                if (j + 1 < KSMAX / 32) TC_LD32(tl + (uint32_t)((j + 1) * 32), vb[(j + 1) & 1]);
+                const float *v = vb[j & 1];
+                float m16[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) m16[q] = fmaxf(v[2 * q], v[2 * q + 1]);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) m16[q] = fmaxf(m16[2 * q], m16[2 * q + 1]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) m16[q] = fmaxf(m16[2 * q], m16[2 * q + 1]);
+                const float cm = fmaxf(fmaxf(m16[0], m16[1]), fmaxf(m16[2], m16[3]));
+                cmx[j] = cm;
+                const bool better = cm > best;
+                cm2 = better ? best : fmaxf(cm2, cm);
+                best = better ? cm : best;
+                bestj = better ? j : bestj;
+                if (better) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        svs[c ^ (te & 7)] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+                }
+                if (j + 1 == NH / 32) {
+                    // every load of the first buffer has completed: hand it back to the MMA warp
+                    tc_before_sync();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar(MB_TFREE + g * 2 + 0));
+                }
+                if (j + 1 < KSMAX / 32) TC_WAIT32(vb[(j + 1) & 1]);
             }
-            const float theta = best - win;
-            int ib = 0, nin = 0;
-#pragma unroll
-            for (int q2 = 31; q2 >= 0; --q2) {
-                ib = (sv[q2] == best) ? q2 : ib;
-                nin += (sv[q2] >= theta) ? 1 : 0;
-            }
-            int code = bestj * 32 + ib;
-            const bool valid = row < r1;
-            const bool unsure = valid && !(nin == 1 && cm2 < theta);
-            if (__any_sync(0xffffffffu, unsure)) {
-                // complete candidate set: the saved chunk, plus every other chunk reaching theta
-                int cand[kMaxCand];
-                int nc = 0;
-                bool over = false;
-                if (unsure) {
-#pragma unroll
-                    for (int q2 = 0; q2 < 32; ++q2)
-                        if (sv[q2] >= theta) cand[nc++] = bestj * 32 + q2;
-                }
-#pragma unroll 1
-                for (int c = 0; c < KSMAX / 32; ++c) {
-                    const bool need = unsure && c != bestj && cmx[c] >= theta;
-                    if (!__any_sync(0xffffffffu, need)) continue;
-                    float v[32];
-                    TC_LD32(tl + (uint32_t)(c * 32), v);
-                    tc_wait_ld();
-                    if (need) {
-#pragma unroll
-                        for (int q2 = 0; q2 < 32; ++q2) {
-                            if (v[q2] >= theta) {
-                                if (nc < kMaxCand) cand[nc++] = c * 32 + q2;
-                                else over = true;
-                            }
-                        }
-                    }
-                }
-                if (unsure) {
-                    const float *cbg = cbf + g * KSMAX * CB_STRIDE;
-                    code = over ? exact_code(x, cbg, cn + g * KSMAX, Ks, nb_orig[h], cb_orig[h]) : rerank(x, cbg, cand, nc);
-                    ++rechecks;
-                }
-            }
+            if (!ok) break;
             tc_before_sync();
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(mb + MB_TFREE + w));
+            if (lane == 0) mbar_arrive(bar(MB_TFREE + g * 2 + 1));
+            // certain when the best chunk holds exactly one score >= theta and no other chunk reaches it;
+            // the sum below packs that count (low 6 bits) and the score's position (bits 6..)
+            const float theta = best - win;
+            float sv[32];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float4 t4 = svs[c ^ (te & 7)];
+                sv[4 * c] = t4.x;
+                sv[4 * c + 1] = t4.y;
+                sv[4 * c + 2] = t4.z;
+                sv[4 * c + 3] = t4.w;
+            }
+            float tally = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) tally = fmaf(sv[q] >= theta ? 1.0f : 0.0f, (float)(1 + 64 * q), tally);
+            const int ti = (int)tally;
+            int code = bestj * 32 + (ti >> 6);
+            const bool valid = row < r1;
+            if (valid && !((ti & 63) == 1 && cm2 < theta)) {
+                unsigned cmask = 0, svmask = 0;
+#pragma unroll
+                for (int c = 0; c < KSMAX / 32; ++c) cmask |= (c != bestj && cmx[c] >= theta) ? (1u << c) : 0u;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) svmask |= (sv[q] >= theta) ? (1u << q) : 0u;
+                code = decide_exact(v0, v1, cbg, svmask, bestj, cmask, Ks);
+                ++rechecks;
+            }
             if (valid) {
-                const float *c = cbf + (g * KSMAX + code) * CB_STRIDE;
+                const float *c = cbg + code * CB_STRIDE;
                 float e = 0.0f;
                 float res[DS];
                 const float4 c0 = *reinterpret_cast<const float4 *>(c);
@@ -600,26 +660,19 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
                     for (int d = 0; d < DS; ++d) atomicAdd(ac + d, res[d]);
                     atomicAdd(cnt + g * KSMAX + code, 1);
                 }
-                code_pair |= (uint32_t)code << (8 * h);
-                if (h == 1 && a.codes)
-                    *reinterpret_cast<uint16_t *>(a.codes + row * a.M + m0 + 2 * w) = (uint16_t)code_pair;
-            }
-            if (h == 1) {
-                code_pair = 0;
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(mb + MB_EMPTY + s));
+                if (a.codes) a.codes[row * a.M + m0 + g] = (uint8_t)code;
             }
         }
         // ---- results of this CTA -------------------------------------------
         asm volatile("bar.sync 1, 256;" ::: "memory");
         if (fit) {
-            for (int e = tid - 64; e < G * KSMAX; e += kCompute) {
-                const int g = e / KSMAX, k = e % KSMAX;
+            for (int e = tid - kEpi0; e < G * KSMAX; e += 256) {
+                const int gg = e / KSMAX, k = e % KSMAX;
                 if (k >= Ks) continue;
-                const size_t base = ((size_t)blockIdx.x * a.M + m0 + g) * Ks + k;
+                const size_t base = ((size_t)blockIdx.x * a.M + m0 + gg) * Ks + k;
 #pragma unroll
-                for (int d = 0; d < DS; ++d) a.part[base * DS + d] = (double)acc[(g * KSMAX + k) * ACC_STRIDE + d];
-                a.part_cnt[base] = cnt[g * KSMAX + k];
+                for (int d = 0; d < DS; ++d) a.part[base * DS + d] = (double)acc[(gg * KSMAX + k) * ACC_STRIDE + d];
+                a.part_cnt[base] = cnt[gg * KSMAX + k];
             }
         }
         double tot = (double)sse_s - (double)sse_c;
@@ -676,6 +729,8 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode()
 
 }  // namespace
 
+int tc_pass_group() { return G; }
+
 bool tc_pass_supported(int D, int M, int Ks) { return M > 0 && D == M * DS && M % G == 0 && Ks >= 1 && Ks <= KSMAX; }
 
 int pq_pass_tc_blocks(const PqPass &p)
@@ -691,10 +746,8 @@ int pq_pass_tc_blocks(const PqPass &p)
 
 int launch_pq_pass_tc(PqPass &p, cudaStream_t s)
 {
-    if (!tc_pass_supported(p.D, p.M, p.Ks)) return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8, M % 4 == 0");
+    if (!tc_pass_supported(p.D, p.M, p.Ks)) return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and M even");
     if (p.N >= (1LL << 31) / TM * TM) return fail(PQ_ENOTSUP, "BF16 tensor-core pass supports N < 2^31");
-    if (p.codes && (reinterpret_cast<uintptr_t>(p.codes) & 3))
-        return fail(PQ_EINVAL, "codes must be 4-byte aligned for the tensor-core pass");
     PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
     if (!enc) return fail(PQ_ECUDA, "cuTensorMapEncodeTiled unavailable");
     CUtensorMap map;
@@ -703,7 +756,7 @@ int launch_pq_pass_tc(PqPass &p, cudaStream_t s)
     const cuuint32_t box[2] = {(cuuint32_t)(G * DS), (cuuint32_t)TM};
     const cuuint32_t estride[2] = {1, 1};
     const CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(p.X), gdim, gstride, box,
-                            estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS) return fail(PQ_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
     int dev = 0;

@@ -44,7 +44,8 @@ def test_encode_bf16_bit_exact(pq, small, n):
 
 
 @pytest.mark.parametrize("D,M,Ks,kind", [(128, 16, 256, "int255"), (96, 12, 256, "cont"), (256, 32, 256, "cont"),
-                                        (32, 4, 100, "cont"), (64, 8, 7, "int255")])
+                                        (32, 4, 100, "cont"), (64, 8, 7, "int255"),
+                                        (48, 6, 256, "cont"), (16, 2, 64, "int255")])
 def test_encode_bf16_shapes(pq, D, M, Ks, kind):
     X = datagen.mixture(20_000, D, 300, kind, 300 + D)
     cb, _ = orc.pq_fit(X[:5000], M, Ks, 3, 1)
