@@ -27,9 +27,10 @@
 // FP64 among the FP32 near-ties, the decision rule of the CPU reference.
 // Codes are exact.
 //
-// Update.  Residuals x - c_code are added with shared-memory FP32 atomics into
-// per-CTA sums; the finalise kernel adds the CTAs in a fixed order in FP64 and
-// moves every codeword by the mean residual of its members.
+// Update.  Residuals x - c_code are added with shared-memory int32 atomics, in
+// an exact fixed-point format (FixFmt below), into per-CTA sums; the finalise
+// kernel adds the CTAs in a fixed order in FP64 and moves every codeword by the
+// mean residual of its members.
 //
 // Pipeline (one CTA per SM, a group of 2 subspaces, persistent over row tiles
 // of 128).  Warp 0 issues TMA loads of 128 x 16 float tiles (64B swizzle) into
@@ -82,8 +83,9 @@ constexpr int OFF_XS = 0;
 constexpr int OFF_A = OFF_XS + NXS * XS_BYTES;  // [stage][g]
 constexpr int OFF_B = OFF_A + NAS * G * A_SUB;  // [g]
 constexpr int OFF_CBF = OFF_B + G * B_SUB;
-constexpr int OFF_ACC = OFF_CBF + G * KSMAX * CB_STRIDE * 4;
-constexpr int OFF_CNT = OFF_ACC + G * KSMAX * ACC_STRIDE * 4;
+constexpr int ACC_BYTES = G * KSMAX * ACC_STRIDE * 4;
+constexpr int OFF_ACC = OFF_CBF + G * KSMAX * CB_STRIDE * 4;  // int32 [3][G][KSMAX][ACC_STRIDE]: high, low, float
+constexpr int OFF_CNT = OFF_ACC + 3 * ACC_BYTES;
 constexpr int OFF_SV = OFF_CNT + G * KSMAX * 4;        // [256 epilogue threads][32] best-chunk scores
 constexpr int OFF_MISC = OFF_SV + 256 * 32 * 4;
 constexpr int MISC_BYTES = 512;
@@ -301,6 +303,32 @@ __device__ __noinline__ int decide_exact(float4 xa, float4 xb, const float *cb, 
     return bk;
 }
 
+// Fixed-point format of the residual sums of one CTA and subspace.  A residual
+// element r becomes q = rint(r * 2^F) and is added as two int32 parts,
+// q >> L and q & (2^L - 1), so that neither running sum can overflow over the
+// CTA's at most n rows: with b = bit length of n, L = 31 - b keeps the low sum
+// below 2^31 and |q| < 2^(61 - 2b) keeps the high sum below 2^31.  F puts twice
+// the largest centred codeword norm R0 at that limit; the rare element beyond it
+// goes to an FP32 sum instead.  The integer sums are exact and independent of
+// the order of the additions.
+struct FixFmt {
+    int L, F;
+    float scale, lim;
+};
+__device__ __forceinline__ FixFmt fix_format(int64_t rows, float r0)
+{
+    const int b = 64 - __clzll((unsigned long long)rows);  // bit length of the row count
+    FixFmt f;
+    f.L = 31 - b;
+    const int qb = min(61 - 2 * b, 30);
+    int e = 0;
+    (void)frexpf(r0 > 0.0f ? r0 : 1.0f, &e);  // r0 < 2^e
+    f.F = max(-100, min(100, qb - e));
+    f.scale = ldexpf(1.0f, f.F);
+    f.lim = ldexpf(1.0f, qb);
+    return f;
+}
+
 __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                   const TcArgs a)
 {
@@ -327,7 +355,9 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
     unsigned char *aop = sm + OFF_A;
     unsigned char *bop = sm + OFF_B;
     float *cbf = reinterpret_cast<float *>(sm + OFF_CBF);
-    float *acc = reinterpret_cast<float *>(sm + OFF_ACC);
+    int *acch = reinterpret_cast<int *>(sm + OFF_ACC);
+    int *accl = acch + ACC_BYTES / 4;
+    float *accf = reinterpret_cast<float *>(accl + ACC_BYTES / 4);
     int *cnt = reinterpret_cast<int *>(sm + OFF_CNT);
     uint64_t *mb = reinterpret_cast<uint64_t *>(sm + OFF_MISC);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + OFF_MISC + MISC_TSLOT);
@@ -394,7 +424,11 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
         }
         if (fit) {
 #pragma unroll
-            for (int j = 0; j < DS; ++j) acc[(g * KSMAX + k) * ACC_STRIDE + j] = 0.0f;
+            for (int j = 0; j < DS; ++j) {
+                acch[(g * KSMAX + k) * ACC_STRIDE + j] = 0;
+                accl[(g * KSMAX + k) * ACC_STRIDE + j] = 0;
+                accf[(g * KSMAX + k) * ACC_STRIDE + j] = 0.0f;
+            }
             cnt[g * KSMAX + k] = 0;
         }
     }
@@ -538,6 +572,7 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
         float4 *svs = reinterpret_cast<float4 *>(sm + OFF_SV) + te * 8;  // 16-byte pieces swizzled by te & 7
         float sse_s = 0.0f, sse_c = 0.0f;  // Kahan pair
         unsigned rechecks = 0;
+        const FixFmt fx = fix_format((int64_t)n_my * TM, 2.0f * __uint_as_float(bnd[g * 2 + 1]));
         for (int i = 0; i < n_my; ++i) {
             const int s = i % NXS;
             const int64_t row = r0 + (int64_t)(lb + i * gxc) * TM + r;
@@ -655,9 +690,25 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
                 sse_c = (t2 - sse_s) - y;
                 sse_s = t2;
                 if (fit) {
-                    float *ac = acc + (g * KSMAX + code) * ACC_STRIDE;
+                    const int o = (g * KSMAX + code) * ACC_STRIDE;
+                    int q[DS];
+                    bool big = false;
 #pragma unroll
-                    for (int d = 0; d < DS; ++d) atomicAdd(ac + d, res[d]);
+                    for (int d = 0; d < DS; ++d) {
+                        const float t = res[d] * fx.scale;
+                        big |= !(fabsf(t) < fx.lim);
+                        q[d] = __float2int_rn(t);
+                    }
+                    if (!big) {
+#pragma unroll
+                        for (int d = 0; d < DS; ++d) {
+                            atomicAdd(acch + o + d, q[d] >> fx.L);
+                            atomicAdd(accl + o + d, q[d] & ((1 << fx.L) - 1));
+                        }
+                    } else {
+#pragma unroll
+                        for (int d = 0; d < DS; ++d) atomicAdd(accf + o + d, res[d]);
+                    }
                     atomicAdd(cnt + g * KSMAX + code, 1);
                 }
                 if (a.codes) a.codes[row * a.M + m0 + g] = (uint8_t)code;
@@ -670,8 +721,13 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
                 const int gg = e / KSMAX, k = e % KSMAX;
                 if (k >= Ks) continue;
                 const size_t base = ((size_t)blockIdx.x * a.M + m0 + gg) * Ks + k;
+                const FixFmt f = fix_format((int64_t)n_my * TM, 2.0f * __uint_as_float(bnd[gg * 2 + 1]));
+                const int o = (gg * KSMAX + k) * ACC_STRIDE;
 #pragma unroll
-                for (int d = 0; d < DS; ++d) a.part[base * DS + d] = (double)acc[(gg * KSMAX + k) * ACC_STRIDE + d];
+                for (int d = 0; d < DS; ++d) {
+                    const long long qs = (long long)acch[o + d] * (1LL << f.L) + (long long)accl[o + d];
+                    a.part[base * DS + d] = ldexp((double)qs, -f.F) + (double)accf[o + d];
+                }
                 a.part_cnt[base] = cnt[gg * KSMAX + k];
             }
         }
