@@ -122,14 +122,26 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Spin budget of every device-side wait: ~2^22 polls with a 64 ns back-off
-// is well under a second of wall time on a healthy GPU.
+// Spin budget of every device-side wait: ~2^22 polls (each an L2 round trip or
+// an mbarrier try-wait) is a few seconds at most on a healthy GPU.
 constexpr unsigned kSpinLimit = 1u << 22;
 
 // Barrier over the `nblk` blocks sharing `bar` ({arrive count, generation}).
 // Blocks must be co-resident (cooperative launch).  Returns false, after
 // recording PQ_ETIMEOUT in *err, if the wait ran out; every later barrier of
 // the same kernel then returns false at once so the kernel can unwind.
+__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// Barrier of the nblk co-resident blocks that share `bar` ([0] arrivals, [1] generation).
+// The arrival is an acquire-release atomic and the wait an acquire load, so the block's
+// writes (ordered before thread 0 by the first __syncthreads) are visible to every block
+// after the barrier.  The wait is bounded: false (PQ_ETIMEOUT recorded) if it ran out
+// or another block already failed.
 __device__ __forceinline__ bool block_group_barrier(unsigned *bar, unsigned nblk, int *err)
 {
     __shared__ int s_ok;
@@ -137,25 +149,20 @@ __device__ __forceinline__ bool block_group_barrier(unsigned *bar, unsigned nblk
     if (threadIdx.x == 0) {
         int ok = (*(volatile int *)err == 0);
         if (ok) {
-            unsigned gen = ld_acquire_u32(bar + 1);
-            __threadfence();
-            unsigned arrived = atomicAdd(bar, 1u);
+            const unsigned gen = ld_acquire_u32(bar + 1);
+            const unsigned arrived = atom_add_acq_rel_u32(bar, 1u);
             if (arrived == nblk - 1) {
                 atomicExch(bar, 0u);
-                __threadfence();
                 st_release_u32(bar + 1, gen + 1);
             } else {
-                unsigned it = 0;
-                while (ld_acquire_u32(bar + 1) == gen) {
-                    if (++it > kSpinLimit || *(volatile int *)err != 0) {
+                for (unsigned it = 0; ld_acquire_u32(bar + 1) == gen; ++it) {
+                    if (it > kSpinLimit || ((it & 255) == 255 && *(volatile int *)err != 0)) {
                         atomicCAS(err, 0, PQ_ETIMEOUT);
                         ok = 0;
                         break;
                     }
-                    __nanosleep(64);
                 }
             }
-            __threadfence();
         }
         s_ok = ok;
     }

@@ -30,6 +30,9 @@ namespace {
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
+constexpr int kPer = 5;              // block sums per lane in the owner search
+constexpr int kMaxBps = 32 * kPer;   // blocks per group
+constexpr int64_t kDynSmemCap = 200 * 1024;  // dynamic shared memory of a block
 
 struct KppArgs {
     const float *X;               // rows, stride ld floats
@@ -45,35 +48,43 @@ struct KppArgs {
     unsigned *dmax_bits;          // [groups]
     int *err;
     int bps;
+    int ncache;                   // points per block kept in shared memory
+    int nb_pad;                   // floats of the per-block D2 copy (multiple of 4)
     SeedChunk ch[kMaxSeedChunks];
 };
 
+// FP32 squared distance in dimension order (each difference, square and sum rounded
+// separately) -- the order the CPU reference uses.  `c` is in shared memory.
 __device__ __forceinline__ float d2_f32_exact(const float *x, const float *c, int ds)
 {
     float acc = 0.0f;
     int j = 0;
     if ((ds & 3) == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0) {
-        // Loads are issued 32 floats ahead; the sum itself stays in dimension order.
+        // loads are issued 32 floats ahead; the sum itself stays in dimension order
         for (; j + 32 <= ds; j += 32) {
             float4 v[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) v[q] = __ldg(reinterpret_cast<const float4 *>(x + j) + q);
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
+                const float4 cc = *reinterpret_cast<const float4 *>(c + j + 4 * q);
                 const float e[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+                const float f[4] = {cc.x, cc.y, cc.z, cc.w};
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
-                    const float t = __fsub_rn(e[r], c[j + 4 * q + r]);
+                    const float t = __fsub_rn(e[r], f[r]);
                     acc = __fadd_rn(acc, __fmul_rn(t, t));
                 }
             }
         }
         for (; j < ds; j += 4) {
             const float4 v = __ldg(reinterpret_cast<const float4 *>(x + j));
+            const float4 cc = *reinterpret_cast<const float4 *>(c + j);
             const float e[4] = {v.x, v.y, v.z, v.w};
+            const float f[4] = {cc.x, cc.y, cc.z, cc.w};
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                const float t = __fsub_rn(e[r], c[j + r]);
+                const float t = __fsub_rn(e[r], f[r]);
                 acc = __fadd_rn(acc, __fmul_rn(t, t));
             }
         }
@@ -84,6 +95,54 @@ __device__ __forceinline__ float d2_f32_exact(const float *x, const float *c, in
         acc = __fadd_rn(acc, __fmul_rn(t, t));
     }
     return acc;
+}
+
+// The same distance for two points at once: two independent chains, twice the loads in
+// flight; each chain keeps the dimension order.  Needs ds % 4 == 0 and 16-byte aligned rows.
+__device__ __forceinline__ void d2_f32_exact2(const float *x0, const float *x1, const float *c, int ds, float &d0,
+                                              float &d1)
+{
+    float a0 = 0.0f, a1 = 0.0f;
+    int j = 0;
+    for (; j + 32 <= ds; j += 32) {
+        float4 v0[8], v1[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            v0[q] = __ldg(reinterpret_cast<const float4 *>(x0 + j) + q);
+            v1[q] = __ldg(reinterpret_cast<const float4 *>(x1 + j) + q);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float4 cc = *reinterpret_cast<const float4 *>(c + j + 4 * q);
+            const float f[4] = {cc.x, cc.y, cc.z, cc.w};
+            const float e0[4] = {v0[q].x, v0[q].y, v0[q].z, v0[q].w};
+            const float e1[4] = {v1[q].x, v1[q].y, v1[q].z, v1[q].w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float t0 = __fsub_rn(e0[r], f[r]);
+                const float t1 = __fsub_rn(e1[r], f[r]);
+                a0 = __fadd_rn(a0, __fmul_rn(t0, t0));
+                a1 = __fadd_rn(a1, __fmul_rn(t1, t1));
+            }
+        }
+    }
+    for (; j < ds; j += 4) {
+        const float4 u0 = __ldg(reinterpret_cast<const float4 *>(x0 + j));
+        const float4 u1 = __ldg(reinterpret_cast<const float4 *>(x1 + j));
+        const float4 cc = *reinterpret_cast<const float4 *>(c + j);
+        const float f[4] = {cc.x, cc.y, cc.z, cc.w};
+        const float e0[4] = {u0.x, u0.y, u0.z, u0.w};
+        const float e1[4] = {u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float t0 = __fsub_rn(e0[r], f[r]);
+            const float t1 = __fsub_rn(e1[r], f[r]);
+            a0 = __fadd_rn(a0, __fmul_rn(t0, t0));
+            a1 = __fadd_rn(a1, __fmul_rn(t1, t1));
+        }
+    }
+    d0 = a0;
+    d1 = a1;
 }
 
 __device__ __forceinline__ uint64_t weight(float d2, double scale, bool any)
@@ -120,14 +179,37 @@ __device__ __forceinline__ uint64_t block_scan_u64(uint64_t v, uint64_t *sh_warp
     return v + add;
 }
 
-__global__ void __launch_bounds__(kThreads) kmeanspp_kernel(KppArgs a)
+// Squared distance of the shared-memory copy of point i (float4 q of point i at
+// pts4[q * ncache + i]) to the seed c, dimension order.
+__device__ __forceinline__ float d2_f32_smem(const float4 *pts4, int ncache, int i, const float *c, int ds)
 {
-    __shared__ float s_center[256];  // ds <= 256
+    float acc = 0.0f;
+    for (int q = 0; q < ds / 4; ++q) {
+        const float4 v = pts4[q * ncache + i];
+        const float4 cc = *reinterpret_cast<const float4 *>(c + 4 * q);
+        const float e[4] = {v.x, v.y, v.z, v.w};
+        const float f[4] = {cc.x, cc.y, cc.z, cc.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float t = __fsub_rn(e[r], f[r]);
+            acc = __fadd_rn(acc, __fmul_rn(t, t));
+        }
+    }
+    return acc;
+}
+
+constexpr int kWalkRegs = 8;  // D2 values per thread kept in registers by the walk
+
+__global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
+{
+    __shared__ __align__(16) float s_center[256];  // ds <= 256
     __shared__ uint64_t s_warp[kWarps];
     __shared__ float s_fmax[kWarps];
     __shared__ long long s_pick;
     __shared__ int s_owner;
     __shared__ unsigned long long s_thr;
+    // dynamic: this block's D2 values [nb_pad], then the first ncache of its points [ds/4][ncache]
+    extern __shared__ float4 s_dyn[];
 
     // group = (chunk, subspace); its points are the chunk's rows or its subsample
     const int grp = blockIdx.y, b = blockIdx.x, tid = threadIdx.x;
@@ -138,10 +220,15 @@ __global__ void __launch_bounds__(kThreads) kmeanspp_kernel(KppArgs a)
     const int ds = a.ds;
     const int64_t nb = (n + a.bps - 1) / a.bps;
     const int64_t i0 = (int64_t)b * nb;
-    const int64_t cnt = max((int64_t)0, min(n, i0 + nb) - i0);
+    const int cnt = (int)max((int64_t)0, min(n, i0 + nb) - i0);
     const float *Pm = a.X + (int64_t)m * ds;
     const int64_t *sub = ck.sub_off >= 0 ? a.sub_rows + ck.sub_off : nullptr;
     auto point = [&](int64_t i) -> const float * { return Pm + (ck.r0 + (sub ? sub[i] : i)) * a.ld; };
+    const bool vec_ok = (ds & 3) == 0 && (a.ld & 3) == 0 && (reinterpret_cast<uintptr_t>(Pm) & 15) == 0;
+    const int ncache = vec_ok ? min(cnt, a.ncache) : 0;
+    float *s_d2 = reinterpret_cast<float *>(s_dyn);
+    const float4 *pts4 = s_dyn + a.nb_pad / 4;
+    float4 *pts4w = s_dyn + a.nb_pad / 4;
     unsigned *bar = a.bars + 2 * grp;
     float *Cm = a.C + ((size_t)chunk * a.M + m) * a.Ks * ds;
     const int groups = a.n_chunks * a.M;
@@ -150,7 +237,7 @@ __global__ void __launch_bounds__(kThreads) kmeanspp_kernel(KppArgs a)
     unsigned long long *bs = a.bsum + (size_t)grp * a.bps;
     const size_t bplane = (size_t)groups * a.bps;
 
-    // ---- round 0 -----------------------------------------------------------
+    // ---- round 0: first seed; D2 of every point; the cached points are copied --------
     long long pick = scale_index(rng_draw(seed, (uint64_t)m, 0) >> 11, (uint64_t)n);
     for (int j = tid; j < ds; j += kThreads) {
         const float v = point(pick)[j];
@@ -159,8 +246,28 @@ __global__ void __launch_bounds__(kThreads) kmeanspp_kernel(KppArgs a)
     }
     __syncthreads();
     float lmax = 0.0f;
-    for (int64_t i = tid; i < cnt; i += kThreads) {
-        const float d = d2_f32_exact(point(i0 + i), s_center, ds);
+    for (int i = tid; i < cnt; i += kThreads) {
+        float d;
+        if (i < ncache) {
+            const float *x = point(i0 + i);
+            float acc = 0.0f;
+            for (int q = 0; q < ds / 4; ++q) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(x) + q);
+                pts4w[q * ncache + i] = v;
+                const float4 cc = *reinterpret_cast<const float4 *>(s_center + 4 * q);
+                const float e[4] = {v.x, v.y, v.z, v.w};
+                const float f[4] = {cc.x, cc.y, cc.z, cc.w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const float t = __fsub_rn(e[r], f[r]);
+                    acc = __fadd_rn(acc, __fmul_rn(t, t));
+                }
+            }
+            d = acc;
+        } else {
+            d = d2_f32_exact(point(i0 + i), s_center, ds);
+        }
+        s_d2[i] = d;
         d2m[plane + i0 + i] = d;  // buffer 1 holds D2 for round 1
         lmax = fmaxf(lmax, d);
     }
@@ -191,19 +298,38 @@ __global__ void __launch_bounds__(kThreads) kmeanspp_kernel(KppArgs a)
     for (int t = 1; t < a.Ks; ++t) {
         const int cur = t & 1;
         float *D2c = d2m + (size_t)cur * plane;
-        const float *D2p = d2m + (size_t)(cur ^ 1) * plane;
-        // fold seed t-1 into this block's D2 (round 1 uses round 0's values) and sum the weights
+        // fold seed t-1 into this block's D2 (round 1 uses round 0's values) and sum the weights;
+        // the block's own D2 values live in shared memory, the global copy serves the walk
         uint64_t part = 0;
-        for (int64_t i = tid; i < cnt; i += kThreads) {
-            float d;
-            if (t == 1) {
-                d = D2c[i0 + i];
-            } else {
-                d = d2_f32_exact(point(i0 + i), s_center, ds);
-                d = fminf(d, D2p[i0 + i]);
+        if (t == 1) {
+            for (int i = tid; i < cnt; i += kThreads) part += weight(s_d2[i], scale, any);
+        } else {
+            int i = tid;
+            for (; i < ncache; i += kThreads) {
+                const float d = fminf(d2_f32_smem(pts4, ncache, i, s_center, ds), s_d2[i]);
+                s_d2[i] = d;
                 D2c[i0 + i] = d;
+                part += weight(d, scale, any);
             }
-            part += weight(d, scale, any);
+            if (vec_ok) {
+                for (; i + kThreads < cnt; i += 2 * kThreads) {
+                    float d0, d1;
+                    d2_f32_exact2(point(i0 + i), point(i0 + i + kThreads), s_center, ds, d0, d1);
+                    d0 = fminf(d0, s_d2[i]);
+                    d1 = fminf(d1, s_d2[i + kThreads]);
+                    s_d2[i] = d0;
+                    s_d2[i + kThreads] = d1;
+                    D2c[i0 + i] = d0;
+                    D2c[i0 + i + kThreads] = d1;
+                    part += weight(d0, scale, any) + weight(d1, scale, any);
+                }
+            }
+            for (; i < cnt; i += kThreads) {
+                const float d = fminf(d2_f32_exact(point(i0 + i), s_center, ds), s_d2[i]);
+                s_d2[i] = d;
+                D2c[i0 + i] = d;
+                part += weight(d, scale, any);
+            }
         }
         part = warp_sum(part);
         if ((tid & 31) == 0) s_warp[tid >> 5] = part;
@@ -215,57 +341,90 @@ __global__ void __launch_bounds__(kThreads) kmeanspp_kernel(KppArgs a)
         }
         if (!block_group_barrier(bar, a.bps, a.err)) return;
 
-        // every block: owner block and threshold
+        // every block: owner block and threshold.  Lane l holds the sums of blocks
+        // [l*kPer, (l+1)*kPer): one round of loads, then a warp scan of the lane totals.
         const uint64_t r = rng_draw(seed, (uint64_t)m, (uint64_t)t) >> 11;
         if (tid < 32) {
             const volatile unsigned long long *bv = bs + (size_t)cur * bplane;
-            uint64_t W = 0;
-            for (int q = tid; q < a.bps; q += 32) W += bv[q];
-            W = warp_sum(W);
-            int owner = -1;
-            uint64_t thr_local = 0;
+            uint64_t v[kPer];
+            uint64_t tot = 0;
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int bi = tid * kPer + q;
+                v[q] = bi < a.bps ? bv[bi] : 0ull;
+                tot += v[q];
+            }
+            const uint64_t incl = warp_incl_scan(tot);
+            const uint64_t W = __shfl_sync(0xffffffffu, incl, 31);
             long long p = -1;
             if (W == 0) {
                 p = scale_index(r, (uint64_t)n);
             } else {
                 const uint64_t thr = (__umul64hi(r, W) << 11) | ((r * W) >> 53);
-                uint64_t acc = 0;
-                for (int base = 0; base < a.bps && owner < 0; base += 32) {
-                    const uint64_t v = (base + tid < a.bps) ? bv[base + tid] : 0ull;
-                    const uint64_t incl = warp_incl_scan(v) + acc;
-                    const unsigned hit = __ballot_sync(0xffffffffu, incl > thr && v > 0);
-                    if (hit) {
-                        const int l = __ffs(hit) - 1;
-                        owner = base + l;
-                        thr_local = thr - (__shfl_sync(0xffffffffu, incl, l) - __shfl_sync(0xffffffffu, v, l));
+                const unsigned hit = __ballot_sync(0xffffffffu, incl > thr);
+                const int l = __ffs(hit) - 1;
+                if (tid == l) {
+                    uint64_t acc = incl - tot;
+                    int owner = -1;
+                    uint64_t thr_local = 0;
+#pragma unroll
+                    for (int q = 0; q < kPer; ++q) {
+                        if (owner < 0 && acc + v[q] > thr) {
+                            owner = tid * kPer + q;
+                            thr_local = thr - acc;
+                        }
+                        acc += v[q];
                     }
-                    acc = __shfl_sync(0xffffffffu, incl, 31);
+                    s_owner = owner;
+                    s_thr = thr_local;
                 }
             }
-            if (tid == 0) {
-                s_pick = p;
-                s_owner = owner;
-                s_thr = thr_local;
-            }
+            if (tid == 0) s_pick = p;
         }
         __syncthreads();
         if (s_pick < 0) {
-            // walk the owner's D2 values in order to the threshold
+            // walk the owner's D2 values in order to the threshold (the owner reads its own copy)
             const int owner = s_owner;
             const uint64_t thr_local = s_thr;
             const int64_t o0 = (int64_t)owner * nb;
-            const int64_t ocnt = min(n, o0 + nb) - o0;
-            const int64_t seg = (ocnt + kThreads - 1) / kThreads;
-            const int64_t s0 = min(ocnt, (int64_t)tid * seg), s1 = min(ocnt, s0 + seg);
+            const int ocnt = (int)(min(n, o0 + nb) - o0);
+            const int seg = (ocnt + kThreads - 1) / kThreads;
+            const int s0 = min(ocnt, tid * seg), s1 = min(ocnt, s0 + seg);
+            const float *src = owner == b ? s_d2 : nullptr;
             uint64_t w = 0;
-            for (int64_t i = s0; i < s1; ++i) w += weight(D2c[o0 + i], scale, any);
-            const uint64_t incl = block_scan_u64(w, s_warp);
-            const uint64_t excl = incl - w;
-            if (excl <= thr_local && thr_local < incl) {
-                uint64_t acc = excl;
-                for (int64_t i = s0; i < s1; ++i) {
-                    acc += weight(D2c[o0 + i], scale, any);
-                    if (acc > thr_local) { s_pick = o0 + i; break; }
+            if (seg <= kWalkRegs) {
+                float dv[kWalkRegs];
+#pragma unroll
+                for (int q = 0; q < kWalkRegs; ++q) {
+                    const int i = s0 + q;
+                    dv[q] = i < s1 ? (src ? src[i] : __ldcg(D2c + o0 + i)) : 0.0f;
+                }
+#pragma unroll
+                for (int q = 0; q < kWalkRegs; ++q) w += s0 + q < s1 ? weight(dv[q], scale, any) : 0ull;
+                const uint64_t incl = block_scan_u64(w, s_warp);
+                const uint64_t excl = incl - w;
+                if (excl <= thr_local && thr_local < incl) {
+                    uint64_t acc = excl;
+                    long long hit = -1;
+#pragma unroll
+                    for (int q = 0; q < kWalkRegs; ++q) {
+                        if (hit < 0 && s0 + q < s1) {
+                            acc += weight(dv[q], scale, any);
+                            if (acc > thr_local) hit = o0 + s0 + q;
+                        }
+                    }
+                    s_pick = hit;
+                }
+            } else {
+                for (int i = s0; i < s1; ++i) w += weight(src ? src[i] : __ldcg(D2c + o0 + i), scale, any);
+                const uint64_t incl = block_scan_u64(w, s_warp);
+                const uint64_t excl = incl - w;
+                if (excl <= thr_local && thr_local < incl) {
+                    uint64_t acc = excl;
+                    for (int i = s0; i < s1; ++i) {
+                        acc += weight(src ? src[i] : __ldcg(D2c + o0 + i), scale, any);
+                        if (acc > thr_local) { s_pick = o0 + i; break; }
+                    }
                 }
             }
             __syncthreads();
@@ -328,14 +487,22 @@ int launch_kmeanspp_chunks(const float *X, int64_t ld, const SeedChunk *chunks, 
     // meet at barriers).  Several chunks: one block per (chunk, subspace), no inter-block waits.
     int bps = 1;
     bool coop = false;
+    if (n_chunks == 1)
+        bps = (int)std::max<int64_t>(
+            1, std::min<int64_t>(std::min(sms / std::max(1, M), kMaxBps), (a.nmax + 255) / 256));
+    // shared memory: the block's D2 copy, then as many of its points as fit
+    const int64_t nb = (a.nmax + bps - 1) / bps;
+    a.nb_pad = (int)((nb + 3) & ~int64_t(3));
+    if ((int64_t)a.nb_pad * 4 > kDynSmemCap)
+        return fail(PQ_ENOTSUP, "k-means++ seeding: %lld points per block exceed shared memory", (long long)nb);
+    a.ncache = (ds % 4 == 0) ? (int)std::min<int64_t>(nb, (kDynSmemCap - (int64_t)a.nb_pad * 4) / (ds * 4)) : 0;
+    const size_t dyn = (size_t)a.nb_pad * 4 + (size_t)a.ncache * ds * 4;
+    PQ_TRY_CUDA(cudaFuncSetAttribute(kmeanspp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     if (n_chunks == 1) {
         int per_sm = 0;
-        PQ_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kmeanspp_kernel, kThreads, 0));
-        const int64_t capacity = (int64_t)per_sm * sms;
-        const int64_t want = std::max<int64_t>(1, std::min<int64_t>(sms / std::max(1, M), (a.nmax + 255) / 256));
-        if (want * M > capacity)
+        PQ_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kmeanspp_kernel, kThreads, dyn));
+        if ((int64_t)bps * M > (int64_t)per_sm * sms)
             return fail(PQ_ENOTSUP, "k-means++ seeding: %d subspaces do not fit one cooperative wave", M);
-        bps = (int)want;
         coop = true;
     }
     a.bps = bps;
@@ -358,9 +525,9 @@ int launch_kmeanspp_chunks(const float *X, int64_t ld, const SeedChunk *chunks, 
     ProfScope ps(tag, s);
     if (coop) {
         void *args[] = {&a};
-        PQ_TRY_CUDA(cudaLaunchCooperativeKernel((void *)kmeanspp_kernel, grid, dim3(kThreads), args, 0, s));
+        PQ_TRY_CUDA(cudaLaunchCooperativeKernel((void *)kmeanspp_kernel, grid, dim3(kThreads), args, dyn, s));
     } else {
-        kmeanspp_kernel<<<grid, kThreads, 0, s>>>(a);
+        kmeanspp_kernel<<<grid, kThreads, dyn, s>>>(a);
         PQ_TRY_CUDA(cudaGetLastError());
     }
     count_launch();
