@@ -43,7 +43,8 @@ struct KppArgs {
     int64_t nmax;                 // largest point count of a group
     float *C;                     // [n_chunks][M][Ks][ds]
     unsigned *bars;               // [groups][2]
-    unsigned long long *bsum;     // [2][groups][bps]
+    unsigned long long *bsum;     // [2][groups][bps] block weight sums
+    unsigned *tags;               // [2][groups][bps] round of the published sum
     float *d2;                    // [2][groups][nmax]
     unsigned *dmax_bits;          // [groups]
     int *err;
@@ -145,9 +146,17 @@ __device__ __forceinline__ void d2_f32_exact2(const float *x0, const float *x1, 
     d1 = a1;
 }
 
-__device__ __forceinline__ uint64_t weight(float d2, double scale, bool any)
+// w = floor(d2 * 2^sh) for d2 >= 0, exactly, in integer arithmetic:
+// d2 = m * 2^(e - 150) for a normal float, m * 2^-149 for a subnormal one.
+__device__ __forceinline__ uint64_t weight(float d2, int sh, bool any)
 {
-    return any ? (uint64_t)__double2ull_rz(__dmul_rn((double)d2, scale)) : 0ull;
+    const unsigned u = __float_as_uint(d2);
+    if (!any || u == 0u) return 0ull;
+    const unsigned be = u >> 23;  // sign bit clear
+    const uint64_t m = be ? ((u & 0x7fffffu) | 0x800000u) : (u & 0x7fffffu);
+    const int sft = (be ? (int)be - 150 : -149) + sh;
+    if (sft >= 0) return m << sft;  // below 2^62: d2 <= max D2 < 2^E and sh = 62 - L - E
+    return sft > -64 ? (m >> (-sft)) : 0ull;
 }
 
 __device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v)
@@ -208,6 +217,7 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
     __shared__ long long s_pick;
     __shared__ int s_owner;
     __shared__ unsigned long long s_thr;
+    __shared__ int s_fail;
     // dynamic: this block's D2 values [nb_pad], then the first ncache of its points [ds/4][ncache]
     extern __shared__ float4 s_dyn[];
 
@@ -235,6 +245,7 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
     const size_t plane = (size_t)groups * a.nmax;  // one D2 buffer
     float *d2m = a.d2 + (size_t)grp * a.nmax;      // + buffer * plane
     unsigned long long *bs = a.bsum + (size_t)grp * a.bps;
+    unsigned *tags = a.tags + (size_t)grp * a.bps;
     const size_t bplane = (size_t)groups * a.bps;
 
     // ---- round 0: first seed; D2 of every point; the cached points are copied --------
@@ -293,7 +304,6 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
         else E = -117 - __clz(bits & 0x7fffff);           // subnormal maximum
     }
     const int sh = 62 - L - E;
-    const double scale = __longlong_as_double((long long)(sh + 1023) << 52);
 
     for (int t = 1; t < a.Ks; ++t) {
         const int cur = t & 1;
@@ -302,14 +312,14 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
         // the block's own D2 values live in shared memory, the global copy serves the walk
         uint64_t part = 0;
         if (t == 1) {
-            for (int i = tid; i < cnt; i += kThreads) part += weight(s_d2[i], scale, any);
+            for (int i = tid; i < cnt; i += kThreads) part += weight(s_d2[i], sh, any);
         } else {
             int i = tid;
             for (; i < ncache; i += kThreads) {
                 const float d = fminf(d2_f32_smem(pts4, ncache, i, s_center, ds), s_d2[i]);
                 s_d2[i] = d;
                 D2c[i0 + i] = d;
-                part += weight(d, scale, any);
+                part += weight(d, sh, any);
             }
             if (vec_ok) {
                 for (; i + kThreads < cnt; i += 2 * kThreads) {
@@ -321,14 +331,14 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
                     s_d2[i + kThreads] = d1;
                     D2c[i0 + i] = d0;
                     D2c[i0 + i + kThreads] = d1;
-                    part += weight(d0, scale, any) + weight(d1, scale, any);
+                    part += weight(d0, sh, any) + weight(d1, sh, any);
                 }
             }
             for (; i < cnt; i += kThreads) {
                 const float d = fminf(d2_f32_exact(point(i0 + i), s_center, ds), s_d2[i]);
                 s_d2[i] = d;
                 D2c[i0 + i] = d;
-                part += weight(d, scale, any);
+                part += weight(d, sh, any);
             }
         }
         part = warp_sum(part);
@@ -338,13 +348,33 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
             uint64_t tot = 0;
             for (int w = 0; w < kWarps; ++w) tot += s_warp[w];
             bs[(size_t)cur * bplane + b] = tot;
+            // publishes the sum and (ordered before it by the __syncthreads above) the block's D2 copy
+            st_release_u32(tags + (size_t)cur * bplane + b, (unsigned)t);
         }
-        if (!block_group_barrier(bar, a.bps, a.err)) return;
 
-        // every block: owner block and threshold.  Lane l holds the sums of blocks
-        // [l*kPer, (l+1)*kPer): one round of loads, then a warp scan of the lane totals.
+        // every block: wait for all round-t sums of its group, then find the owner block and
+        // threshold.  Lane l polls and holds the sums of blocks [l*kPer, (l+1)*kPer).
         const uint64_t r = rng_draw(seed, (uint64_t)m, (uint64_t)t) >> 11;
         if (tid < 32) {
+            const unsigned *tg = tags + (size_t)cur * bplane;
+            bool ok = true;
+            for (unsigned it = 0;; ++it) {
+                bool mine = true;
+#pragma unroll
+                for (int q = 0; q < kPer; ++q) {
+                    const int bi = tid * kPer + q;
+                    if (bi < a.bps) mine &= ld_acquire_u32(tg + bi) == (unsigned)t;
+                }
+                if (__all_sync(0xffffffffu, mine)) break;
+                // warp-uniform decision to give up (bounded wait)
+                const bool give_up = it > kSpinLimit || ((it & 255) == 255 && *(volatile int *)a.err != 0);
+                if (__any_sync(0xffffffffu, give_up)) {
+                    if (tid == 0) atomicCAS(a.err, 0, PQ_ETIMEOUT);
+                    ok = false;
+                    break;
+                }
+            }
+            if (tid == 0) s_fail = !ok;
             const volatile unsigned long long *bv = bs + (size_t)cur * bplane;
             uint64_t v[kPer];
             uint64_t tot = 0;
@@ -382,6 +412,7 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
             if (tid == 0) s_pick = p;
         }
         __syncthreads();
+        if (s_fail) return;
         if (s_pick < 0) {
             // walk the owner's D2 values in order to the threshold (the owner reads its own copy)
             const int owner = s_owner;
@@ -400,7 +431,7 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
                     dv[q] = i < s1 ? (src ? src[i] : __ldcg(D2c + o0 + i)) : 0.0f;
                 }
 #pragma unroll
-                for (int q = 0; q < kWalkRegs; ++q) w += s0 + q < s1 ? weight(dv[q], scale, any) : 0ull;
+                for (int q = 0; q < kWalkRegs; ++q) w += s0 + q < s1 ? weight(dv[q], sh, any) : 0ull;
                 const uint64_t incl = block_scan_u64(w, s_warp);
                 const uint64_t excl = incl - w;
                 if (excl <= thr_local && thr_local < incl) {
@@ -409,20 +440,20 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
 #pragma unroll
                     for (int q = 0; q < kWalkRegs; ++q) {
                         if (hit < 0 && s0 + q < s1) {
-                            acc += weight(dv[q], scale, any);
+                            acc += weight(dv[q], sh, any);
                             if (acc > thr_local) hit = o0 + s0 + q;
                         }
                     }
                     s_pick = hit;
                 }
             } else {
-                for (int i = s0; i < s1; ++i) w += weight(src ? src[i] : __ldcg(D2c + o0 + i), scale, any);
+                for (int i = s0; i < s1; ++i) w += weight(src ? src[i] : __ldcg(D2c + o0 + i), sh, any);
                 const uint64_t incl = block_scan_u64(w, s_warp);
                 const uint64_t excl = incl - w;
                 if (excl <= thr_local && thr_local < incl) {
                     uint64_t acc = excl;
                     for (int i = s0; i < s1; ++i) {
-                        acc += weight(src ? src[i] : __ldcg(D2c + o0 + i), scale, any);
+                        acc += weight(src ? src[i] : __ldcg(D2c + o0 + i), sh, any);
                         if (acc > thr_local) { s_pick = o0 + i; break; }
                     }
                 }
@@ -510,6 +541,7 @@ int launch_kmeanspp_chunks(const float *X, int64_t ld, const SeedChunk *chunks, 
     a.C = C;
     a.bars = ws.get<unsigned>(2 * (size_t)groups, true);
     a.bsum = ws.get<unsigned long long>(2 * (size_t)groups * bps, true);
+    a.tags = ws.get<unsigned>(2 * (size_t)groups * bps, true);
     a.d2 = ws.get<float>(2 * (size_t)groups * a.nmax);
     a.dmax_bits = ws.get<unsigned>((size_t)groups, true);
     if (ws.status) return ws.status;
