@@ -349,6 +349,207 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def _timed_steps(torch, step, steps, flush):
+    """CUDA-event time (ms) of each of `steps` calls of step(), L2 flushed before each."""
+    stream = torch.cuda.current_stream()
+    out = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def _common_line(args, world, metric, value, unit, ms, dtype, cfg, kern, launches, clk):
+    return {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic (seeded Gaussian mixture standing in for the paper's data)", "config": cfg,
+            "gpu_launches": int(launches), "kernels": kern, "clocks": clk.summary()}
+
+
+def run_gpu_chunked(args):
+    """Divide-and-conquer PQ over 64 lognormal chunks (Sec. 3): one step = pq_fit_chunked."""
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_2604_21645_gb300 import pqgb
+    w = datagen.CHUNKED
+    off = datagen.chunk_offsets(w)
+    N = int(off[-1])
+    X = datagen.mixture(N, w.d, w.n_comp, w.kind, w.seed)
+    Xd = torch.from_numpy(X).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    offl = off.tolist()
+    ctas, tune_ms = pqgb.tune_chunked(Xd, offl, w.m, w.ks, prec=args.prec)
+    out = {}
+
+    def step():
+        out["r"] = pqgb.fit_chunked(Xd, offl, w.m, w.ks, iters=w.iters, seed=w.init_seed, prec=args.prec,
+                                    want_rmse=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    l0 = pqgb.launch_count()
+    pqgb.profile_enable(True)
+    with ClockSampler(local) as clk:
+        ms = _timed_steps(torch, step, args.steps, flush)
+    launches = pqgb.launch_count() - l0
+    kern = pqgb.profile_collect()
+    pqgb.profile_enable(False)
+    t = float(np.mean(ms)) / 1e3
+    cb, codes, _ = out["r"]
+    _, rmse = pqgb.decode_rmse(codes, cb, Xd)
+    # e2e: rows from pinned host memory, codes and global codebooks back
+    Xh = torch.from_numpy(X).pin_memory()
+    Xe = torch.empty_like(Xd)
+    codes_h = torch.empty(codes.shape, dtype=torch.uint8).pin_memory()
+    cb_h = torch.empty(cb.shape, dtype=torch.float32).pin_memory()
+
+    def step_e2e():
+        Xe.copy_(Xh, non_blocking=True)
+        c, k, _ = pqgb.fit_chunked(Xe, offl, w.m, w.ks, iters=w.iters, seed=w.init_seed, prec=args.prec,
+                                   want_rmse=False)
+        k_h = codes_h.copy_(k, non_blocking=True)
+        cb_h.copy_(c, non_blocking=True)
+
+    e2e = _timed_steps(torch, step_e2e, args.steps, flush)
+    peaks, peak_src = load_peaks()
+    pname = "pq_pass_tc" if args.prec == "bf16" else "pq_pass_f32"
+    roof = None
+    if pname in kern:
+        # rows through the pass: every local iteration covers all N rows, the global fit the
+        # n_chunks * Ks pooled codewords, the final encode N rows again
+        rows = w.iters * N + w.iters * len(offl[:-1]) * w.ks + N
+        bound, work, unit, kind = kernel_work(pname, w, rows)
+        secs = kern[pname]["ms"] / 1e3 / args.steps
+        ach = work / secs / 1e12
+        peak = compare_peak_t(peaks) if kind == "cmp" else fp32_peak_tflops(peaks)
+        roof = {"kernel": pname, "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (derived)",
+                "avg_launch_ms": kern[pname]["ms"] / max(kern[pname]["launches"], 1),
+                "share": kern[pname]["ms"] / max(sum(v["ms"] for v in kern.values()), 1e-9)}
+    cfg = {"workload": w.name, "N": N, "n_chunks": w.n_chunks, "D": w.d, "M": w.m, "Ks": w.ks, "iters": w.iters,
+           "chunk_rows": {"min": int(np.diff(off).min()), "median": int(np.median(np.diff(off))),
+                          "max": int(np.diff(off).max())},
+           "prec": args.prec, "tuned_ctas_per_group": ctas, "tuned_pass_ms": tune_ms, "parallelism": "replicas1",
+           "l2": f"256 MB buffer written between steps; X ({X.nbytes // 10**6} MB) exceeds L2"}
+    line = _common_line(args, 1, "chunked PQ fit+encode Mvec/s", N / t / 1e6, "Mvec/s", t * 1e3,
+                        "f32" if args.prec == "fp32" else "bf16", cfg, kern, launches, clk)
+    line["rmse"] = rmse
+    line["roofline"] = roof
+    line["e2e"] = {"value": N / (float(np.mean(e2e)) / 1e3) / 1e6, "unit": "Mvec/s",
+                   "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(codes.numel() + cb.numel() * 4)}
+    if not args.no_cpu_baseline:
+        import oracle as orc
+        rows_c = 20_000
+        off_s = np.arange(0, 4 * rows_c + 1, rows_c, dtype=np.int64)
+        Xs = datagen.mixture(int(off_s[-1]), w.d, w.n_comp, w.kind, w.seed)
+        t0 = time.perf_counter()
+        orc.pq_fit_chunked(Xs, off_s, w.m, w.ks, w.iters, w.init_seed)
+        tc = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": off_s[-1] / tc / 1e6, "unit": "Mvec/s", "cores": orc.num_threads(),
+                                "kind": "oracle",
+                                "sample": f"FP64 oracle pq_fit_chunked on 4 chunks of {rows_c} rows, {tc:.1f} s"}
+    print(json.dumps(line), flush=True)
+
+
+SOFTPQ_FLOPS_FWD = 34   # per (row, subspace, codeword): distance 16, exp 1, normaliser 1, soft reconstruction 16
+SOFTPQ_FLOPS_BWD = 91   # recomputed weight 17, r.c 16, q 2, dX sum 16, dC sums 40
+
+
+def run_gpu_softpq(args):
+    """Soft-assignment refinement loss: one step = forward + backward (dL/dC and dL/dX)."""
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_2604_21645_gb300 import pqgb
+    from paper_2604_21645_gb300.softpq import softpq_loss
+    w = datagen.SOFTPQ
+    X = w.data()
+    Xd = torch.from_numpy(X).cuda()
+    C0 = pqgb.fit(Xd, w.m, w.ks, iters=5, seed=w.init_seed, prec="bf16")  # starting codebooks, untimed
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    Xg = Xd.clone().requires_grad_(True)
+    Cg = C0.clone().requires_grad_(True)
+    out = {}
+
+    def step():
+        Xg.grad = None
+        Cg.grad = None
+        loss = softpq_loss(Xg, Cg, w.tau)
+        loss.backward()
+        out["loss"] = loss
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    l0 = pqgb.launch_count()
+    pqgb.profile_enable(True)
+    with ClockSampler(local) as clk:
+        ms = _timed_steps(torch, step, args.steps, flush)
+    launches = pqgb.launch_count() - l0
+    kern = pqgb.profile_collect()
+    pqgb.profile_enable(False)
+    t = float(np.mean(ms)) / 1e3
+    peaks, _ = load_peaks()
+    scores = float(w.n) * w.m * w.ks
+    roof = None
+    dom = max(kern, key=lambda n: kern[n]["ms"]) if kern else None
+    if dom in ("softpq_bwd", "softpq_fwd"):
+        per = SOFTPQ_FLOPS_BWD if dom == "softpq_bwd" else SOFTPQ_FLOPS_FWD
+        secs = kern[dom]["ms"] / 1e3 / max(kern[dom]["launches"], 1)
+        ach = scores * per / secs / 1e12
+        peak = fp32_peak_tflops(peaks)
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2 flop per FFMA x max SM clock",
+                "avg_launch_ms": secs * 1e3,
+                "share": kern[dom]["ms"] / max(sum(v["ms"] for v in kern.values()), 1e-9)}
+    # e2e: rows and codebooks from pinned host memory, gradients and loss back
+    Xh = torch.from_numpy(X).pin_memory()
+    Ch = C0.cpu().pin_memory()
+    dX_h = torch.empty_like(Xh).pin_memory()
+    dC_h = torch.empty_like(Ch).pin_memory()
+    loss_h = torch.empty((), dtype=torch.float32).pin_memory()
+
+    def step_e2e():
+        Xg.data.copy_(Xh, non_blocking=True)
+        Cg.data.copy_(Ch, non_blocking=True)
+        step()
+        dX_h.copy_(Xg.grad, non_blocking=True)
+        dC_h.copy_(Cg.grad, non_blocking=True)
+        loss_h.copy_(out["loss"], non_blocking=True)
+
+    e2e = _timed_steps(torch, step_e2e, args.steps, flush)
+    cfg = {"workload": w.name, "N": w.n, "D": w.d, "M": w.m, "Ks": w.ks, "tau": w.tau, "parallelism": "replicas1",
+           "l2": f"256 MB buffer written between steps; X ({X.nbytes // 10**6} MB) exceeds L2"}
+    line = _common_line(args, 1, "soft-PQ loss forward+backward Mvec/s", w.n / t / 1e6, "Mvec/s", t * 1e3, "f32",
+                        cfg, kern, launches, clk)
+    line["loss"] = float(out["loss"].item())
+    line["roofline"] = roof
+    line["e2e"] = {"value": w.n / (float(np.mean(e2e)) / 1e3) / 1e6, "unit": "Mvec/s",
+                   "h2d_bytes_per_step": int(X.nbytes + C0.numel() * 4),
+                   "d2h_bytes_per_step": int(X.nbytes + C0.numel() * 4 + 4)}
+    if not args.no_cpu_baseline:
+        import oracle as orc
+        rows = 2000
+        Xs = X[:rows].astype(np.float64)
+        Cs = C0.cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        orc.softpq_forward(Xs, Cs, w.tau)
+        orc.softpq_backward(Xs, Cs, w.tau)
+        tc = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": rows / tc / 1e6, "unit": "Mvec/s", "cores": 1, "kind": "oracle",
+                                "sample": f"FP64 oracle softpq_forward + softpq_backward on the first {rows} rows, "
+                                          f"{tc:.1f} s"}
+    print(json.dumps(line), flush=True)
+
+
 def oracle_fit_encode(w, rows):
     import oracle as orc
     X = datagen.mixture(rows, w.d, w.n_comp, w.kind, w.seed)
@@ -366,29 +567,58 @@ def cpu_baseline(w, rows):
                       f"{rows} rows of the same seeded mixture, {t:.1f} s"}
 
 
+def _oracle_chunked_sample(w):
+    import oracle as orc
+    rows_c = 20_000
+    off_s = np.arange(0, 4 * rows_c + 1, rows_c, dtype=np.int64)
+    Xs = datagen.mixture(int(off_s[-1]), w.d, w.n_comp, w.kind, w.seed)
+    t0 = time.perf_counter()
+    orc.pq_fit_chunked(Xs, off_s, w.m, w.ks, w.iters, w.init_seed)
+    return int(off_s[-1]), time.perf_counter() - t0, f"pq_fit_chunked on 4 chunks of {rows_c} rows"
+
+
+def _oracle_softpq_sample(w):
+    import oracle as orc
+    rows = 2000
+    Xs = w.data(rows).astype(np.float64)
+    rng = np.random.default_rng(w.seed + 11)
+    Cs = Xs[rng.integers(0, rows, size=w.ks)].reshape(w.ks, w.m, w.d // w.m).transpose(1, 0, 2).copy()
+    t0 = time.perf_counter()
+    orc.softpq_forward(Xs, Cs, w.tau)
+    orc.softpq_backward(Xs, Cs, w.tau)
+    return rows, time.perf_counter() - t0, f"softpq_forward + softpq_backward on {rows} rows"
+
+
 def run_reference(args):
+    """The FP64 oracle on the host cores, on a bounded sample of the same workload, per step."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return
     import oracle as orc
     w = datagen.WORKLOADS[args.workload]
-    rows = args.cpu_rows
+    if w.name == datagen.CHUNKED.name:
+        sample, metric, cores = (lambda: _oracle_chunked_sample(w)), "chunked PQ fit+encode Mvec/s", orc.num_threads()
+    elif w.name == datagen.SOFTPQ.name:
+        sample, metric, cores = (lambda: _oracle_softpq_sample(w)), "soft-PQ loss forward+backward Mvec/s", 1
+    else:
+        rows = args.cpu_rows
+        sample = lambda: (rows, oracle_fit_encode(w, rows), f"pq_fit + pq_encode on the first {rows} rows")
+        metric = "PQ fit+encode Mvec/s" + (" (IVF-ADC queries/s reported beside it)" if w.nlist else "")
+        cores = orc.num_threads()
     for _ in range(args.warmup):
-        oracle_fit_encode(w, rows // 4)
-    times = [oracle_fit_encode(w, rows) for _ in range(args.steps)]
-    t = float(np.mean(times))
+        sample()
+    res = [sample() for _ in range(args.steps)]
+    rows = res[0][0]
+    t = float(np.mean([r[1] for r in res]))
     v = rows / t / 1e6
     print(json.dumps({
-        "impl": "reference",
-        "metric": "PQ fit+encode Mvec/s" + (" (IVF-ADC queries/s reported beside it)" if w.nlist else ""),
-        "value": v, "unit": "Mvec/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic (seeded Gaussian mixture standing in for the paper's data)",
-        "config": {"workload": w.name, "N": w.n, "D": w.d, "M": w.m, "Ks": w.ks, "iters": w.iters,
-                   "sample_rows": rows},
-        "cpu_baseline": {"value": v, "unit": "Mvec/s", "cores": orc.num_threads(), "kind": "oracle",
-                         "sample": f"fit+encode on the first {rows} of {w.n} rows per step"},
+        "impl": "reference", "metric": metric, "value": v, "unit": "Mvec/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Gaussian mixture standing in for the paper's data)",
+        "config": {"workload": w.name, "N": w.n, "D": w.d, "M": w.m, "Ks": w.ks, "iters": w.iters, "sample_rows": rows},
+        "cpu_baseline": {"value": v, "unit": "Mvec/s", "cores": cores, "kind": "oracle",
+                         "sample": f"FP64 oracle {res[0][2]} per step"},
         "e2e": {"value": v, "unit": "Mvec/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -399,8 +629,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default=datagen.IVF_MEDIUM.name, choices=[datagen.IVF_MEDIUM.name,
-                                                                            datagen.PQ_10M.name])
+    ap.add_argument("--workload", default=datagen.IVF_MEDIUM.name,
+                    choices=[datagen.IVF_MEDIUM.name, datagen.PQ_10M.name, datagen.CHUNKED.name, datagen.SOFTPQ.name])
     ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--compare-fp32", action="store_true", help="also time the plain FP32 form of fit + encode")
     ap.add_argument("--cpu-rows", type=int, default=50_000)
@@ -410,6 +640,10 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == datagen.CHUNKED.name:
+        run_gpu_chunked(args)
+    elif args.workload == datagen.SOFTPQ.name:
+        run_gpu_softpq(args)
     else:
         run_gpu(args)
 

@@ -190,6 +190,23 @@ int softpq_forward(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, 
 int softpq_backward(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, const float *codebooks, float tau,
                     const float *grad_loss, float *dcodebooks, float *dX, void *stream);
 
+/*
+ * pq_tune_chunked -- autotuner of the batched Lloyd pass of pq_fit_chunked.
+ *   Same X, chunk_offsets (HOST array), n_chunks, D, M, Ks and prec rules as
+ *   pq_fit_chunked.  Seeds every chunk, then times one batched pass (mean of
+ *   three after a warm-up, CUDA events on `stream`) for each candidate number of
+ *   CTAs per subspace group (0.5x to 4x the default, shared out over the chunks
+ *   in proportion to their rows) and keeps the fastest in a process-wide cache
+ *   keyed by the shape (n_chunks, N, D, M, Ks, prec, SM count, chunk offsets);
+ *   later pq_fit_chunked calls of that shape use it.  Synchronizes `stream`.
+ *   ctas     receives the chosen CTAs per subspace group (nullable).
+ *   pass_ms  receives its measured pass time in milliseconds (nullable).
+ * pq_tune_clear forgets every tuned shape.
+ */
+int pq_tune_chunked(const float *X, const int64_t *chunk_offsets, int32_t n_chunks, int32_t D, int32_t M, int32_t Ks,
+                    int32_t prec, int32_t *ctas, float *pass_ms, void *stream);
+int pq_tune_clear(void);
+
 /* Opaque inverted-file index, allocated by ivf_build and owned by the library until ivf_free. */
 typedef struct ivf_index ivf_index;
 

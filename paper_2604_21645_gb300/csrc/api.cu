@@ -362,6 +362,37 @@ int pq_fit_chunked(const float *X, const int64_t *chunk_offsets, int32_t n_chunk
                               static_cast<cudaStream_t>(stream));
 }
 
+int pq_tune_chunked(const float *X, const int64_t *chunk_offsets, int32_t n_chunks, int32_t D, int32_t M, int32_t Ks,
+                    int32_t prec, int32_t *ctas, float *pass_ms, void *stream)
+{
+    g_msg[0] = 0;
+    if (!X || !chunk_offsets) return fail(PQ_EINVAL, "null pointer");
+    if (n_chunks < 1 || n_chunks > kMaxSeedChunks) return fail(PQ_EINVAL, "n_chunks=%d must be in [1, %d]", n_chunks,
+                                                               kMaxSeedChunks);
+    if (chunk_offsets[0] != 0) return fail(PQ_EINVAL, "chunk_offsets[0] must be 0");
+    for (int c = 0; c < n_chunks; ++c)
+        if (chunk_offsets[c + 1] - chunk_offsets[c] < Ks)
+            return fail(PQ_EINVAL, "chunk %d has %lld rows, fewer than Ks=%d", c,
+                        (long long)(chunk_offsets[c + 1] - chunk_offsets[c]), Ks);
+    PQ_TRY(check_pq_shape(chunk_offsets[n_chunks], D, M, Ks, true));
+    PQ_TRY(check_prec(prec));
+    if (!aligned16(X)) return fail(PQ_EINVAL, "X must be 16-byte aligned");
+    if (prec == PQ_PREC_BF16 && !tc_pass_supported(D, M, Ks))
+        return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and M even");
+    int best = 0;
+    float ms = 0.0f;
+    PQ_TRY(run_pq_tune_chunked(X, chunk_offsets, n_chunks, D, M, Ks, prec, &best, &ms, static_cast<cudaStream_t>(stream)));
+    if (ctas) *ctas = best;
+    if (pass_ms) *pass_ms = ms;
+    return PQ_OK;
+}
+
+int pq_tune_clear(void)
+{
+    clear_tuning();
+    return PQ_OK;
+}
+
 static int check_softpq(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, const float *codebooks, float tau)
 {
     if (!codebooks || (N > 0 && !X)) return fail(PQ_EINVAL, "null pointer");

@@ -14,6 +14,9 @@
 // requested, so it can be captured in a CUDA graph.
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -59,6 +62,46 @@ __global__ void pool_codewords_kernel(const float *__restrict__ C, int n_chunks,
     }
 }
 
+// Grid blocks shared out over the chunks in proportion to their rows: `per` blocks
+// for the whole data set, at least one and at most one row tile's worth per chunk.
+int build_chunk_table(const int64_t *off, int n_chunks, int per, bool tc, ChunkTableParams &tp)
+{
+    const int64_t N = off[n_chunks];
+    tp.n = n_chunks;
+    tp.blk[0] = 0;
+    for (int c = 0; c <= n_chunks; ++c) tp.off[c] = off[c];
+    for (int c = 0; c < n_chunks; ++c) {
+        const int64_t rows = off[c + 1] - off[c];
+        int64_t g = std::max<int64_t>(1, (int64_t)std::llround((double)per * (double)rows / (double)N));
+        g = std::min<int64_t>(g, tc ? (rows + 127) / 128 : (rows + 255) / 256);
+        tp.blk[c + 1] = tp.blk[c] + (int)std::max<int64_t>(1, g);
+    }
+    return tp.blk[n_chunks];
+}
+
+int default_per(int sms, int64_t N, int M, bool tc)
+{
+    PqPass base;
+    base.N = N;
+    base.M = M;
+    return tc ? std::max(1, sms / std::max(1, M / tc_pass_group())) : pq_pass_blocks_per_subspace(base);
+}
+
+// Tuned block counts of the batched pass, keyed by the shape of the problem.
+using TuneKey = std::tuple<int, int64_t, int, int, int, int, int, uint64_t>;
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+
+TuneKey tune_key(const int64_t *off, int n_chunks, int D, int M, int Ks, int prec, int sms)
+{
+    uint64_t h = 1469598103934665603ull;  // FNV-1a over the chunk offsets
+    for (int c = 0; c <= n_chunks; ++c) {
+        h ^= (uint64_t)off[c];
+        h *= 1099511628211ull;
+    }
+    return TuneKey(n_chunks, off[n_chunks], D, M, Ks, prec, sms, h);
+}
+
 }  // namespace
 
 int run_pq_fit_chunked(const float *X, const int64_t *off, int n_chunks, int D, int M, int Ks, int iters,
@@ -86,22 +129,16 @@ int run_pq_fit_chunked(const float *X, const int64_t *off, int n_chunks, int D, 
     }
     PQ_TRY(launch_kmeanspp_chunks(X, D, ch.data(), n_chunks, ds, M, Ks, Cl, ws, err, s, "kmeanspp_chunks"));
 
-    // (2) batched Lloyd iterations: blocks shared out in proportion to the rows
-    ChunkTableParams tp;
-    tp.n = n_chunks;
-    tp.blk[0] = 0;
-    PqPass base;
-    base.N = N;
-    base.M = M;
-    const int per = tc ? std::max(1, sms / std::max(1, M / tc_pass_group())) : pq_pass_blocks_per_subspace(base);
-    for (int c = 0; c <= n_chunks; ++c) tp.off[c] = off[c];
-    for (int c = 0; c < n_chunks; ++c) {
-        const int64_t rows = off[c + 1] - off[c];
-        int64_t g = std::max<int64_t>(1, (int64_t)std::llround((double)per * (double)rows / (double)N));
-        g = std::min<int64_t>(g, tc ? (rows + 127) / 128 : (rows + 255) / 256);
-        tp.blk[c + 1] = tp.blk[c] + (int)std::max<int64_t>(1, g);
+    // (2) batched Lloyd iterations: blocks shared out in proportion to the rows, as many as
+    // the autotuner chose for this shape (pq_tune_chunked) or the default
+    int per = default_per(sms, N, M, tc);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(tune_key(off, n_chunks, D, M, Ks, prec, sms));
+        if (it != g_tuned.end()) per = it->second;
     }
-    const int gx = tp.blk[n_chunks];
+    ChunkTableParams tp;
+    const int gx = build_chunk_table(off, n_chunks, per, tc, tp);
     int64_t *d_off = ws.get<int64_t>((size_t)n_chunks + 1);
     int *d_blk = ws.get<int>((size_t)n_chunks + 1);
     int *d_bc = ws.get<int>((size_t)gx);
@@ -160,6 +197,108 @@ int run_pq_fit_chunked(const float *X, const int64_t *off, int n_chunks, int D, 
         *rmse = std::sqrt(h / ((double)N * (double)D));
     }
     return ws.status;
+}
+
+int run_pq_tune_chunked(const float *X, const int64_t *off, int n_chunks, int D, int M, int Ks, int prec,
+                        int *best_per, float *best_ms, cudaStream_t s)
+{
+    const int64_t N = off[n_chunks];
+    const int ds = D / M;
+    const bool tc = prec == PQ_PREC_BF16;
+    int dev = 0, sms = 0;
+    PQ_TRY_CUDA(cudaGetDevice(&dev));
+    PQ_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int *err = device_error_word(dev);
+    if (!err) return fail(PQ_ENOMEM, "device error word");
+    Scratch ws(s);
+    const size_t cbsz = (size_t)M * Ks * ds;
+    float *Cl = ws.get<float>((size_t)n_chunks * cbsz);
+    if (ws.status) return ws.status;
+    // realistic codebooks: the local seeds of every chunk
+    std::vector<SeedChunk> ch(n_chunks);
+    for (int c = 0; c < n_chunks; ++c) {
+        ch[c].r0 = off[c];
+        ch[c].rows = off[c + 1] - off[c];
+        ch[c].seed = rng_draw(0x7E57ull, kStreamChunk, (uint64_t)c);
+    }
+    PQ_TRY(launch_kmeanspp_chunks(X, D, ch.data(), n_chunks, ds, M, Ks, Cl, ws, err, s, "kmeanspp_chunks"));
+    // candidate block counts around the default; the part buffers are sized for the largest
+    const int base = default_per(sms, N, M, tc);
+    const double scales[] = {0.5, 0.75, 1.0, 1.25, 1.5, 2.0, 3.0, 4.0};
+    std::vector<int> cand;
+    for (double f : scales) {
+        const int v = std::max(1, (int)std::llround(base * f));
+        if (std::find(cand.begin(), cand.end(), v) == cand.end()) cand.push_back(v);
+    }
+    ChunkTableParams tp;
+    int gmax = 0;
+    for (int v : cand) gmax = std::max(gmax, build_chunk_table(off, n_chunks, v, tc, tp));
+    int64_t *d_off = ws.get<int64_t>((size_t)n_chunks + 1);
+    int *d_blk = ws.get<int>((size_t)n_chunks + 1);
+    int *d_bc = ws.get<int>((size_t)gmax);
+    double *part = ws.get<double>((size_t)gmax * M * Ks * ds);
+    int *part_cnt = ws.get<int>((size_t)gmax * M * Ks);
+    if (ws.status) return ws.status;
+    cudaEvent_t e0, e1;
+    PQ_TRY_CUDA(cudaEventCreate(&e0));
+    PQ_TRY_CUDA(cudaEventCreate(&e1));
+    int best = base;
+    float bms = 1e30f;
+    int st = PQ_OK;
+    for (int v : cand) {
+        const int gx = build_chunk_table(off, n_chunks, v, tc, tp);
+        chunk_tables_kernel<<<(std::max(n_chunks + 1, gx) + 127) / 128, 128, 0, s>>>(tp, gx, d_off, d_blk, d_bc);
+        count_launch();
+        PqPass p;
+        p.X = X;
+        p.N = N;
+        p.D = D;
+        p.M = M;
+        p.Ks = Ks;
+        p.ds = ds;
+        p.C = Cl;
+        p.gx = gx;
+        p.part = part;
+        p.part_cnt = part_cnt;
+        p.blk_chunk = d_bc;
+        p.chunk_off = d_off;
+        p.chunk_blk = d_blk;
+        p.n_chunks = n_chunks;
+        // one pass to warm up, then the mean of three (the codebooks are not updated)
+        for (int r = 0; r < 4 && st == PQ_OK; ++r) {
+            if (r == 1) cudaEventRecord(e0, s);
+            st = tc ? launch_pq_pass_tc(p, s) : launch_pq_pass_f32(p, s);
+        }
+        if (st != PQ_OK) break;
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = cuda_check(cudaGetLastError(), "pq_tune_chunked");
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 3.0f;
+        if (ms < bms) {
+            bms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != PQ_OK) return st;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[tune_key(off, n_chunks, D, M, Ks, prec, sms)] = best;
+    }
+    if (best_per) *best_per = best;
+    if (best_ms) *best_ms = bms;
+    return ws.status;
+}
+
+void clear_tuning()
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned.clear();
 }
 
 }  // namespace pqgb

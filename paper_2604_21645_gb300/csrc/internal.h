@@ -125,4 +125,9 @@ int run_softpq_forward(const float *X, int64_t N, int D, int M, int Ks, const fl
 int run_softpq_backward(const float *X, int64_t N, int D, int M, int Ks, const float *C, float tau,
                         const float *grad_loss, float *dC, float *dX, cudaStream_t s);
 
+// ---- autotuner of the batched pass (chunked.cu) --------------------------
+int run_pq_tune_chunked(const float *X, const int64_t *off, int n_chunks, int D, int M, int Ks, int prec,
+                        int *best_per, float *best_ms, cudaStream_t s);
+void clear_tuning();
+
 }  // namespace pqgb

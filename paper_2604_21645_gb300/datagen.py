@@ -148,3 +148,10 @@ CHUNKED = Workload("chunked_64x_d96_m12", 0, 96, 12, 256, 20, 256, "cont", BASE_
 SOFTPQ = Workload("softpq_1m_d256_m32", 1_000_000, 256, 32, 256, 0, 256, "cont", BASE_SEED + 5, tau=0.1)
 
 WORKLOADS = {w.name: w for w in (PQ_SMALL, IVF_MEDIUM, PQ_10M, CHUNKED, SOFTPQ)}
+
+
+def chunk_offsets(w: Workload, n_chunks: int | None = None) -> np.ndarray:
+    """Row offsets (n_chunks + 1) of the lognormal chunks of a chunked workload."""
+    e = w.extra
+    sizes = chunk_sizes(n_chunks or w.n_chunks, e["median"], e["log_sigma"], e["lo"], e["hi"], w.seed)
+    return np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)

@@ -23,7 +23,7 @@ STATS_MAX_ITERS = 64
 EXPORTS = ("pq_fit", "pq_init_kmeanspp", "pq_encode", "pq_decode_rmse", "ivf_build", "ivf_search", "ivf_get_info",
            "ivf_copy_coarse", "ivf_copy_lists", "ivf_free", "pq_sync_status", "pq_last_error", "pq_launch_count",
            "pq_profile_enable", "pq_profile_collect", "pq_profile_names", "pq_lloyd_noalloc", "pq_fit_chunked",
-           "softpq_forward", "softpq_backward")
+           "softpq_forward", "softpq_backward", "pq_tune_chunked", "pq_tune_clear")
 
 
 class PqStats(C.Structure):
@@ -67,6 +67,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "pq_lloyd_noalloc": (i32, [p, i64, i32, i32, i32, i32, p, p, p]),
         "pq_fit_chunked": (i32, [p, C.POINTER(i64), i32, i32, i32, i32, i32, u64, i32, p, p, C.POINTER(dbl), p]),
         "softpq_forward": (i32, [p, i64, i32, i32, i32, p, C.c_float, p, p]),
+        "pq_tune_chunked": (i32, [p, C.POINTER(i64), i32, i32, i32, i32, i32, C.POINTER(i32), C.POINTER(C.c_float), p]),
+        "pq_tune_clear": (i32, []),
         "softpq_backward": (i32, [p, i64, i32, i32, i32, p, C.c_float, p, p, p, p]),
     }
     for name, (res, args) in sigs.items():
@@ -229,6 +231,24 @@ def softpq_backward(X: torch.Tensor, codebooks: torch.Tensor, tau: float, grad_l
         _check(_lib.softpq_backward(px, N, D, M, Ks, pc, float(tau), pg, C.c_void_p(dC.data_ptr()),
                                     C.c_void_p(dX.data_ptr()) if dX is not None else None, _stream(X)))
     return dC, dX
+
+
+def tune_chunked(X: torch.Tensor, chunk_offsets, M: int, Ks: int = 256, prec: str = "fp32"):
+    """Autotune the batched pass of fit_chunked for this shape; returns (CTAs per subspace group, pass ms)."""
+    px = _need(X, torch.float32, 2, "X")
+    N, D = X.shape
+    off = (C.c_int64 * len(chunk_offsets))(*[int(v) for v in chunk_offsets])
+    n_chunks = len(chunk_offsets) - 1
+    if n_chunks < 1 or off[n_chunks] != N:
+        raise ValueError("chunk_offsets must end at N")
+    ctas, ms = C.c_int32(0), C.c_float(0.0)
+    with torch.cuda.device(X.device):
+        _check(_lib.pq_tune_chunked(px, off, n_chunks, D, M, Ks, PREC[prec], C.byref(ctas), C.byref(ms), _stream(X)))
+    return ctas.value, ms.value
+
+
+def tune_clear():
+    _check(_lib.pq_tune_clear())
 
 
 def encode(X: torch.Tensor, codebooks: torch.Tensor, prec: str = "fp32", out: torch.Tensor | None = None,

@@ -78,6 +78,18 @@ def test_argument_errors_before_any_launch(lib):
     assert _status(lib, "ivf_build", vp(16), vp(16), i64(10), 32, 4, 2, 5, C.c_uint64(0), 0, None, None) == -1
     # search on a null index
     assert _status(lib, "ivf_search", None, vp(16), 256, vp(16), i64(4), 1, 10, vp(16), vp(16), None) == -1
+    # chunked form and its tuner: chunk smaller than Ks, offsets not starting at 0
+    off = (C.c_int64 * 3)(0, 10, 1000)
+    assert _status(lib, "pq_fit_chunked", vp(16), off, 2, 32, 4, 64, 5, C.c_uint64(0), 0, vp(16), vp(16), None,
+                   None) == -1
+    off2 = (C.c_int64 * 2)(5, 1000)
+    assert _status(lib, "pq_tune_chunked", vp(16), off2, 1, 32, 4, 64, 0, None, None, None) == -1
+    # soft PQ: tau must be positive, Ds must be 4, 8 or 16
+    f = lib.softpq_forward
+    f.restype = C.c_int
+    f.argtypes = [vp, i64, C.c_int32, C.c_int32, C.c_int32, vp, C.c_float, vp, vp]
+    assert f(vp(16), 10, 64, 8, 256, vp(16), 0.0, vp(16), None) == -1
+    assert f(vp(16), 10, 96, 8, 256, vp(16), 0.1, vp(16), None) == -5
 
 
 def test_launch_counter_starts_at_zero(lib):

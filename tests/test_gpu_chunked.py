@@ -93,3 +93,17 @@ def test_chunked_capturable_in_cuda_graph(pq, case):
     g.replay()
     torch.cuda.synchronize()
     assert_codebooks_close(out[0].cpu().numpy(), gC)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_autotuned_chunked_matches_oracle(pq, case, prec):
+    """The tuner picks a CTA distribution for the batched pass; results stay within the oracle bars."""
+    X, off, (gC, codes_ref, rmse_ref, local) = case
+    Xd = dev(X)
+    pq.tune_clear()
+    ctas, ms = pq.tune_chunked(Xd, off.tolist(), 4, 64, prec=prec)
+    assert ctas >= 1 and ms > 0.0
+    cb, codes, rmse = pq.fit_chunked(Xd, off.tolist(), 4, 64, iters=5, seed=77, prec=prec)
+    assert_codebooks_close(cb.cpu().numpy(), gC)
+    assert abs(rmse - rmse_ref) <= RMSE_RTOL * rmse_ref
+    pq.tune_clear()
