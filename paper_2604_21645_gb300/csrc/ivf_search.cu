@@ -25,7 +25,7 @@ int launch_coarse_all_scores(const float *Q, int64_t nq, int D, const float *C, 
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kCap = 2048;  // candidate buffer entries per query
+constexpr int kMaxProbe = 256;  // probed lists per query held in shared memory
 
 struct Cand {
     float d;
@@ -149,89 +149,190 @@ __device__ __forceinline__ void load_codes(const uint8_t *p, uint8_t (&c)[M])
     }
 }
 
-// Sort the buffer, keep the first k, return the new threshold.
-__device__ float compact(Cand *buf, int *count, int k)
+constexpr int kScanThreads = 256;
+constexpr int kSelCap = 2048;   // candidate buffer entries per query
+constexpr int kSamples = 512;   // codes scored first to set the candidate threshold
+
+// In-place ascending bitonic sort of n (power of two) entries by every thread of the block.
+__device__ void bitonic_sort_n(Cand *v, int n)
 {
-    const int n = *count;
-    for (int i = n + threadIdx.x; i < kCap; i += blockDim.x) { buf[i].d = FLT_MAX; buf[i].id = 0x7fffffff; }
-    bitonic_sort(buf, kCap);
-    const int keep = min(n, k);
-    float tau = (n >= k) ? buf[k - 1].d : FLT_MAX;
+    for (int size = 2; size <= n; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < (n >> 1); i += blockDim.x) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                Cand x = v[lo], y = v[hi];
+                if (cand_less(y, x) == up) { v[lo] = y; v[hi] = x; }
+            }
+        }
+    }
     __syncthreads();
-    if (threadIdx.x == 0) *count = keep;
-    __syncthreads();
-    return tau;
 }
 
-template <int M>
-__global__ void __launch_bounds__(kThreads) adc_scan_kernel(const float *__restrict__ Q, int D, int Ks,
-                                                            const float *__restrict__ codebooks,
-                                                            const int32_t *__restrict__ probes, int nprobe,
-                                                            const int64_t *__restrict__ offsets,
-                                                            const int64_t *__restrict__ ids,
-                                                            const uint8_t *__restrict__ list_codes, int k,
-                                                            int64_t *__restrict__ out_ids, float *__restrict__ out_d)
+template <int M, int KS>
+__device__ __forceinline__ float adc_score(const float *lut, const uint8_t *code)
+{
+    uint8_t c[M];
+    load_codes<M>(code, c);
+    float d = 0.0f;
+#pragma unroll
+    for (int m = 0; m < M; ++m) d += lut[m * KS + c[m]];
+    return d;
+}
+
+// Scan of one query (one block), in two phases.  (1) A threshold: the scores of
+// kSamples codes spread evenly over the probed lists are sorted and the one at about
+// twice the expected rank of k is taken.  (2) Every probed code is scored and the
+// ones at or below the threshold (all ties included) go to the candidate buffer,
+// which is sorted by (score, id) at the end.  If the threshold turns out too tight
+// (fewer than k candidates) or too loose (buffer full), the scan is repeated with the
+// threshold at +inf and the buffer compacted by sorting whenever it fills.
+template <int M, int KS>
+__global__ void __launch_bounds__(kScanThreads) adc_scan_kernel(const float *__restrict__ Q, int D, int Ks,
+                                                                const float *__restrict__ codebooks,
+                                                                const int32_t *__restrict__ probes, int nprobe,
+                                                                const int64_t *__restrict__ offsets,
+                                                                const int64_t *__restrict__ ids,
+                                                                const uint8_t *__restrict__ list_codes, int k,
+                                                                int64_t *__restrict__ out_ids, float *__restrict__ out_d)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *lut = reinterpret_cast<float *>(smem_raw);                 // [M][Ks]
-    Cand *buf = reinterpret_cast<Cand *>(lut + (size_t)M * Ks);       // [kCap]
-    __shared__ int s_count;
+    float *lut = reinterpret_cast<float *>(smem_raw);                 // [M][KS]
+    Cand *buf = reinterpret_cast<Cand *>(lut + M * KS);               // [kSelCap]
+    __shared__ int64_t s_beg[kMaxProbe];
+    __shared__ int s_pre[kMaxProbe + 1];
+    __shared__ int s_count, s_n;
     const int64_t q = blockIdx.x;
     const float *qv = Q + q * D;
     const int ds = D / M;
-    for (int e = threadIdx.x; e < M * Ks; e += kThreads) {
-        const int m = e / Ks, kk = e % Ks;
-        const float *c = codebooks + ((size_t)m * Ks + kk) * ds;
+    for (int e = threadIdx.x; e < M * KS; e += kScanThreads) {
+        const int m = e / KS, kk = e % KS;
         float acc = 0.0f;
-        for (int j = 0; j < ds; ++j) {
-            const float t = qv[m * ds + j] - c[j];
-            acc = fmaf(t, t, acc);
+        if (kk < Ks) {
+            const float *c = codebooks + ((size_t)m * Ks + kk) * ds;
+            for (int j = 0; j < ds; ++j) {
+                const float t = qv[m * ds + j] - c[j];
+                acc = fmaf(t, t, acc);
+            }
         }
         lut[e] = acc;
     }
-    if (threadIdx.x == 0) s_count = 0;
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int p = 0; p < nprobe; ++p) {
+            const int l = probes[q * nprobe + p];
+            s_beg[p] = offsets[l];
+            s_pre[p] = tot;
+            const int64_t len = offsets[l + 1] - offsets[l];
+            tot += (int)(len < 0x3fffffff - tot ? len : 0x3fffffff - tot);
+        }
+        s_pre[nprobe] = tot;
+        s_n = tot;
+        s_count = 0;
+    }
     __syncthreads();
+    const int n = s_n;
+    auto code_at = [&](int pos, int &p) -> const uint8_t * {
+        p = 0;
+        while (s_pre[p + 1] <= pos) ++p;
+        return list_codes + (size_t)(s_beg[p] + (pos - s_pre[p])) * M;
+    };
+    // ---- (1) threshold from a sorted sample --------------------------------
     float tau = FLT_MAX;
-    for (int p = 0; p < nprobe; ++p) {
-        const int l = probes[q * nprobe + p];
-        const int64_t beg = offsets[l], end = offsets[l + 1];
-        for (int64_t e0 = beg; e0 < end; e0 += kThreads) {
-            const int64_t e = e0 + threadIdx.x;
-            if (e < end) {
-                uint8_t c[M];
-                load_codes<M>(list_codes + e * M, c);
-                float d = 0.0f;
-#pragma unroll
-                for (int m = 0; m < M; ++m) d += lut[m * Ks + c[m]];
-                if (d <= tau) {
-                    const int slot = atomicAdd(&s_count, 1);
-                    buf[slot].d = d;
-                    buf[slot].id = (int)ids[e];
+    if (n > kSamples) {
+        for (int j = threadIdx.x; j < kSamples; j += kScanThreads) {
+            int p;
+            const int pos = (int)(((int64_t)j * n) / kSamples);
+            buf[j].d = adc_score<M, KS>(lut, code_at(pos, p));
+            buf[j].id = j;
+        }
+        bitonic_sort_n(buf, kSamples);
+        const int r = (int)(((int64_t)2 * k * kSamples + n - 1) / n) + 2;
+        tau = r < kSamples ? buf[r].d : FLT_MAX;
+        __syncthreads();
+    }
+    // ---- (2) filtered scan, repeated without a threshold if it missed -------
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        const bool stream = attempt == 1;  // threshold +inf, compaction by sorting
+        if (stream) tau = FLT_MAX;
+        if (threadIdx.x == 0) s_count = 0;
+        __syncthreads();
+        bool overflow = false;
+        for (int p = 0; p < nprobe; ++p) {
+            const int len = s_pre[p + 1] - s_pre[p];
+            const uint8_t *lc = list_codes + s_beg[p] * M;
+            const int64_t ib = s_beg[p];
+            for (int e0 = 0; e0 < len; e0 += kScanThreads) {
+                const int e = e0 + threadIdx.x;
+                if (e < len) {
+                    const float d = adc_score<M, KS>(lut, lc + (size_t)e * M);
+                    if (d <= tau) {
+                        const int slot = atomicAdd(&s_count, 1);
+                        if (slot < kSelCap) {
+                            buf[slot].d = d;
+                            buf[slot].id = (int)ids[ib + e];
+                        }
+                    }
+                }
+                if (stream) {
+                    __syncthreads();
+                    if (s_count > kSelCap - kScanThreads) {
+                        const int cnt = s_count;
+                        for (int i = cnt + threadIdx.x; i < kSelCap; i += kScanThreads) {
+                            buf[i].d = FLT_MAX;
+                            buf[i].id = 0x7fffffff;
+                        }
+                        bitonic_sort_n(buf, kSelCap);
+                        tau = cnt >= k ? buf[k - 1].d : FLT_MAX;
+                        __syncthreads();
+                        if (threadIdx.x == 0) s_count = min(cnt, k);
+                        __syncthreads();
+                    }
                 }
             }
-            __syncthreads();
-            if (s_count > kCap - kThreads) tau = compact(buf, &s_count, k);
         }
-    }
-    tau = compact(buf, &s_count, k);
-    const int n = s_count;
-    for (int r = threadIdx.x; r < k; r += kThreads) {
-        out_ids[q * k + r] = r < n ? (int64_t)buf[r].id : -1;
-        out_d[q * k + r] = r < n ? buf[r].d : __int_as_float(0x7f800000);
+        __syncthreads();
+        const int cnt = s_count;
+        overflow = cnt > kSelCap;
+        if (!stream && (overflow || (cnt < k && cnt < n))) continue;  // threshold missed: scan again
+        const int c = min(cnt, kSelCap);
+        int p2 = 1;
+        while (p2 < c) p2 <<= 1;
+        for (int i = c + threadIdx.x; i < p2; i += kScanThreads) { buf[i].d = FLT_MAX; buf[i].id = 0x7fffffff; }
+        bitonic_sort_n(buf, p2);
+        const int kk = min(c, k);
+        for (int r2 = threadIdx.x; r2 < k; r2 += kScanThreads) {
+            out_ids[q * k + r2] = r2 < kk ? (int64_t)buf[r2].id : -1;
+            out_d[q * k + r2] = r2 < kk ? buf[r2].d : __int_as_float(0x7f800000);
+        }
+        return;
     }
 }
 
-template <int M>
-int launch_scan(const SearchArgs &a, const int32_t *probes, cudaStream_t s)
+template <int M, int KS>
+int launch_scan_ks(const SearchArgs &a, const int32_t *probes, cudaStream_t s)
 {
-    const size_t smem = (size_t)M * a.Ks * sizeof(float) + kCap * sizeof(Cand);
-    PQ_TRY_CUDA(cudaFuncSetAttribute(adc_scan_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = (size_t)M * KS * sizeof(float) + kSelCap * sizeof(Cand);
+    PQ_TRY_CUDA(cudaFuncSetAttribute(adc_scan_kernel<M, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ProfScope ps("adc_scan", s);
-    adc_scan_kernel<M><<<(unsigned)a.nq, kThreads, smem, s>>>(a.Q, a.D, a.Ks, a.codebooks, probes, a.nprobe,
-                                                             a.offsets, a.ids, a.list_codes, a.k, a.out_ids, a.out_d);
+    adc_scan_kernel<M, KS><<<(unsigned)a.nq, kScanThreads, smem, s>>>(a.Q, a.D, a.Ks, a.codebooks, probes, a.nprobe,
+                                                                     a.offsets, a.ids, a.list_codes, a.k, a.out_ids,
+                                                                     a.out_d);
     count_launch();
     PQ_TRY_CUDA(cudaGetLastError());
     return PQ_OK;
+}
+
+// The LUT row length is a template parameter (codes index it with an immediate offset);
+// a codebook with fewer codewords uses the next supported length, its extra entries unused.
+template <int M>
+int launch_scan(const SearchArgs &a, const int32_t *probes, cudaStream_t s)
+{
+    if (a.nprobe > kMaxProbe) return fail(PQ_ENOTSUP, "nprobe=%d exceeds %d", a.nprobe, kMaxProbe);
+    if (a.Ks <= 64) return launch_scan_ks<M, 64>(a, probes, s);
+    return launch_scan_ks<M, 256>(a, probes, s);
 }
 
 }  // namespace

@@ -99,6 +99,22 @@ def test_search_pads_missing_results(pq):
     check_topk(ids, d, ref_ids, ref_d)
 
 
+def test_search_exact_ties_ordered_by_id(pq):
+    """Many rows with identical codes: every score ties, the k results are the lowest ids (Sec. 2.2 reading)."""
+    base = datagen.mixture(50, 32, 10, "int255", 8)
+    X = np.ascontiguousarray(np.tile(base, (400, 1)))  # 20,000 rows, 50 distinct
+    M, Ks, nlist = 4, 32, 8
+    cb, _ = orc.pq_fit(X[:5000], M, Ks, 2, 4)
+    codes = orc.pq_encode(X, cb)
+    ref = orc.ivf_build(X, codes, nlist, 2, 5)
+    idx = pq.IVFIndex.build(dev(X), dev(codes), nlist, iters=2, seed=5)
+    Q = datagen.queries(16, 32, 10, "int255", 8)
+    for nprobe, k in [(2, 100), (8, 1000)]:
+        ref_ids, ref_d, _ = orc.ivf_search(ref, cb, Q, nprobe, k)
+        ids, d = idx.search(dev(cb), dev(Q), nprobe, k)
+        check_topk(ids.cpu().numpy(), d.cpu().numpy(), ref_ids, ref_d)
+
+
 def test_search_argument_errors(pq, setup):
     idx, cb, Q = setup["idx"], dev(setup["cb"]), dev(setup["Q"])
     for nprobe, k in [(0, 10), (setup["nlist"] + 1, 10), (4, 0), (4, 1025)]:
