@@ -34,8 +34,8 @@
 //
 // Pipeline (one CTA per SM, a group of 2 subspaces, persistent over row tiles
 // of 128).  Warp 0 issues TMA loads of 128 x 16 float tiles (64B swizzle) into
-// three stages.  Warp 3 (the operand warp) turns each tile into the bf16 A
-// operands of both subspaces (two A stages).  Warps 1 and 2 issue the MMAs of
+// five stages.  Warp 3 (the operand warp) turns each tile into the bf16 A
+// operands of both subspaces (two A stages, so the loads run three tiles ahead).  Warps 1 and 2 issue the MMAs of
 // subspace 0 and 1.  Warps 4-7 and 8-11 (the epilogue
 // warpgroups; thread = row = TMEM lane) own subspace 0 and 1 and two 128-column
 // TMEM buffers each, one per codeword half: the MMA of a half is issued as soon
@@ -62,7 +62,7 @@ constexpr int TM = 128;     // rows per tile
 constexpr int KSMAX = 256;  // codewords
 constexpr int NH = 128;     // codewords per MMA (one TMEM buffer)
 constexpr int DS = 8;       // subspace width
-constexpr int NXS = 3;      // X stages
+constexpr int NXS = 5;      // X stages
 constexpr int NAS = 2;      // A stages
 // Warps per block must keep ceil(warps / 4) * 32 * registers within one SM sub-partition's
 // 16K registers: 12 warps leave room for the epilogue's double-buffered TMEM loads.
@@ -90,19 +90,21 @@ constexpr int OFF_SV = OFF_CNT + G * KSMAX * 4;        // [256 epilogue threads]
 constexpr int OFF_MISC = OFF_SV + 256 * 32 * 4;
 constexpr int MISC_BYTES = 512;
 constexpr int SMEM_BYTES = OFF_MISC + MISC_BYTES + 1024;  // + alignment slack
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory of the tensor-core pass exceeds one CTA's limit");
 
 // mbarrier slots in the misc area
-constexpr int MB_FULL = 0;     // [NXS]  TMA -> operand + epilogue warps
-constexpr int MB_EMPTY = 3;    // [NXS]  12 warps -> TMA
-constexpr int MB_AREADY = 6;   // [NAS][G] operand warpgroup (4 warps) -> MMA lane g
-constexpr int MB_AFREE = 10;   // [NAS][G] MMA completion -> operand warpgroup
-constexpr int MB_MMAF = 14;    // [G][2]  MMA completion of a half -> epilogue warpgroup g
-constexpr int MB_TFREE = 18;   // [G][2]  epilogue warpgroup g (4 warps) -> MMA lane g
-constexpr int MB_DRAIN = 22;   // [G]     final commit of MMA lane g
-constexpr int MB_COUNT = 24;
-constexpr int MISC_TSLOT = 8 * MB_COUNT;  // 192
-constexpr int MISC_MU = 256;              // [G][8] floats
-constexpr int MISC_BND = 320;             // [G][4] float bits
+constexpr int MB_FULL = 0;                       // [NXS]  TMA -> operand + epilogue warps
+constexpr int MB_EMPTY = MB_FULL + NXS;          // [NXS]  operand + epilogue warps -> TMA
+constexpr int MB_AREADY = MB_EMPTY + NXS;        // [NAS][G] operand warp -> MMA warp g
+constexpr int MB_AFREE = MB_AREADY + NAS * G;    // [NAS][G] MMA completion -> operand warp
+constexpr int MB_MMAF = MB_AFREE + NAS * G;      // [G][2]  MMA completion of a half -> epilogue warpgroup g
+constexpr int MB_TFREE = MB_MMAF + G * 2;        // [G][2]  epilogue warpgroup g (4 warps) -> MMA warp g
+constexpr int MB_DRAIN = MB_TFREE + G * 2;       // [G]     final commit of MMA warp g
+constexpr int MB_COUNT = MB_DRAIN + G;
+constexpr int MISC_TSLOT = 8 * MB_COUNT;
+constexpr int MISC_MU = 320;                     // [G][8] floats
+constexpr int MISC_BND = 384;                    // [G][4] float bits
+static_assert(MISC_TSLOT + 4 <= MISC_MU, "mbarriers overlap the misc data");
 
 constexpr float kC1 = 7.5e-5f;
 constexpr float kC2 = 2.7e-5f;
@@ -262,45 +264,90 @@ __device__ __forceinline__ float d2_fp32(const float *x, const float *c)
     return d;
 }
 
-// Exact decision among every codeword that may be the nearest: the codewords of the saved
-// chunk `bestj` whose scores reach the bound (bits of svmask) and all codewords of the
-// chunks in cmask.  FP32 direct differences (relative error below 1e-6 for Ds = 8), then
-// FP64 among the FP32 near-ties; ties to the lowest index -- the decision rule of the CPU
-// reference.  The row comes by value so that the caller's copy stays in registers.
-__device__ __noinline__ int decide_exact(float4 xa, float4 xb, const float *cb, unsigned svmask, int bestj,
-                                         unsigned cmask, int Ks)
+// Merge of two running (best, index, second-best) triples; ties of the best go to the lower index.
+__device__ __forceinline__ void top2_merge(float &d1, int &k1, float &d2, float e1, int j1, float e2)
 {
-    const float x[DS] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
-    Top2 t;
-    for (unsigned m = svmask; m; m &= m - 1) {
-        const int k = bestj * 32 + __ffs(m) - 1;
-        t.add(d2_fp32(x, cb + k * CB_STRIDE), k);
+    if (e1 < d1 || (e1 == d1 && j1 < k1)) {
+        d2 = fminf(d1, e2);
+        d1 = e1;
+        k1 = j1;
+    } else {
+        d2 = fminf(d2, e1);
     }
-    for (unsigned m = cmask; m; m &= m - 1) {
-        const int c = __ffs(m) - 1;
-        for (int k = c * 32; k < c * 32 + 32 && k < Ks; ++k) t.add(d2_fp32(x, cb + k * CB_STRIDE), k);
-    }
-    const float margin = 4e-6f * t.d2 + 1e-30f;
-    if (t.d2 - t.d1 > margin) return t.k1;
-    const float lim = t.d1 + margin;
-    double best = DBL_MAX;
-    int bk = INT_MAX;
-    auto fp64 = [&](int k) {
-        const float *c = cb + k * CB_STRIDE;
-        if (d2_fp32(x, c) <= lim) {
-            const double e = d2_fp64(x, c, DS);
-            if (e < best || (e == best && k < bk)) {
-                best = e;
-                bk = k;
-            }
+}
+
+// Exact decision for the uncertain rows of a warp, warp-cooperatively.  The warp takes
+// the uncertain lanes one at a time; each lane scores one candidate codeword of that row
+// per pass -- the codewords of the saved chunk `bestj` whose scores reach the bound (bits
+// of svmask), then all codewords of the chunks in cmask -- by FP32 direct differences
+// (relative error below 1e-6 for Ds = 8), and a warp reduction gives the best and
+// second-best distances (ties to the lower index).  Unless the FP32 gap settles it, the
+// candidates within the FP32 margin are compared in FP64 (ties to the lower index) -- the
+// decision rule of the CPU reference.  Every lane of the warp must call this.
+__device__ __forceinline__ void decide_exact_warp(bool unsure, float4 v0, float4 v1, const float *cb,
+                                                  unsigned svmask, int bestj, unsigned cmask, int Ks, int &code)
+{
+    const int lane = threadIdx.x & 31;
+    for (unsigned todo = __ballot_sync(0xffffffffu, unsure); todo; todo &= todo - 1) {
+        const int u = __ffs(todo) - 1;
+        const float x[DS] = {__shfl_sync(0xffffffffu, v0.x, u), __shfl_sync(0xffffffffu, v0.y, u),
+                             __shfl_sync(0xffffffffu, v0.z, u), __shfl_sync(0xffffffffu, v0.w, u),
+                             __shfl_sync(0xffffffffu, v1.x, u), __shfl_sync(0xffffffffu, v1.y, u),
+                             __shfl_sync(0xffffffffu, v1.z, u), __shfl_sync(0xffffffffu, v1.w, u)};
+        const unsigned sm = __shfl_sync(0xffffffffu, svmask, u);
+        const unsigned cm = __shfl_sync(0xffffffffu, cmask, u);
+        const int bj = __shfl_sync(0xffffffffu, bestj, u);
+        float d1 = FLT_MAX, d2 = FLT_MAX;
+        int k1 = INT_MAX;
+        if ((sm >> lane) & 1u) {
+            const int k = bj * 32 + lane;
+            top2_merge(d1, k1, d2, d2_fp32(x, cb + k * CB_STRIDE), k, FLT_MAX);
         }
-    };
-    for (unsigned m = svmask; m; m &= m - 1) fp64(bestj * 32 + __ffs(m) - 1);
-    for (unsigned m = cmask; m; m &= m - 1) {
-        const int c = __ffs(m) - 1;
-        for (int k = c * 32; k < c * 32 + 32 && k < Ks; ++k) fp64(k);
+        for (unsigned m = cm; m; m &= m - 1) {
+            const int k = (__ffs(m) - 1) * 32 + lane;
+            if (k < Ks) top2_merge(d1, k1, d2, d2_fp32(x, cb + k * CB_STRIDE), k, FLT_MAX);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float e1 = __shfl_xor_sync(0xffffffffu, d1, o);
+            const int j1 = __shfl_xor_sync(0xffffffffu, k1, o);
+            const float e2 = __shfl_xor_sync(0xffffffffu, d2, o);
+            top2_merge(d1, k1, d2, e1, j1, e2);
+        }
+        int result = k1;
+        const float margin = 4e-6f * d2 + 1e-30f;
+        if (!(d2 - d1 > margin)) {
+            const float lim = d1 + margin;
+            double best = DBL_MAX;
+            int bk = INT_MAX;
+            auto fp64 = [&](int k) {
+                const float *c = cb + k * CB_STRIDE;
+                if (d2_fp32(x, c) <= lim) {
+                    const double e = d2_fp64(x, c, DS);
+                    if (e < best || (e == best && k < bk)) {
+                        best = e;
+                        bk = k;
+                    }
+                }
+            };
+            if ((sm >> lane) & 1u) fp64(bj * 32 + lane);
+            for (unsigned m = cm; m; m &= m - 1) {
+                const int k = (__ffs(m) - 1) * 32 + lane;
+                if (k < Ks) fp64(k);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double e = __shfl_xor_sync(0xffffffffu, best, o);
+                const int j = __shfl_xor_sync(0xffffffffu, bk, o);
+                if (e < best || (e == best && j < bk)) {
+                    best = e;
+                    bk = j;
+                }
+            }
+            result = bk;
+        }
+        if (lane == u) code = result;
     }
-    return bk;
 }
 
 // Fixed-point format of the residual sums of one CTA and subspace.  A residual
@@ -487,8 +534,8 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
         if (lane == 0) {
             const int g = warp - 1;
             for (int i = 0; i < n_my; ++i) {
-                const int as = i & 1;
-                if (!mbar_wait(bar(MB_AREADY + as * G + g), (i >> 1) & 1, a.err)) break;
+                const int as = i % NAS;
+                if (!mbar_wait(bar(MB_AREADY + as * G + g), (i / NAS) & 1, a.err)) break;
                 bool ok = true;
                 for (int h = 0; h < 2 && ok; ++h) {
                     if (i >= 1 && !mbar_wait(bar(MB_TFREE + g * 2 + h), (i - 1) & 1, a.err)) {
@@ -514,7 +561,7 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
         // ---- operand warp: bf16 A operands of both subspaces, rows t + 32 rr
         const int t = tid - kOp0;
         for (int i = 0; i < n_my; ++i) {
-            const int s = i % NXS, as = i & 1;
+            const int s = i % NXS, as = i % NAS;
             if (!__all_sync(0xffffffffu, mbar_wait(bar(MB_FULL + s), (i / NXS) & 1, a.err))) break;
             const float *stage = xs + s * (XS_BYTES / 4);
             float4 v[kOpRows][4];
@@ -529,7 +576,7 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 if (i >= NAS &&
-                    !__all_sync(0xffffffffu, mbar_wait(bar(MB_AFREE + as * G + g), ((i >> 1) - 1) & 1, a.err))) {
+                    !__all_sync(0xffffffffu, mbar_wait(bar(MB_AFREE + as * G + g), ((i / NAS) - 1) & 1, a.err))) {
                     ok = false;
                     break;
                 }
@@ -664,14 +711,15 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
             const int ti = (int)tally;
             int code = bestj * 32 + (ti >> 6);
             const bool valid = row < r1;
-            if (valid && !((ti & 63) == 1 && cm2 < theta)) {
+            const bool unsure = valid && !((ti & 63) == 1 && cm2 < theta);
+            if (__any_sync(0xffffffffu, unsure)) {
                 unsigned cmask = 0, svmask = 0;
 #pragma unroll
                 for (int c = 0; c < KSMAX / 32; ++c) cmask |= (c != bestj && cmx[c] >= theta) ? (1u << c) : 0u;
 #pragma unroll
                 for (int q = 0; q < 32; ++q) svmask |= (sv[q] >= theta) ? (1u << q) : 0u;
-                code = decide_exact(v0, v1, cbg, svmask, bestj, cmask, Ks);
-                ++rechecks;
+                decide_exact_warp(unsure, v0, v1, cbg, svmask, bestj, cmask, Ks, code);
+                rechecks += unsure ? 1u : 0u;
             }
             if (valid) {
                 const float *c = cbg + code * CB_STRIDE;
