@@ -232,6 +232,26 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
+// max of three FP32 values in one instruction
+__device__ __forceinline__ float fmax3(float a, float b, float c)
+{
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// maximum of 32 scores: a three-input tree (17 instructions)
+__device__ __forceinline__ float max32(const float *v)
+{
+    float a[11];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) a[i] = fmax3(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
+    a[10] = fmaxf(v[30], v[31]);
+    const float b0 = fmax3(a[0], a[1], a[2]), b1 = fmax3(a[3], a[4], a[5]), b2 = fmax3(a[6], a[7], a[8]);
+    const float b3 = fmaxf(a[9], a[10]);
+    return fmaxf(fmax3(b0, b1, b2), b3);
+}
+
 // 16-byte chunk c (0..3) of row r in a 64B-swizzled TMA stage (row = 64 bytes)
 __device__ __forceinline__ const float4 *xs_chunk(const float *stage, int r, int c)
 {
@@ -663,14 +683,7 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
                 }
                 if (j + 1 < KSMAX / 32) TC_LD32(tl + (uint32_t)((j + 1) * 32), vb[(j + 1) & 1]);
                 const float *v = vb[j & 1];
-                float m16[16];
-#pragma unroll
-                for (int q = 0; q < 16; ++q) m16[q] = fmaxf(v[2 * q], v[2 * q + 1]);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) m16[q] = fmaxf(m16[2 * q], m16[2 * q + 1]);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) m16[q] = fmaxf(m16[2 * q], m16[2 * q + 1]);
-                const float cm = fmaxf(fmaxf(m16[0], m16[1]), fmaxf(m16[2], m16[3]));
+                const float cm = max32(v);
                 cmx[j] = cm;
                 const bool better = cm > best;
                 cm2 = better ? best : fmaxf(cm2, cm);
