@@ -150,6 +150,18 @@ def kernel_work(name, w, n_launch_rows):
     return None, None, None, None
 
 
+def measured_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu capture, or None if absent or the kernel changed since."""
+    try:
+        with open(TRAFFIC_PATH) as f:
+            tr = json.load(f).get(kernel)
+        if tr and tr.get("source_hash") == source_hash(*tr["sources"]):
+            return tr.get("per_workload", {}).get(workload)
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
 def roofline(kern, w, peaks, peak_src):
     """Roofline record of the kernel with the largest share of the timed region."""
     if not kern:
@@ -172,14 +184,7 @@ def roofline(kern, w, peaks, peak_src):
     else:
         achieved, peak = work / avg_s / 1e12, fp32_peak_tflops(peaks)
         src = "152 SMs x 128 FP32 lanes x 2 flop per FFMA x max SM clock"
-    traffic = None
-    try:
-        with open(TRAFFIC_PATH) as f:
-            tr = json.load(f).get(dominant)
-        if tr and tr.get("source_hash") == source_hash(*tr["sources"]) and tr.get("workload") == w.name:
-            traffic = tr["bytes_per_launch"]
-    except (OSError, KeyError, ValueError):
-        traffic = None
+    traffic = measured_traffic(dominant, w.name)
     return {"kernel": dominant, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak, "traffic": traffic, "peak_source": src, "avg_launch_ms": avg_s * 1e3,
             "share": share}
@@ -431,7 +436,7 @@ def run_gpu_chunked(args):
         ach = work / secs / 1e12
         peak = compare_peak_t(peaks) if kind == "cmp" else fp32_peak_tflops(peaks)
         roof = {"kernel": pname, "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-                "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (derived)",
+                "traffic": measured_traffic(pname, w.name), "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (derived)",
                 "avg_launch_ms": kern[pname]["ms"] / max(kern[pname]["launches"], 1),
                 "share": kern[pname]["ms"] / max(sum(v["ms"] for v in kern.values()), 1e-9)}
     cfg = {"workload": w.name, "N": N, "n_chunks": w.n_chunks, "D": w.d, "M": w.m, "Ks": w.ks, "iters": w.iters,
@@ -507,7 +512,7 @@ def run_gpu_softpq(args):
         ach = scores * per / secs / 1e12
         peak = fp32_peak_tflops(peaks)
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2 flop per FFMA x max SM clock",
+                "traffic": measured_traffic(dom, w.name), "peak_source": "152 SMs x 128 FP32 lanes x 2 flop per FFMA x max SM clock",
                 "avg_launch_ms": secs * 1e3,
                 "share": kern[dom]["ms"] / max(sum(v["ms"] for v in kern.values()), 1e-9)}
     # e2e: rows and codebooks from pinned host memory, gradients and loss back
