@@ -15,12 +15,13 @@
 // within twice the bound; every other row goes to the FP64 re-check queue
 // (coarse.cu), so the list of every row is exact.
 //
-// Pipeline, one CTA (192 threads) per SM, persistent over 128-row tiles:
+// Pipeline, one CTA (224 threads) per SM, persistent over 128-row tiles:
 // lane 0 of warp 0 loads the X tile by TMA (128B-swizzled 32-column boxes),
-// lane 1 of warp 0 streams the pre-tiled B operand (8 KB tiles, bulk copies)
-// through a 4-slot ring, lane 0 of warp 1 issues M=128 N=256 K=16 MMAs into two
-// TMEM accumulators (256 centroids each), warps 2-5 build the A operand and run
-// the epilogue.  Every wait is bounded.
+// lane 0 of warp 2 streams the pre-tiled B operand (8 KB tiles, bulk copies)
+// through an 8-slot ring (each producer in a warp of its own, so one's wait
+// never stalls the other), lane 0 of warp 1 issues M=128 N=256 K=16 MMAs into
+// two TMEM accumulators (256 centroids each), warps 3-6 build the A operand and
+// run the epilogue.  Every wait is bounded.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -38,10 +39,11 @@ constexpr int TM = 128;
 constexpr int NBLK = 256;            // centroids per MMA / TMEM accumulator
 constexpr int DMAX = 128;
 constexpr int KDMAX = DMAX / 16;     // K steps of one term
-constexpr int kThreads = 64 + 128;
+constexpr int kThreads = 96 + 128;  // X-load warp, MMA warp, B-load warp, epilogue warpgroup
+constexpr int kEpi0 = 96;
 constexpr int A_TILE = TM * 16 * 2;  // 4 KB
 constexpr int B_TILE = NBLK * 16 * 2;  // 8 KB
-constexpr int RING = 4;
+constexpr int RING = 8;
 constexpr int XBOX = TM * 32 * 4;    // 16 KB, one 32-column box
 constexpr int OFF_X = 0;                                  // 4 boxes
 constexpr int OFF_A = OFF_X + (DMAX / 32) * XBOX;        // (2*KD + 1) tiles
@@ -273,8 +275,10 @@ __global__ void __launch_bounds__(kThreads, 1) coarse_tc_kernel(const __grid_con
                 ++issued;
             }
             if (issued) mbar_wait(smem_u32(mb + MB_XFULL), (issued - 1) & 1, a.err);
-        } else if (lane == 1) {
-            // B tiles in MMA order through the ring
+        }
+    } else if (warp == 2) {
+        if (lane == 0) {
+            // B tiles in MMA order through the ring (a warp of its own: its waits never hold up the X loads)
             int z = 0;
             bool ok = true;
             for (int i = 0; i < n_my && ok; ++i)
@@ -328,8 +332,8 @@ __global__ void __launch_bounds__(kThreads, 1) coarse_tc_kernel(const __grid_con
                 mma_commit(smem_u32(mb + MB_AFREE));
             }
         }
-    } else {
-        const int q = warp & 3;
+    } else if (warp >= kEpi0 / 32) {
+        const int q = warp & 3;  // TMEM lane quadrant of this warp
         const int r = q * 32 + lane;
         const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
         const float nmax = __uint_as_float(a.maxbits[0]) * (1.0f + 1e-5f);

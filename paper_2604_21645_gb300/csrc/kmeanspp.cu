@@ -51,6 +51,8 @@ struct KppArgs {
     int bps;
     int ncache;                   // points per block kept in shared memory
     int nb_pad;                   // floats of the per-block D2 copy (multiple of 4)
+    float *gpts;                  // [groups][bps][ustride][ds] the other points, gathered contiguously
+    int ustride;                  // points per block in gpts
     SeedChunk ch[kMaxSeedChunks];
 };
 
@@ -236,7 +238,12 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
     auto point = [&](int64_t i) -> const float * { return Pm + (ck.r0 + (sub ? sub[i] : i)) * a.ld; };
     const bool vec_ok = (ds & 3) == 0 && (a.ld & 3) == 0 && (reinterpret_cast<uintptr_t>(Pm) & 15) == 0;
     const int ncache = vec_ok ? min(cnt, a.ncache) : 0;
+    // a block alone in its group walks only its own shared-memory D2 copy: no global copy
+    const bool solo = a.bps == 1;
     float *s_d2 = reinterpret_cast<float *>(s_dyn);
+    // points past the shared-memory cache, gathered into a contiguous copy at round 0
+    float *gp0 = (a.gpts && vec_ok) ? a.gpts + ((size_t)grp * a.bps + b) * a.ustride * ds : nullptr;
+    auto upoint = [&](int i) -> const float * { return gp0 ? gp0 + (size_t)(i - ncache) * ds : point(i0 + i); };
     const float4 *pts4 = s_dyn + a.nb_pad / 4;
     float4 *pts4w = s_dyn + a.nb_pad / 4;
     unsigned *bar = a.bars + 2 * grp;
@@ -275,11 +282,28 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
                 }
             }
             d = acc;
+        } else if (gp0) {
+            const float *x = point(i0 + i);
+            float *dst = gp0 + (size_t)(i - ncache) * ds;
+            float acc = 0.0f;
+            for (int q = 0; q < ds / 4; ++q) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(x) + q);
+                reinterpret_cast<float4 *>(dst)[q] = v;
+                const float4 cc = *reinterpret_cast<const float4 *>(s_center + 4 * q);
+                const float e[4] = {v.x, v.y, v.z, v.w};
+                const float f[4] = {cc.x, cc.y, cc.z, cc.w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const float t = __fsub_rn(e[r], f[r]);
+                    acc = __fadd_rn(acc, __fmul_rn(t, t));
+                }
+            }
+            d = acc;
         } else {
             d = d2_f32_exact(point(i0 + i), s_center, ds);
         }
         s_d2[i] = d;
-        d2m[plane + i0 + i] = d;  // buffer 1 holds D2 for round 1
+        if (!solo) d2m[plane + i0 + i] = d;  // buffer 1 holds D2 for round 1
         lmax = fmaxf(lmax, d);
     }
 #pragma unroll
@@ -318,26 +342,59 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
             for (; i < ncache; i += kThreads) {
                 const float d = fminf(d2_f32_smem(pts4, ncache, i, s_center, ds), s_d2[i]);
                 s_d2[i] = d;
-                D2c[i0 + i] = d;
+                if (!solo) D2c[i0 + i] = d;
                 part += weight(d, sh, any);
+            }
+            if (vec_ok && ds == 8) {
+                // eight uncached points per thread, all their loads in flight before the sums
+                for (; i + 7 * kThreads < cnt; i += 8 * kThreads) {
+                    float4 u[8][2];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 *x4 = reinterpret_cast<const float4 *>(upoint(i + q * kThreads));
+                        u[q][0] = __ldg(x4);
+                        u[q][1] = __ldg(x4 + 1);
+                    }
+                    const float4 c0 = *reinterpret_cast<const float4 *>(s_center);
+                    const float4 c1 = *reinterpret_cast<const float4 *>(s_center + 4);
+                    const float f[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const float e[8] = {u[q][0].x, u[q][0].y, u[q][0].z, u[q][0].w,
+                                            u[q][1].x, u[q][1].y, u[q][1].z, u[q][1].w};
+                        float acc = 0.0f;
+#pragma unroll
+                        for (int r = 0; r < 8; ++r) {
+                            const float t = __fsub_rn(e[r], f[r]);
+                            acc = __fadd_rn(acc, __fmul_rn(t, t));
+                        }
+                        const int ii = i + q * kThreads;
+                        const float d = fminf(acc, s_d2[ii]);
+                        s_d2[ii] = d;
+                        if (!solo) D2c[i0 + ii] = d;
+                        part += weight(d, sh, any);
+                    }
+                }
             }
             if (vec_ok) {
                 for (; i + kThreads < cnt; i += 2 * kThreads) {
                     float d0, d1;
-                    d2_f32_exact2(point(i0 + i), point(i0 + i + kThreads), s_center, ds, d0, d1);
+                    d2_f32_exact2(upoint(i), upoint(i + kThreads), s_center, ds, d0, d1);
                     d0 = fminf(d0, s_d2[i]);
                     d1 = fminf(d1, s_d2[i + kThreads]);
                     s_d2[i] = d0;
                     s_d2[i + kThreads] = d1;
-                    D2c[i0 + i] = d0;
-                    D2c[i0 + i + kThreads] = d1;
+                    if (!solo) {
+                        D2c[i0 + i] = d0;
+                        D2c[i0 + i + kThreads] = d1;
+                    }
                     part += weight(d0, sh, any) + weight(d1, sh, any);
                 }
             }
             for (; i < cnt; i += kThreads) {
-                const float d = fminf(d2_f32_exact(point(i0 + i), s_center, ds), s_d2[i]);
+                const float d = fminf(d2_f32_exact(upoint(i), s_center, ds), s_d2[i]);
                 s_d2[i] = d;
-                D2c[i0 + i] = d;
+                if (!solo) D2c[i0 + i] = d;
                 part += weight(d, sh, any);
             }
         }
@@ -527,6 +584,8 @@ int launch_kmeanspp_chunks(const float *X, int64_t ld, const SeedChunk *chunks, 
     if ((int64_t)a.nb_pad * 4 > kDynSmemCap)
         return fail(PQ_ENOTSUP, "k-means++ seeding: %lld points per block exceed shared memory", (long long)nb);
     a.ncache = (ds % 4 == 0) ? (int)std::min<int64_t>(nb, (kDynSmemCap - (int64_t)a.nb_pad * 4) / (ds * 4)) : 0;
+    a.ustride = (ds % 4 == 0) ? (int)(a.nb_pad - a.ncache) : 0;
+    a.gpts = nullptr;
     const size_t dyn = (size_t)a.nb_pad * 4 + (size_t)a.ncache * ds * 4;
     PQ_TRY_CUDA(cudaFuncSetAttribute(kmeanspp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     if (n_chunks == 1) {
@@ -542,6 +601,7 @@ int launch_kmeanspp_chunks(const float *X, int64_t ld, const SeedChunk *chunks, 
     a.bars = ws.get<unsigned>(2 * (size_t)groups, true);
     a.bsum = ws.get<unsigned long long>(2 * (size_t)groups * bps, true);
     a.tags = ws.get<unsigned>(2 * (size_t)groups * bps, true);
+    if (a.ustride > 0) a.gpts = ws.get<float>((size_t)groups * bps * a.ustride * ds);
     a.d2 = ws.get<float>(2 * (size_t)groups * a.nmax);
     a.dmax_bits = ws.get<unsigned>((size_t)groups, true);
     if (ws.status) return ws.status;
