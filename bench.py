@@ -150,6 +150,22 @@ def kernel_work(name, w, n_launch_rows):
     return None, None, None, None
 
 
+def slowest_rank(values, world, device="cuda"):
+    """Element-wise maximum of per-rank timings over all ranks (the replica job ends with its slowest rank)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def replica_throughput(units_per_rank, seconds, world):
+    """Whole-job throughput of `world` replicas that each processed units_per_rank in (max) seconds."""
+    return world * units_per_rank / seconds
+
+
 def measured_traffic(kernel, workload):
     """DRAM bytes per launch from the committed ncu capture, or None if absent or the kernel changed since."""
     try:
@@ -267,15 +283,14 @@ def run_gpu(args):
     kern = pqgb.profile_collect()
     pqgb.profile_enable(False)
     _, rmse = pqgb.decode_rmse(codes, cbs, Xd)
+    _, est = pqgb.encode(Xd, cbs, prec=prec, stats=True)
+    near_ties = est["fp64_rechecks"] / (w.n * w.m)
 
     t_fe = (per_step[0] + per_step[1]) / 1e3
     t_step = per_step.sum() / 1e3
     t_search = per_step[3] / 1e3 if ivf else 0.0
-    if world > 1:
-        t = torch.tensor([t_fe, t_step, t_search], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_fe, t_step, t_search = t.tolist()
-    value = world * w.n / t_fe / 1e6
+    t_fe, t_step, t_search = slowest_rank([t_fe, t_step, t_search], world)
+    value = replica_throughput(w.n, t_fe, world) / 1e6
 
     # the plain FP32 form of the same fit + encode, for the precision comparison
     fp32_form = None
@@ -307,11 +322,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         if i >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
-    t_e2e = float(np.mean(e2e_ms)) / 1e3
-    if world > 1:
-        t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = t.item()
+    t_e2e = slowest_rank([float(np.mean(e2e_ms)) / 1e3], world)[0]
 
     peaks, peak_src = load_peaks()
     cfg = {"workload": w.name, "N": w.n, "D": w.d, "M": w.m, "Ks": w.ks, "iters": w.iters}
@@ -335,7 +346,9 @@ def run_gpu(args):
         "config": cfg,
         "phases_ms": dict(zip(names, per_step.tolist())),
         "rmse": rmse,
-        "e2e": {"value": world * w.n / t_e2e / 1e6, "unit": "Mvec/s", "h2d_bytes_per_step": int(X.nbytes),
+        "exact_rerank_fraction": near_ties,
+        "e2e": {"value": replica_throughput(w.n, t_e2e, world) / 1e6, "unit": "Mvec/s",
+                "h2d_bytes_per_step": int(X.nbytes),
                 "d2h_bytes_per_step": int(codes.numel() + cbs.numel() * 4)},
         "gpu_launches": int(launches),
         "kernels": kern,
