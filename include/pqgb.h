@@ -53,7 +53,8 @@ enum {
     PQ_ENOMEM = -2,   /* device scratch or host allocation failed           */
     PQ_ECUDA = -3,    /* a CUDA runtime call failed                         */
     PQ_ETIMEOUT = -4, /* a device-side bounded wait ran out                 */
-    PQ_ENOTSUP = -5   /* valid but unsupported shape/precision combination  */
+    PQ_ENOTSUP = -5,  /* valid but unsupported shape/precision combination  */
+    PQ_EINTERNAL = -6 /* a device-side consistency check failed             */
 };
 
 /* Arithmetic of the distance contraction used to find nearest centroids. */

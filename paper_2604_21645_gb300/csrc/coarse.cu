@@ -304,7 +304,12 @@ __global__ void bucket_hist_kernel(const int32_t *__restrict__ lst, int64_t N, i
     __syncthreads();
     const int64_t t0 = (int64_t)blockIdx.x * kTileRows;
     const int64_t t1 = min(N, t0 + kTileRows);
-    for (int64_t n = t0 + threadIdx.x; n < t1; n += blockDim.x) atomicAdd(s_hist + lst[n], 1);
+    // an index outside [0, nlist) is only left behind by a kernel that reported a device-side
+    // failure; both bucketing passes map it to list 0 so that no access leaves the histogram
+    for (int64_t n = t0 + threadIdx.x; n < t1; n += blockDim.x) {
+        const int l = lst[n];
+        atomicAdd(s_hist + ((unsigned)l < (unsigned)nlist ? l : 0), 1);
+    }
     __syncthreads();
     for (int l = threadIdx.x; l < nlist; l += blockDim.x) tile_cnt[(size_t)blockIdx.x * nlist + l] = s_hist[l];
 }
@@ -381,6 +386,7 @@ __global__ void bucket_scatter_kernel(const int32_t *__restrict__ lst, int64_t N
         const bool act = n < t1;
         const unsigned amask = __ballot_sync(0xffffffffu, act);
         int l = act ? lst[n] : -1;
+        if (act && (unsigned)l >= (unsigned)nlist) l = 0;  // as in bucket_hist_kernel
         const unsigned peers = __match_any_sync(0xffffffffu, l);
         if (act) {
             const int rank = __popc(peers & ((1u << lane) - 1u));

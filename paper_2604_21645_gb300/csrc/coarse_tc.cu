@@ -51,6 +51,7 @@ constexpr int OFF_RING = OFF_A + (2 * KDMAX + 1) * A_TILE;
 constexpr int OFF_MISC = OFF_RING + RING * B_TILE;
 constexpr int OFF_CMX = OFF_MISC + 1024;                  // [32 chunks][128 rows] chunk maxima
 constexpr int SMEM_BYTES = OFF_CMX + 32 * TM * 4 + 1024;
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory of one CTA");
 
 // mbarrier slots
 constexpr int MB_XFULL = 0, MB_XEMPTY = 1, MB_AREADY = 2, MB_AFREE = 3, MB_MMA = 4 /*2*/, MB_TFREE = 6 /*2*/,
@@ -215,7 +216,7 @@ __global__ void coarse_prep_kernel(const float *C, int nlist, int nlist_pad, int
 
 struct CoarseTcArgs {
     int64_t N;
-    int D, nlist_pad, tiles;
+    int D, nlist, nlist_pad, tiles;
     const unsigned char *Bp;
     const float *mu;
     const unsigned *maxbits;
@@ -441,7 +442,15 @@ __global__ void __launch_bounds__(kThreads, 1) coarse_tc_kernel(const __grid_con
             }
             if (row < a.N) {
                 if (nin == 1 && cm2 < theta) {
-                    a.list_of_row[row] = bestj * 32 + ib;
+                    const int l = bestj * 32 + ib;
+                    // a padded centroid scores -3e38 and can never be certified; should one be,
+                    // the scores were corrupt: report it instead of passing on an invalid list
+                    if (l < a.nlist) {
+                        a.list_of_row[row] = l;
+                    } else {
+                        a.list_of_row[row] = 0;
+                        atomicCAS(a.err, 0, PQ_EINTERNAL);
+                    }
                 } else {
                     uint32_t mask = 0;
                     if (NBT > 0) {
@@ -522,6 +531,7 @@ int launch_coarse_tc(const float *X, int64_t N, int D, const float *C, int nlist
     CoarseTcArgs a;
     a.N = N;
     a.D = D;
+    a.nlist = nlist;
     a.nlist_pad = nlist_pad;
     a.tiles = (int)((N + TM - 1) / TM);
     a.Bp = Bp;

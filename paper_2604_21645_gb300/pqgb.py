@@ -16,7 +16,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpqgb.so")
 
-PQ_OK, PQ_EINVAL, PQ_ENOMEM, PQ_ECUDA, PQ_ETIMEOUT, PQ_ENOTSUP = 0, -1, -2, -3, -4, -5
+PQ_OK, PQ_EINVAL, PQ_ENOMEM, PQ_ECUDA, PQ_ETIMEOUT, PQ_ENOTSUP, PQ_EINTERNAL = 0, -1, -2, -3, -4, -5, -6
 PQ_PREC_FP32, PQ_PREC_BF16 = 0, 1
 PREC = {"fp32": PQ_PREC_FP32, "bf16": PQ_PREC_BF16}
 STATS_MAX_ITERS = 64
