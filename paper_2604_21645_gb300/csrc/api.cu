@@ -467,14 +467,17 @@ int ivf_build(const float *X, const uint8_t *codes, int64_t N, int32_t D, int32_
     {
         Scratch ws(s);
         int32_t *lst = ws.get<int32_t>((size_t)N);
+        unsigned *xrange = ws.get<unsigned>(2);
         if (ws.status) return cleanup(ws.status);
         CoarseBound b{idx->half_norm, idx->maxes};
+        if (iters > 0) st = launch_x_exponent_range(X, N, D, xrange, s);
+        if (st) return cleanup(st);
         st = seed_codebooks(X, N, D, 1, nlist, seed, idx->coarse, ws, err, s, "kmeanspp_coarse");
         for (int t = 0; st == PQ_OK && t < iters; ++t) {
             st = launch_coarse_norms(idx->coarse, nlist, D, b, s);
             if (!st) st = coarse_assign(X, N, D, idx->coarse, nlist, b, lst, ws, prec, s);
             if (!st) st = bucket_rows(lst, N, nlist, nullptr, M, idx->offsets, idx->ids, nullptr, ws, s);
-            if (!st) st = launch_list_mean(X, D, idx->offsets, idx->ids, nlist, idx->coarse, s);
+            if (!st) st = launch_list_mean(X, D, idx->offsets, idx->ids, nlist, xrange, idx->coarse, s);
         }
         if (!st) st = launch_coarse_norms(idx->coarse, nlist, D, b, s);
         if (!st) st = coarse_assign(X, N, D, idx->coarse, nlist, b, lst, ws, prec, s);

@@ -407,25 +407,175 @@ __global__ void bucket_scatter_kernel(const int32_t *__restrict__ lst, int64_t N
     }
 }
 
-__global__ void list_mean_kernel(const float *__restrict__ X, int D, const int64_t *__restrict__ offsets,
-                                 const int64_t *__restrict__ ids, float *__restrict__ C)
+// List means (the centroid update of Sec. 2.2), each equal to the sum of the list's rows in
+// ascending row order in FP64, divided by the count and rounded to FP32.  The sequential FP64
+// sum is obtained without FP64 additions whenever it is exact: a column whose elements are all
+// multiples of 2^(e - 150) (e = the smallest biased exponent among them, subnormals counted as
+// 1) and whose sum of magnitudes is below 2^(e - 150 + 53) has every partial sum representable
+// in 53 bits, so each FP64 addition is exact and the sequential sum is the exact sum.  That sum
+// is accumulated exactly as a 128-bit integer in units of 2^(g - 150), g = the smallest exponent
+// of all of X, using integer instructions only.  A column that fails the test (or all columns,
+// when X spans too many binades for 128 bits or holds Inf/NaN) is summed in FP64 in row order.
+
+// Exponent range of the nonzero elements of X: r[0] = min, r[1] = max biased exponent
+// (subnormals as 1, Inf/NaN as 255).
+__global__ void x_exponent_range_kernel(const uint32_t *__restrict__ bits, int64_t n, unsigned *__restrict__ r)
 {
+    unsigned lo = 255u, hi = 0u;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t b = bits[i];
+        if ((b & 0x7FFFFFFFu) == 0u) continue;
+        const unsigned e = max((b >> 23) & 0xFFu, 1u);
+        lo = min(lo, e);
+        hi = max(hi, e);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(r, lo);
+        atomicMax(r + 1, hi);
+    }
+}
+
+constexpr int kMeanThreads = 1024;
+
+// Row-order FP64 sum of column j over rows [b, e) of a list by one warp: 32 rows are loaded at a
+// time (one per lane), then every lane adds them in row order, so all lanes hold the same sum.
+__device__ double list_sum_fp64_warp(const float *__restrict__ X, int D, const int64_t *__restrict__ ids, int64_t b,
+                                     int64_t e, int j, int lane)
+{
+    double s = 0.0;
+    float v = (b + lane < e) ? X[ids[b + lane] * D + j] : 0.0f;
+    for (int64_t p0 = b; p0 < e; p0 += 32) {
+        const int64_t pn = p0 + 32 + lane;
+        const float vn = pn < e ? X[ids[pn] * D + j] : 0.0f;  // next batch in flight
+        const int cnt = (int)min((int64_t)32, e - p0);
+        for (int k = 0; k < cnt; ++k) s = __dadd_rn(s, (double)__shfl_sync(0xffffffffu, v, k));
+        v = vn;
+    }
+    return s;
+}
+
+// One block per list, threads = row groups x columns.  Each thread adds its rows (a stride of
+// the list) exactly into a 128-bit integer; the row groups' partials are combined exactly, so
+// the sum is the same whatever the split.
+__global__ void __launch_bounds__(kMeanThreads) list_mean_kernel(const float *__restrict__ X, int D,
+                                                                 const int64_t *__restrict__ offsets,
+                                                                 const int64_t *__restrict__ ids,
+                                                                 const unsigned *__restrict__ xrange,
+                                                                 float *__restrict__ C)
+{
+    __shared__ unsigned long long s_lo[kMeanThreads], s_hi[kMeanThreads];
+    __shared__ unsigned s_neg[kMeanThreads], s_emin[kMeanThreads];
+    __shared__ float s_abs[kMeanThreads];
+    __shared__ int s_flag[256];
+    __shared__ int s_nflag;
     const int l = blockIdx.x;
     const int64_t b = offsets[l], e = offsets[l + 1];
     if (e == b) return;  // empty list keeps its centroid
-    for (int j = threadIdx.x; j < D; j += blockDim.x) {
-        double s = 0.0;
-        int64_t p = b;
-        // loads issued eight rows ahead; the additions stay in ascending row order
-        for (; p + 8 <= e; p += 8) {
-            float v[8];
+    const int64_t n = e - b;
+    const int Dp = (D + 31) & ~31, RG = blockDim.x / Dp;
+    const int j = threadIdx.x % Dp, rg = threadIdx.x / Dp;
+    unsigned g = xrange[0], gmax = xrange[1];
+    if (g > gmax) g = gmax = 1u;  // X is all zeros
+    // |sum| < n 2^(gmax - 126) = 2^(log2 n + gmax - g + 24) units, plus a sign bit
+    const int nbits = 64 - __clzll((unsigned long long)n);
+    const bool fast = gmax < 255u && (int)(gmax - g) + 24 + nbits + 1 <= 127;
+    if (threadIdx.x == 0) s_nflag = 0;
+    if (fast && rg < RG) {
+        unsigned long long lo = 0ull, hi = 0ull;
+        unsigned nneg = 0u, emin = 255u;
+        float sabs = 0.0f;
+        if (j < D) {
+            const uint32_t *xb = reinterpret_cast<const uint32_t *>(X);
+            auto add = [&](uint32_t w) {
+                const unsigned f = (w >> 23) & 0xFFu;
+                const uint32_t m = (w & 0x7FFFFFu) | (f ? 0x800000u : 0u);
+                const unsigned ee = max(f, 1u);
+                emin = min(emin, m ? ee : 255u);
+                sabs += fabsf(__uint_as_float(w));
+                const unsigned sh = m ? ee - g : 0u;  // < 103: the fast test bounds gmax - g
+                unsigned long long vlo, vhi;
+                if (sh < 64u) {
+                    vlo = (unsigned long long)m << sh;
+                    vhi = sh > 40u ? (unsigned long long)m >> (64u - sh) : 0ull;
+                } else {
+                    vlo = 0ull;
+                    vhi = (unsigned long long)m << (sh - 64u);
+                }
+                // a negative term adds its one's complement; the missing +1s are counted
+                const unsigned long long neg = (w >> 31) ? ~0ull : 0ull;
+                nneg += (unsigned)(w >> 31);
+                asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(vlo ^ neg), "l"(vhi ^ neg));
+            };
+            int64_t p = b + rg;
+            for (; p + 3 * RG < e; p += 4 * RG) {
+                uint32_t w[4];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = X[ids[p + q] * D + j];
+                for (int q = 0; q < 4; ++q) w[q] = xb[ids[p + q * RG] * D + j];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) s = __dadd_rn(s, (double)v[q]);
+                for (int q = 0; q < 4; ++q) add(w[q]);
+            }
+            for (; p < e; p += RG) add(xb[ids[p] * D + j]);
         }
-        for (; p < e; ++p) s = __dadd_rn(s, (double)X[ids[p] * D + j]);
-        C[(size_t)l * D + j] = __double2float_rn(__ddiv_rn(s, (double)(e - b)));
+        s_lo[threadIdx.x] = lo;
+        s_hi[threadIdx.x] = hi;
+        s_neg[threadIdx.x] = nneg;
+        s_emin[threadIdx.x] = emin;
+        s_abs[threadIdx.x] = sabs;
+    }
+    __syncthreads();
+    if (rg == 0 && j < D) {
+        bool exact = false;
+        double sum = 0.0;
+        if (fast) {
+            unsigned long long lo = 0ull, hi = 0ull, nneg = 0ull;
+            unsigned emin = 255u;
+            float sabs = 0.0f;
+            for (int r = 0; r < RG; ++r) {
+                const int t = r * Dp + j;
+                asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(s_lo[t]), "l"(s_hi[t]));
+                nneg += s_neg[t];
+                emin = min(emin, s_emin[t]);
+                sabs += s_abs[t];
+            }
+            asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(lo), "+l"(hi) : "l"(nneg));
+            if (emin == 255u) {
+                exact = true;  // every element is zero
+            } else {
+                // sum of magnitudes (FP32, relative error below n 2^-24) against 2^(emin - 97)
+                const double bound = (double)sabs * (1.0 + 1.2e-7 * (double)n);
+                if (bound < ldexp(1.0, (int)emin - 97)) {
+                    const unsigned sh = emin - g;  // the sum is a multiple of 2^sh units
+                    long long J;
+                    if (sh >= 64u) {
+                        J = (long long)hi >> (sh - 64u);
+                    } else if (sh == 0u) {
+                        J = (long long)lo;
+                    } else {
+                        J = (long long)((lo >> sh) | (hi << (64u - sh)));
+                    }
+                    sum = ldexp((double)J, (int)emin - 150);  // |J| < 2^53: exact
+                    exact = true;
+                }
+            }
+        }
+        if (exact) {
+            C[(size_t)l * D + j] = __double2float_rn(__ddiv_rn(sum, (double)n));
+        } else {
+            s_flag[atomicAdd(&s_nflag, 1)] = j;
+        }
+    }
+    __syncthreads();
+    // columns whose row-order FP64 sum is not provably exact: one warp each
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int f = warp; f < s_nflag; f += nwarps) {
+        const int jj = s_flag[f];
+        const double sum = list_sum_fp64_warp(X, D, ids, b, e, jj, lane);
+        if (lane == 0) C[(size_t)l * D + jj] = __double2float_rn(__ddiv_rn(sum, (double)n));
     }
 }
 
@@ -508,11 +658,24 @@ int bucket_rows(const int32_t *list_of_row, int64_t N, int nlist, const uint8_t 
     return PQ_OK;
 }
 
-int launch_list_mean(const float *X, int D, const int64_t *offsets, const int64_t *ids, int nlist, float *C,
-                     cudaStream_t s)
+int launch_x_exponent_range(const float *X, int64_t N, int D, unsigned *xrange, cudaStream_t s)
+{
+    PQ_TRY_CUDA(cudaMemsetAsync(xrange, 0xFF, sizeof(unsigned), s));
+    PQ_TRY_CUDA(cudaMemsetAsync(xrange + 1, 0, sizeof(unsigned), s));
+    ProfScope ps("x_exponent_range", s);
+    x_exponent_range_kernel<<<152 * 4, 256, 0, s>>>(reinterpret_cast<const uint32_t *>(X), N * D, xrange);
+    count_launch();
+    PQ_TRY_CUDA(cudaGetLastError());
+    return PQ_OK;
+}
+
+int launch_list_mean(const float *X, int D, const int64_t *offsets, const int64_t *ids, int nlist,
+                     const unsigned *xrange, float *C, cudaStream_t s)
 {
     ProfScope ps("list_mean", s);
-    list_mean_kernel<<<nlist, std::min(256, ((D + 31) / 32) * 32), 0, s>>>(X, D, offsets, ids, C);
+    if (D > 256) return fail(PQ_ENOTSUP, "list means support D <= 256");
+    const int Dp = (D + 31) / 32 * 32;
+    list_mean_kernel<<<nlist, Dp * (kMeanThreads / Dp), 0, s>>>(X, D, offsets, ids, xrange, C);
     count_launch();
     PQ_TRY_CUDA(cudaGetLastError());
     return PQ_OK;

@@ -94,9 +94,12 @@ int launch_coarse_tc(const float *X, int64_t N, int D, const float *C, int nlist
 // and, if codes != null, list_codes[N][M] in list order.
 int bucket_rows(const int32_t *list_of_row, int64_t N, int nlist, const uint8_t *codes, int M, int64_t *offsets,
                 int64_t *ids, uint8_t *list_codes, Scratch &ws, cudaStream_t s);
-// Coarse centroid update: FP64 sums of each list's rows in ascending row order.
-int launch_list_mean(const float *X, int D, const int64_t *offsets, const int64_t *ids, int nlist, float *C,
-                     cudaStream_t s);
+// Coarse centroid update: FP64 sums of each list's rows in ascending row order (computed as
+// exact integer sums where those are provably equal).  xrange = [min, max] biased exponent of
+// the nonzero elements of X, from launch_x_exponent_range (X is the same for every update).
+int launch_x_exponent_range(const float *X, int64_t N, int D, unsigned *xrange, cudaStream_t s);
+int launch_list_mean(const float *X, int D, const int64_t *offsets, const int64_t *ids, int nlist,
+                     const unsigned *xrange, float *C, cudaStream_t s);
 
 // ---- chunked divide and conquer (chunked.cu) -------------------------------
 int run_pq_fit_chunked(const float *X, const int64_t *off, int n_chunks, int D, int M, int Ks, int iters,

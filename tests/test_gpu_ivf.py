@@ -74,6 +74,32 @@ def test_build_bf16_shapes(pq, D, nlist, kind):
     assert np.array_equal(off, ref["offsets"]) and np.array_equal(ids, ref["ids"])
 
 
+@pytest.mark.parametrize("kind", ["tiny", "wide", "subnormal"])
+def test_list_means_exact_and_sequential_paths(pq, kind):
+    """List means equal the oracle's row-order FP64 sums on every path: exact integer sums
+    (most columns), the row-order FP64 fallback (columns holding values far below their sum's
+    ulp), and the all-sequential form (X spanning more binades than 128 bits hold)."""
+    N, D, nlist = 20_011, 64, 40
+    X = datagen.mixture(N, D, 40, "cont", 5151)
+    rng = np.random.default_rng(5152)
+    pick = rng.random(X.shape) < 0.003
+    if kind == "tiny":
+        X[pick] *= np.float32(1e-9)
+    elif kind == "wide":
+        X[pick] = np.float32(3e-36)
+    else:
+        X[pick] = np.float32(2e-41)  # subnormal
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    codes = np.zeros((N, 8), dtype=np.uint8)
+    ref = orc.ivf_build(X, codes, nlist, 3, 77)
+    for prec in ("fp32", "bf16"):
+        idx = pq.IVFIndex.build(dev(X), dev(codes), nlist, iters=3, seed=77, prec=prec)
+        assert np.array_equal(idx.coarse().cpu().numpy(), ref["coarse"]), prec
+        off, ids, _ = (t.cpu().numpy() for t in idx.lists())
+        assert np.array_equal(off, ref["offsets"]) and np.array_equal(ids, ref["ids"]), prec
+        idx.close()
+
+
 @pytest.mark.parametrize("nprobe,k", [(1, 1), (4, 10), (8, 100), (48, 50)])
 def test_search_matches_oracle(pq, setup, nprobe, k):
     ref_ids, ref_d, _ = orc.ivf_search(setup["ref"], setup["cb"], setup["Q"], nprobe, k)
