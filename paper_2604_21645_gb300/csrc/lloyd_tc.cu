@@ -18,9 +18,9 @@
 // C1 = 7.5e-5, C2 = 2.7e-5 keep a 1.5x margin over the sum of those terms.
 //
 // Decision.  The epilogue reads each row's 256 scores from TMEM in chunks of
-// 32, keeps the eight chunk maxima and the values of the best chunk, and
-// accepts the argmax when no other score lies within twice the error bound of
-// it.  For the other rows (about 0.2% on clustered data) every codeword that
+// 32 (each load also returns the chunk's maximum, tcgen05.ld.red), keeps the
+// eight chunk maxima and the values of the best chunk, and accepts the argmax
+// when no other score lies within twice the error bound of it.  For the other rows (about 0.2% on clustered data) every codeword that
 // may be the nearest -- the saved chunk's scores within the bound, and all
 // codewords of any other chunk whose maximum reaches it -- is re-ranked exactly
 // from the FP32 codebook copy in shared memory: FP32 direct differences, then
@@ -226,30 +226,31 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar)
                  :                                                                                                \
                  : "memory")
 
+// The same load with a max reduction: m receives the largest of the 32 values this thread loads
+// (one row's 32 consecutive columns), so a chunk's maximum needs no instructions of its own.
+#define TC_LDMAX32(base, v, m)                                                                                      \
+    asm volatile("tcgen05.ld.red.sync.aligned.32x32b.x32.max.f32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"  \
+                 "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, %32, [%33];"             \
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]),   \
+                   "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]),         \
+                   "=f"(v[15]), "=f"(v[16]), "=f"(v[17]), "=f"(v[18]), "=f"(v[19]), "=f"(v[20]), "=f"(v[21]),       \
+                   "=f"(v[22]), "=f"(v[23]), "=f"(v[24]), "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]),       \
+                   "=f"(v[29]), "=f"(v[30]), "=f"(v[31]), "=f"(m)                                                   \
+                 : "r"(base))
+#define TC_WAITMAX32(v, m)                                                                                        \
+    asm volatile("tcgen05.wait::ld.sync.aligned;"                                                                 \
+                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]),  \
+                   "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]),         \
+                   "+f"(v[15]), "+f"(v[16]), "+f"(v[17]), "+f"(v[18]), "+f"(v[19]), "+f"(v[20]), "+f"(v[21]),       \
+                   "+f"(v[22]), "+f"(v[23]), "+f"(v[24]), "+f"(v[25]), "+f"(v[26]), "+f"(v[27]), "+f"(v[28]),       \
+                   "+f"(v[29]), "+f"(v[30]), "+f"(v[31]), "+f"(m)                                                   \
+                 :                                                                                                \
+                 : "memory")
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t *>(&v);
-}
-
-// max of three FP32 values in one instruction
-__device__ __forceinline__ float fmax3(float a, float b, float c)
-{
-    float d;
-    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
-    return d;
-}
-
-// maximum of 32 scores: a three-input tree (17 instructions)
-__device__ __forceinline__ float max32(const float *v)
-{
-    float a[11];
-#pragma unroll
-    for (int i = 0; i < 10; ++i) a[i] = fmax3(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
-    a[10] = fmaxf(v[30], v[31]);
-    const float b0 = fmax3(a[0], a[1], a[2]), b1 = fmax3(a[3], a[4], a[5]), b2 = fmax3(a[6], a[7], a[8]);
-    const float b3 = fmaxf(a[9], a[10]);
-    return fmaxf(fmax3(b0, b1, b2), b3);
 }
 
 // 16-byte chunk c (0..3) of row r in a 64B-swizzled TMA stage (row = 64 bytes)
@@ -671,9 +672,9 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
             bool ok = __all_sync(0xffffffffu, mbar_wait(bar(MB_MMAF + g * 2 + 0), i & 1, a.err));
             if (!ok) break;
             tc_after_sync();
-            float vb[2][32];
-            TC_LD32(tl, vb[0]);
-            TC_WAIT32(vb[0]);
+            float vb[2][32], mb2[2];
+            TC_LDMAX32(tl, vb[0], mb2[0]);
+            TC_WAITMAX32(vb[0], mb2[0]);
 #pragma unroll
             for (int j = 0; j < KSMAX / 32; ++j) {
                 if (j + 1 == NH / 32) {
@@ -681,9 +682,9 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
                     if (!ok) break;
                     tc_after_sync();
                 }
-                if (j + 1 < KSMAX / 32) TC_LD32(tl + (uint32_t)((j + 1) * 32), vb[(j + 1) & 1]);
+                if (j + 1 < KSMAX / 32) TC_LDMAX32(tl + (uint32_t)((j + 1) * 32), vb[(j + 1) & 1], mb2[(j + 1) & 1]);
                 const float *v = vb[j & 1];
-                const float cm = max32(v);
+                const float cm = mb2[j & 1];
                 cmx[j] = cm;
                 const bool better = cm > best;
                 cm2 = better ? best : fmaxf(cm2, cm);
@@ -700,7 +701,7 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
                     __syncwarp();
                     if (lane == 0) mbar_arrive(bar(MB_TFREE + g * 2 + 0));
                 }
-                if (j + 1 < KSMAX / 32) TC_WAIT32(vb[(j + 1) & 1]);
+                if (j + 1 < KSMAX / 32) TC_WAITMAX32(vb[(j + 1) & 1], mb2[(j + 1) & 1]);
             }
             if (!ok) break;
             tc_before_sync();
