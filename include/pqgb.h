@@ -104,6 +104,28 @@ int pq_init_kmeanspp(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks
                      void *stream);
 
 /*
+ * pq_fit_encode_host -- pq_fit followed by pq_encode of the same rows, for rows
+ * that live in host memory (Sec. 2.1; the same results as the two device calls).
+ *   X_host          [N][D] float32 in page-locked host memory (cudaHostAlloc or
+ *                   cudaHostRegister), 16-byte aligned.  The seeding reads its
+ *                   subsample rows from it directly while the whole matrix is
+ *                   copied to device scratch on a second stream; the Lloyd
+ *                   passes wait only for that copy.
+ *   codebooks_host  [M][Ks][Ds] float32 host output.
+ *   codes_host      [N][M] uint8 host output, or NULL (codes not returned).
+ *   iters, seed, prec as pq_fit (no init_codebooks, no stats).
+ *   stream          every step is ordered on it: the outputs are complete when
+ *                   the stream passes the call's work.  Page-locked outputs are
+ *                   written asynchronously; the host buffers must stay valid
+ *                   until then.
+ * Returns PQ_EINVAL if X_host is not page-locked host memory of this device's
+ * context, PQ_ENOMEM if the device scratch (N*D*4 + N*M bytes) cannot be
+ * allocated.
+ */
+int pq_fit_encode_host(const float *X_host, int64_t N, int32_t D, int32_t M, int32_t Ks, int32_t iters,
+                       uint64_t seed, int32_t prec, float *codebooks_host, uint8_t *codes_host, void *stream);
+
+/*
  * pq_encode -- PQ codes (Sec. 2.1).
  *   codes   [N][M] uint8 output.
  *   sse     NULL, or a device double that receives the total squared

@@ -52,6 +52,19 @@ int *device_error_word(int device)
     return g_err_word[device];
 }
 
+// One non-blocking copy stream per device (created on first use, never destroyed), for copies
+// that run beside the caller's stream and are joined to it with events.
+static cudaStream_t g_copy_stream[64];
+static std::mutex g_copy_mu;
+static cudaStream_t copy_stream(int device)
+{
+    if (device < 0 || device >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_copy_mu);
+    if (!g_copy_stream[device] && cudaStreamCreateWithFlags(&g_copy_stream[device], cudaStreamNonBlocking) != cudaSuccess)
+        g_copy_stream[device] = nullptr;
+    return g_copy_stream[device];
+}
+
 struct ProfRec {
     const char *name;
     cudaEvent_t a, b;
@@ -267,6 +280,85 @@ int pq_fit(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, int32_t 
             return fail(herr, "device-side failure %d during pq_fit", herr);
         }
     }
+    return ws.status;
+}
+
+int pq_fit_encode_host(const float *X_host, int64_t N, int32_t D, int32_t M, int32_t Ks, int32_t iters,
+                       uint64_t seed, int32_t prec, float *codebooks_host, uint8_t *codes_host, void *stream)
+{
+    g_msg[0] = 0;
+    PQ_TRY(check_pq_shape(N, D, M, Ks, true));
+    PQ_TRY(check_prec(prec));
+    if (!X_host || !codebooks_host) return fail(PQ_EINVAL, "null pointer");
+    if (!aligned16(X_host)) return fail(PQ_EINVAL, "X_host must be 16-byte aligned");
+    if (iters < 0 || iters > PQ_STATS_MAX_ITERS) return fail(PQ_EINVAL, "iters=%d must be in [0, %d]", iters,
+                                                             PQ_STATS_MAX_ITERS);
+    if (prec == PQ_PREC_BF16 && !tc_pass_supported(D, M, Ks))
+        return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and M even");
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, X_host) != cudaSuccess || at.type != cudaMemoryTypeHost || !at.devicePointer) {
+        cudaGetLastError();
+        return fail(PQ_EINVAL, "X_host must be page-locked host memory");
+    }
+    const float *X_map = static_cast<const float *>(at.devicePointer);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    PQ_TRY_CUDA(cudaGetDevice(&dev));
+    int *err = device_error_word(dev);
+    if (!err) return fail(PQ_ENOMEM, "device error word");
+    cudaStream_t cs = copy_stream(dev);
+    if (!cs) return fail(PQ_ECUDA, "copy stream");
+    const int Ds = D / M;
+    const size_t cb_bytes = (size_t)M * Ks * Ds * sizeof(float);
+    Scratch ws(s);
+    float *Xd = ws.get<float>((size_t)N * D);
+    float *cb = ws.get<float>((size_t)M * Ks * Ds);
+    uint8_t *codes = codes_host ? ws.get<uint8_t>((size_t)N * M) : nullptr;
+    unsigned long long *counters = ws.get<unsigned long long>(2, true);
+    if (ws.status) return ws.status;
+    // the copy of X runs beside the seeding, which reads its subsample rows from host memory
+    cudaEvent_t ready = nullptr, copied = nullptr;
+    PQ_TRY_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    if (cudaEventCreateWithFlags(&copied, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventDestroy(ready);
+        return fail(PQ_ECUDA, "event");
+    }
+    struct Events {
+        cudaEvent_t a, b;
+        ~Events()
+        {
+            cudaEventDestroy(a);  // released once pending work completes
+            cudaEventDestroy(b);
+        }
+    } ev{ready, copied};
+    PQ_TRY_CUDA(cudaEventRecord(ready, s));
+    PQ_TRY_CUDA(cudaStreamWaitEvent(cs, ready, 0));
+    PQ_TRY_CUDA(cudaMemcpyAsync(Xd, X_host, (size_t)N * D * sizeof(float), cudaMemcpyHostToDevice, cs));
+    PQ_TRY_CUDA(cudaEventRecord(copied, cs));
+    // every return from here on (errors included) leaves the caller's stream behind the copy,
+    // so the scratch is never released while the copy writes it
+    struct JoinCopy {
+        cudaStream_t s;
+        cudaEvent_t e;
+        ~JoinCopy() { cudaStreamWaitEvent(s, e, 0); }
+    } join{s, copied};
+    PQ_TRY(seed_codebooks(X_map, N, D, M, Ks, seed, cb, ws, err, s));
+    PQ_TRY_CUDA(cudaStreamWaitEvent(s, copied, 0));
+    PQ_TRY(lloyd(Xd, N, D, M, Ks, iters, prec, cb, nullptr, counters, ws, s));
+    if (codes) {
+        PqPass p;
+        p.X = Xd;
+        p.N = N;
+        p.D = D;
+        p.M = M;
+        p.Ks = Ks;
+        p.ds = Ds;
+        p.C = cb;
+        p.codes = codes;
+        PQ_TRY(run_pass(p, prec, s));
+        PQ_TRY_CUDA(cudaMemcpyAsync(codes_host, codes, (size_t)N * M, cudaMemcpyDeviceToHost, s));
+    }
+    PQ_TRY_CUDA(cudaMemcpyAsync(codebooks_host, cb, cb_bytes, cudaMemcpyDeviceToHost, s));
     return ws.status;
 }
 

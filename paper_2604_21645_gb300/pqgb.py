@@ -23,7 +23,7 @@ STATS_MAX_ITERS = 64
 EXPORTS = ("pq_fit", "pq_init_kmeanspp", "pq_encode", "pq_decode_rmse", "ivf_build", "ivf_search", "ivf_get_info",
            "ivf_copy_coarse", "ivf_copy_lists", "ivf_free", "pq_sync_status", "pq_last_error", "pq_launch_count",
            "pq_profile_enable", "pq_profile_collect", "pq_profile_names", "pq_lloyd_noalloc", "pq_fit_chunked",
-           "softpq_forward", "softpq_backward", "pq_tune_chunked", "pq_tune_clear")
+           "softpq_forward", "softpq_backward", "pq_tune_chunked", "pq_tune_clear", "pq_fit_encode_host")
 
 
 class PqStats(C.Structure):
@@ -70,6 +70,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "pq_tune_chunked": (i32, [p, C.POINTER(i64), i32, i32, i32, i32, i32, C.POINTER(i32), C.POINTER(C.c_float), p]),
         "pq_tune_clear": (i32, []),
         "softpq_backward": (i32, [p, i64, i32, i32, i32, p, C.c_float, p, p, p, p]),
+        "pq_fit_encode_host": (i32, [p, i64, i32, i32, i32, i32, u64, i32, p, p, p]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -158,6 +159,44 @@ def fit(X: torch.Tensor, M: int, Ks: int = 256, iters: int = 20, seed: int = 0, 
         _check(_lib.pq_fit(px, N, D, M, Ks, iters, seed & (2**64 - 1), PREC[prec], pi, po,
                            C.byref(st) if st is not None else None, _stream(X)))
     return (out, st.as_dict()) if stats else out
+
+
+def _need_pinned(t, dtype, ndim, name):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.is_cuda or not t.is_pinned():
+        raise ValueError(f"{name} must be a CPU tensor in pinned memory")
+    if t.dtype != dtype or t.dim() != ndim or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {ndim}-dim {dtype} tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def fit_encode_host(X: torch.Tensor, M: int, Ks: int = 256, iters: int = 20, seed: int = 0, prec: str = "fp32",
+                    codebooks: torch.Tensor | None = None, codes: torch.Tensor | None = None, want_codes: bool = True,
+                    device=None, sync: bool = True):
+    """fit + encode of pinned host rows in one call (``pq_fit_encode_host``).
+
+    The seeding reads its subsample from host memory while X is copied to the device on a
+    second stream.  Returns pinned CPU tensors (codebooks [M][Ks][D/M], codes [N][M] or None);
+    with ``sync=False`` they are complete once the device's current stream has passed the call.
+    """
+    px = _need_pinned(X, torch.float32, 2, "X")
+    N, D = X.shape
+    if codebooks is None:
+        codebooks = torch.empty((M, Ks, D // M), dtype=torch.float32).pin_memory()
+    pcb = _need_pinned(codebooks, torch.float32, 3, "codebooks")
+    pcd = None
+    if want_codes:
+        if codes is None:
+            codes = torch.empty((N, M), dtype=torch.uint8).pin_memory()
+        pcd = _need_pinned(codes, torch.uint8, 2, "codes")
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    with torch.cuda.device(dev):
+        st = C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+        _check(_lib.pq_fit_encode_host(px, N, D, M, Ks, iters, seed & (2**64 - 1), PREC[prec], pcb, pcd, st))
+        if sync:
+            torch.cuda.current_stream(dev).synchronize()
+    return codebooks, (codes if want_codes else None)
 
 
 def lloyd_noalloc(X: torch.Tensor, init: torch.Tensor, iters: int, out: torch.Tensor | None = None) -> torch.Tensor:
