@@ -224,6 +224,33 @@ __global__ void coarse_recheck_kernel(const float *__restrict__ X, int D, const 
 // One warp per queued row whose candidates are confined to the 32-centroid chunks of
 // its mask (as found by the tensor-core kernel): FP32 direct differences over those
 // chunks, then FP64 among the FP32 near-ties.  A zero mask means every chunk.
+// FP32 squared distance by direct differences: four partial sums over 16-byte loads when rows
+// are 16-byte aligned (D % 4 == 0), one sum otherwise.  Either way its error is below gamma_D
+// times the exact value, the bound the re-check's margin is built on.
+__device__ __forceinline__ float d2_f32(const float *__restrict__ x, const float *__restrict__ c, int D)
+{
+    if ((D & 3) == 0) {
+        const float4 *x4 = reinterpret_cast<const float4 *>(x), *c4 = reinterpret_cast<const float4 *>(c);
+        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+#pragma unroll 4
+        for (int j = 0; j < D / 4; ++j) {
+            const float4 u = x4[j], v = c4[j];
+            const float t0 = u.x - v.x, t1 = u.y - v.y, t2 = u.z - v.z, t3 = u.w - v.w;
+            a0 = fmaf(t0, t0, a0);
+            a1 = fmaf(t1, t1, a1);
+            a2 = fmaf(t2, t2, a2);
+            a3 = fmaf(t3, t3, a3);
+        }
+        return (a0 + a1) + (a2 + a3);
+    }
+    float d = 0.0f;
+    for (int j = 0; j < D; ++j) {
+        const float t = x[j] - c[j];
+        d = fmaf(t, t, d);
+    }
+    return d;
+}
+
 __global__ void coarse_recheck_masked_kernel(const float *__restrict__ X, int D, const float *__restrict__ C,
                                              int nlist, const int64_t *__restrict__ queue,
                                              const uint32_t *__restrict__ qmask,
@@ -245,12 +272,7 @@ __global__ void coarse_recheck_masked_kernel(const float *__restrict__ X, int D,
             if (m != 0u && c < 32 && !((m >> c) & 1u)) continue;
             const int l = c * 32 + lane;
             if (l >= nlist) continue;
-            const float *cl = C + (size_t)l * D;
-            float d = 0.0f;
-            for (int j = 0; j < D; ++j) {
-                const float t = x[j] - cl[j];
-                d = fmaf(t, t, d);
-            }
+            const float d = d2_f32(x, C + (size_t)l * D, D);
             if (d < d1) { d2 = d1; d1 = d; i1 = l; }
             else if (d < d2) { d2 = d; }
         }
@@ -275,11 +297,7 @@ __global__ void coarse_recheck_masked_kernel(const float *__restrict__ X, int D,
                 const int l = c * 32 + lane;
                 if (l >= nlist) continue;
                 const float *cl = C + (size_t)l * D;
-                float d = 0.0f;
-                for (int j = 0; j < D; ++j) {
-                    const float t = x[j] - cl[j];
-                    d = fmaf(t, t, d);
-                }
+                const float d = d2_f32(x, cl, D);
                 if (d <= d1 + margin) {
                     const double e = d2_fp64(x, cl, D);
                     if (e < best || (e == best && l < bl)) { best = e; bl = l; }
@@ -314,18 +332,26 @@ __global__ void bucket_hist_kernel(const int32_t *__restrict__ lst, int64_t N, i
     for (int l = threadIdx.x; l < nlist; l += blockDim.x) tile_cnt[(size_t)blockIdx.x * nlist + l] = s_hist[l];
 }
 
-// Per list: running count over tiles (in place) and the list total.
+// Per list: running count over tiles (in place) and the list total.  One warp per list takes
+// 32 consecutive tiles at a time and scans them with shuffles.
 __global__ void bucket_column_kernel(int *__restrict__ tile_cnt, int n_tiles, int nlist, int64_t *__restrict__ total)
 {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= nlist) return;
+    const int l = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (l >= nlist) return;  // whole warps only
     int64_t run = 0;
-    for (int t = 0; t < n_tiles; ++t) {
-        const int c = tile_cnt[(size_t)t * nlist + l];
-        tile_cnt[(size_t)t * nlist + l] = (int)run;
-        run += c;
+    for (int t0 = 0; t0 < n_tiles; t0 += 32) {
+        const int t = t0 + lane;
+        const int c = t < n_tiles ? tile_cnt[(size_t)t * nlist + l] : 0;
+        int inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (t < n_tiles) tile_cnt[(size_t)t * nlist + l] = (int)(run + inc - c);
+        run += __shfl_sync(0xffffffffu, inc, 31);
     }
-    total[l] = run;
+    if (lane == 0) total[l] = run;
 }
 
 // Exclusive scan of the list totals into offsets[0..nlist], one block.
@@ -649,7 +675,7 @@ int bucket_rows(const int32_t *list_of_row, int64_t N, int nlist, const uint8_t 
     PQ_TRY_CUDA(cudaFuncSetAttribute(bucket_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
     ProfScope ps("bucket", s);
     bucket_hist_kernel<<<(unsigned)n_tiles, 256, hsm, s>>>(list_of_row, N, nlist, tile_cnt);
-    bucket_column_kernel<<<(nlist + 255) / 256, 256, 0, s>>>(tile_cnt, (int)n_tiles, nlist, total);
+    bucket_column_kernel<<<(nlist + 7) / 8, 256, 0, s>>>(tile_cnt, (int)n_tiles, nlist, total);
     bucket_offsets_kernel<<<1, 1024, 0, s>>>(total, nlist, offsets);
     bucket_scatter_kernel<<<(unsigned)n_tiles, 32, hsm, s>>>(list_of_row, N, nlist, tile_cnt, offsets, codes, M, ids,
                                                               list_codes);
