@@ -107,10 +107,10 @@ int pq_init_kmeanspp(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks
  * pq_fit_encode_host -- pq_fit followed by pq_encode of the same rows, for rows
  * that live in host memory (Sec. 2.1; the same results as the two device calls).
  *   X_host          [N][D] float32 in page-locked host memory (cudaHostAlloc or
- *                   cudaHostRegister), 16-byte aligned.  The seeding reads its
- *                   subsample rows from it directly while the whole matrix is
- *                   copied to device scratch on a second stream; the Lloyd
- *                   passes wait only for that copy.
+ *                   cudaHostRegister), 16-byte aligned.  When N > 100*Ks the
+ *                   seeding's subsample rows are gathered from it directly and
+ *                   seeded while the whole matrix is copied to device scratch on
+ *                   a second stream; the Lloyd passes wait only for that copy.
  *   codebooks_host  [M][Ks][Ds] float32 host output.
  *   codes_host      [N][M] uint8 host output, or NULL (codes not returned).
  *   iters, seed, prec as pq_fit (no init_codebooks, no stats).

@@ -316,7 +316,13 @@ int pq_fit_encode_host(const float *X_host, int64_t N, int32_t D, int32_t M, int
     uint8_t *codes = codes_host ? ws.get<uint8_t>((size_t)N * M) : nullptr;
     unsigned long long *counters = ws.get<unsigned long long>(2, true);
     if (ws.status) return ws.status;
-    // the copy of X runs beside the seeding, which reads its subsample rows from host memory
+    // When N > 100*Ks the seeding needs only its subsample rows: they are gathered from host
+    // memory first (the copy would share the host link with the gather), then seeded while X
+    // is copied on the second stream.
+    const int64_t cap = 100LL * Ks;
+    float *G = N > cap ? ws.get<float>((size_t)cap * D) : nullptr;
+    if (ws.status) return ws.status;
+    if (G) PQ_TRY(launch_gather_subsample(X_map, N, D, Ks, seed, G, s));
     cudaEvent_t ready = nullptr, copied = nullptr;
     PQ_TRY_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
     if (cudaEventCreateWithFlags(&copied, cudaEventDisableTiming) != cudaSuccess) {
@@ -342,8 +348,14 @@ int pq_fit_encode_host(const float *X_host, int64_t N, int32_t D, int32_t M, int
         cudaEvent_t e;
         ~JoinCopy() { cudaStreamWaitEvent(s, e, 0); }
     } join{s, copied};
-    PQ_TRY(seed_codebooks(X_map, N, D, M, Ks, seed, cb, ws, err, s));
-    PQ_TRY_CUDA(cudaStreamWaitEvent(s, copied, 0));
+    if (G) {
+        // seeding the gathered rows gives the codebooks that seeding all of X gives
+        PQ_TRY(seed_codebooks(G, cap, D, M, Ks, seed, cb, ws, err, s));
+        PQ_TRY_CUDA(cudaStreamWaitEvent(s, copied, 0));
+    } else {
+        PQ_TRY_CUDA(cudaStreamWaitEvent(s, copied, 0));
+        PQ_TRY(seed_codebooks(Xd, N, D, M, Ks, seed, cb, ws, err, s));
+    }
     PQ_TRY(lloyd(Xd, N, D, M, Ks, iters, prec, cb, nullptr, counters, ws, s));
     if (codes) {
         PqPass p;

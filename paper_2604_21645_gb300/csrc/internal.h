@@ -35,6 +35,9 @@ struct SeedChunk {
 // Ks codewords in each of the M subspaces (width ds) of every chunk; C is [n_chunks][M][Ks][ds].
 int launch_kmeanspp_chunks(const float *X, int64_t ld, const SeedChunk *chunks, int n_chunks, int ds, int M, int Ks,
                            float *C, Scratch &ws, int *err, cudaStream_t s, const char *tag);
+// The 100*Ks rows that the seeding of N > 100*Ks rows draws (its with-replacement subsample), in
+// draw order, gathered into G [100*Ks][D]: seeding G as a whole gives the same codebooks.
+int launch_gather_subsample(const float *X, int64_t N, int D, int Ks, uint64_t seed, float *G, cudaStream_t s);
 // One chunk: all N rows of X (row stride D).
 int launch_kmeanspp(const float *X, int64_t N, int D, int M, int Ks, uint64_t seed, float *C, Scratch &ws, int *err,
                     cudaStream_t s, const char *tag = "kmeanspp");

@@ -537,7 +537,37 @@ __global__ void subsample_rows_kernel(const KppArgs a, int64_t n_s, int64_t *sub
         sub_rows[ck.sub_off + l] = scale_index(rng_draw(ck.seed, kStreamSubsample, (uint64_t)l) >> 11, (uint64_t)ck.rows);
 }
 
+// Row l of G = row floor(u_l * N) of X, u_l the draw l of the subsample stream: the rows the
+// seeding of one chunk reads (the same draws as subsample_rows_kernel), one warp per row.
+__global__ void gather_subsample_kernel(const float *__restrict__ X, int64_t N, int D, uint64_t seed, int64_t n_s,
+                                        float *__restrict__ G)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; l < n_s; l += nw) {
+        const int64_t row = scale_index(rng_draw(seed, kStreamSubsample, (uint64_t)l) >> 11, (uint64_t)N);
+        const float *src = X + row * D;
+        float *dst = G + l * D;
+        if ((D & 3) == 0) {
+            for (int j = lane; j < D / 4; j += 32)
+                reinterpret_cast<float4 *>(dst)[j] = reinterpret_cast<const float4 *>(src)[j];
+        } else {
+            for (int j = lane; j < D; j += 32) dst[j] = src[j];
+        }
+    }
+}
+
 }  // namespace
+
+int launch_gather_subsample(const float *X, int64_t N, int D, int Ks, uint64_t seed, float *G, cudaStream_t s)
+{
+    const int64_t n_s = 100LL * Ks;
+    ProfScope ps("gather_subsample", s);
+    gather_subsample_kernel<<<152 * 4, 256, 0, s>>>(X, N, D, seed, n_s, G);
+    count_launch();
+    PQ_TRY_CUDA(cudaGetLastError());
+    return PQ_OK;
+}
 
 int launch_kmeanspp_chunks(const float *X, int64_t ld, const SeedChunk *chunks, int n_chunks, int ds, int M, int Ks,
                            float *C, Scratch &ws, int *err, cudaStream_t s, const char *tag)
