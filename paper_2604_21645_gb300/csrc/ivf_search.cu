@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kThreads) probe_select_kernel(const float *__r
 {
     extern __shared__ Cand s_c[];  // [nlist_p2]
     __shared__ float s_xx[kThreads / 32];
-    __shared__ int s_nsure, s_band_lo, s_band_hi;
+    __shared__ int s_band_lo, s_band_hi;
     const int64_t q = blockIdx.x;
     const float *Sq = S + q * nlist;
     const float *qv = Q + q * D;
@@ -89,7 +89,6 @@ __global__ void __launch_bounds__(kThreads) probe_select_kernel(const float *__r
         while (lo < nlist && s_c[lo].d < vp - 2.0f * delta) ++lo;
         int hi = nprobe;
         while (hi < nlist && s_c[hi].d <= vp + 2.0f * delta) ++hi;
-        s_nsure = lo;
         s_band_lo = lo;
         s_band_hi = hi;
     }

@@ -259,21 +259,7 @@ __device__ __forceinline__ const float4 *xs_chunk(const float *stage, int r, int
     return reinterpret_cast<const float4 *>(stage + r * 16 + ((c ^ ((r >> 1) & 3)) << 2));
 }
 
-// Running top-2 of FP32 direct distances over candidate codewords (ties to the lowest index).
-struct Top2 {
-    float d1 = FLT_MAX, d2 = FLT_MAX;
-    int k1 = INT_MAX;
-    __device__ __forceinline__ void add(float d, int k)
-    {
-        if (d < d1 || (d == d1 && k < k1)) {
-            d2 = d1;
-            d1 = d;
-            k1 = k;
-        } else if (d < d2) {
-            d2 = d;
-        }
-    }
-};
+// FP32 squared distance of one subspace row to a codeword, direct differences in dimension order.
 __device__ __forceinline__ float d2_fp32(const float *x, const float *c)
 {
     float d = 0.0f;
