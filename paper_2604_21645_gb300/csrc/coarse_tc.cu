@@ -162,13 +162,23 @@ __device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(_
 // ---- preparation: centring mean, bounds, tiled B operand -------------------
 // Bp layout: [blk][tile][256 rows][16 bf16] core-matrix tiles; tile 2k = ch of K step k,
 // 2k+1 = cl of K step k, 2*KD = the half-norm tile.
-__global__ void coarse_mu_kernel(const float *C, int nlist, int D, float *mu)
+// mu = mean of the centroids (the centring of the scores; any fixed value keeps the decisions
+// exact).  Block of 1024 threads: 8 groups of lists per dimension, added in a fixed order.
+constexpr int kMuGroups = 8;
+__global__ void __launch_bounds__(1024) coarse_mu_kernel(const float *C, int nlist, int D, float *mu)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= D) return;
+    __shared__ float part[kMuGroups][DMAX];
+    const int j = threadIdx.x % DMAX, g = threadIdx.x / DMAX;
     float s = 0.0f;
-    for (int l = 0; l < nlist; ++l) s += C[(size_t)l * D + j];
-    mu[j] = s / (float)nlist;
+    if (j < D)
+        for (int l = g; l < nlist; l += kMuGroups) s += C[(size_t)l * D + j];
+    part[g][j] = s;
+    __syncthreads();
+    if (g == 0 && j < D) {
+        float t = 0.0f;
+        for (int q = 0; q < kMuGroups; ++q) t += part[q][j];
+        mu[j] = t / (float)nlist;
+    }
 }
 
 __global__ void coarse_prep_kernel(const float *C, int nlist, int nlist_pad, int D, const float *mu,
@@ -514,7 +524,7 @@ int launch_coarse_tc(const float *X, int64_t N, int D, const float *C, int nlist
     if (!err) return fail(PQ_ENOMEM, "device error word");
     {
         ProfScope ps("coarse_prep", s);
-        coarse_mu_kernel<<<(D + 127) / 128, 128, 0, s>>>(C, nlist, D, mu);
+        coarse_mu_kernel<<<1, kMuGroups * DMAX, 0, s>>>(C, nlist, D, mu);
         coarse_prep_kernel<<<(nlist_pad + 127) / 128, 128, 0, s>>>(C, nlist, nlist_pad, D, mu, Bp, maxbits);
         count_launch(2);
         PQ_TRY_CUDA(cudaGetLastError());
