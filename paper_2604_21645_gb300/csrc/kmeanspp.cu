@@ -100,54 +100,6 @@ __device__ __forceinline__ float d2_f32_exact(const float *x, const float *c, in
     return acc;
 }
 
-// The same distance for two points at once: two independent chains, twice the loads in
-// flight; each chain keeps the dimension order.  Needs ds % 4 == 0 and 16-byte aligned rows.
-__device__ __forceinline__ void d2_f32_exact2(const float *x0, const float *x1, const float *c, int ds, float &d0,
-                                              float &d1)
-{
-    float a0 = 0.0f, a1 = 0.0f;
-    int j = 0;
-    for (; j + 32 <= ds; j += 32) {
-        float4 v0[8], v1[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            v0[q] = __ldg(reinterpret_cast<const float4 *>(x0 + j) + q);
-            v1[q] = __ldg(reinterpret_cast<const float4 *>(x1 + j) + q);
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const float4 cc = *reinterpret_cast<const float4 *>(c + j + 4 * q);
-            const float f[4] = {cc.x, cc.y, cc.z, cc.w};
-            const float e0[4] = {v0[q].x, v0[q].y, v0[q].z, v0[q].w};
-            const float e1[4] = {v1[q].x, v1[q].y, v1[q].z, v1[q].w};
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const float t0 = __fsub_rn(e0[r], f[r]);
-                const float t1 = __fsub_rn(e1[r], f[r]);
-                a0 = __fadd_rn(a0, __fmul_rn(t0, t0));
-                a1 = __fadd_rn(a1, __fmul_rn(t1, t1));
-            }
-        }
-    }
-    for (; j < ds; j += 4) {
-        const float4 u0 = __ldg(reinterpret_cast<const float4 *>(x0 + j));
-        const float4 u1 = __ldg(reinterpret_cast<const float4 *>(x1 + j));
-        const float4 cc = *reinterpret_cast<const float4 *>(c + j);
-        const float f[4] = {cc.x, cc.y, cc.z, cc.w};
-        const float e0[4] = {u0.x, u0.y, u0.z, u0.w};
-        const float e1[4] = {u1.x, u1.y, u1.z, u1.w};
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const float t0 = __fsub_rn(e0[r], f[r]);
-            const float t1 = __fsub_rn(e1[r], f[r]);
-            a0 = __fadd_rn(a0, __fmul_rn(t0, t0));
-            a1 = __fadd_rn(a1, __fmul_rn(t1, t1));
-        }
-    }
-    d0 = a0;
-    d1 = a1;
-}
-
 // w = floor(d2 * 2^sh) for d2 >= 0, exactly, in integer arithmetic:
 // d2 = m * 2^(e - 150) for a normal float, m * 2^-149 for a subnormal one.
 __device__ __forceinline__ uint64_t weight(float d2, int sh, bool any)
@@ -209,7 +161,70 @@ __device__ __forceinline__ float d2_f32_smem(const float4 *pts4, int ncache, int
     return acc;
 }
 
+// The same distances for points whose float4 piece q is f(q) (for the gathered copy, pieces of one
+// point are ustride float4s apart, so a warp's loads of one piece are contiguous).  Pieces are
+// fetched eight at a time before the sums, which keep the dimension order.
+template <typename F>
+__device__ __forceinline__ float d2_f32_pieces(F f, const float *c, int ds)
+{
+    float acc = 0.0f;
+    int q0 = 0;
+    auto add4 = [&](const float4 v, int q) {
+        const float4 cc = *reinterpret_cast<const float4 *>(c + 4 * q);
+        const float e[4] = {v.x, v.y, v.z, v.w};
+        const float g[4] = {cc.x, cc.y, cc.z, cc.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float t = __fsub_rn(e[r], g[r]);
+            acc = __fadd_rn(acc, __fmul_rn(t, t));
+        }
+    };
+    for (; q0 + 8 <= ds / 4; q0 += 8) {
+        float4 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = f(q0 + q);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) add4(v[q], q0 + q);
+    }
+    for (; q0 < ds / 4; ++q0) add4(f(q0), q0);
+    return acc;
+}
+
+template <typename F0, typename F1>
+__device__ __forceinline__ void d2_f32_pieces2(F0 f0, F1 f1, const float *c, int ds, float &d0, float &d1)
+{
+    float a0 = 0.0f, a1 = 0.0f;
+    auto add4 = [&](const float4 v0, const float4 v1, int q) {
+        const float4 cc = *reinterpret_cast<const float4 *>(c + 4 * q);
+        const float g[4] = {cc.x, cc.y, cc.z, cc.w};
+        const float e0[4] = {v0.x, v0.y, v0.z, v0.w};
+        const float e1[4] = {v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float t0 = __fsub_rn(e0[r], g[r]);
+            const float t1 = __fsub_rn(e1[r], g[r]);
+            a0 = __fadd_rn(a0, __fmul_rn(t0, t0));
+            a1 = __fadd_rn(a1, __fmul_rn(t1, t1));
+        }
+    };
+    int q0 = 0;
+    for (; q0 + 8 <= ds / 4; q0 += 8) {
+        float4 v0[8], v1[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            v0[q] = f0(q0 + q);
+            v1[q] = f1(q0 + q);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) add4(v0[q], v1[q], q0 + q);
+    }
+    for (; q0 < ds / 4; ++q0) add4(f0(q0), f1(q0), q0);
+    d0 = a0;
+    d1 = a1;
+}
+
 constexpr int kWalkRegs = 8;  // D2 values per thread kept in registers by the walk
+
 
 __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
 {
@@ -243,7 +258,13 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
     float *s_d2 = reinterpret_cast<float *>(s_dyn);
     // points past the shared-memory cache, gathered into a contiguous copy at round 0
     float *gp0 = (a.gpts && vec_ok) ? a.gpts + ((size_t)grp * a.bps + b) * a.ustride * ds : nullptr;
-    auto upoint = [&](int i) -> const float * { return gp0 ? gp0 + (size_t)(i - ncache) * ds : point(i0 + i); };
+    // piece q (a float4) of point i past the cache: in the gathered copy, piece-major ([ds/4][ustride]),
+    // so that consecutive threads read consecutive addresses
+    float4 *gp4 = reinterpret_cast<float4 *>(gp0);
+    auto upiece = [&](int i, int q) -> float4 {
+        return gp0 ? __ldg(gp4 + (size_t)q * a.ustride + (i - ncache))
+                   : __ldg(reinterpret_cast<const float4 *>(point(i0 + i)) + q);
+    };
     const float4 *pts4 = s_dyn + a.nb_pad / 4;
     float4 *pts4w = s_dyn + a.nb_pad / 4;
     unsigned *bar = a.bars + 2 * grp;
@@ -284,11 +305,11 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
             d = acc;
         } else if (gp0) {
             const float *x = point(i0 + i);
-            float *dst = gp0 + (size_t)(i - ncache) * ds;
+            float4 *dst = gp4 + (i - ncache);
             float acc = 0.0f;
             for (int q = 0; q < ds / 4; ++q) {
                 const float4 v = __ldg(reinterpret_cast<const float4 *>(x) + q);
-                reinterpret_cast<float4 *>(dst)[q] = v;
+                dst[(size_t)q * a.ustride] = v;
                 const float4 cc = *reinterpret_cast<const float4 *>(s_center + 4 * q);
                 const float e[4] = {v.x, v.y, v.z, v.w};
                 const float f[4] = {cc.x, cc.y, cc.z, cc.w};
@@ -351,9 +372,8 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
                     float4 u[8][2];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
-                        const float4 *x4 = reinterpret_cast<const float4 *>(upoint(i + q * kThreads));
-                        u[q][0] = __ldg(x4);
-                        u[q][1] = __ldg(x4 + 1);
+                        u[q][0] = upiece(i + q * kThreads, 0);
+                        u[q][1] = upiece(i + q * kThreads, 1);
                     }
                     const float4 c0 = *reinterpret_cast<const float4 *>(s_center);
                     const float4 c1 = *reinterpret_cast<const float4 *>(s_center + 4);
@@ -379,7 +399,9 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
             if (vec_ok) {
                 for (; i + kThreads < cnt; i += 2 * kThreads) {
                     float d0, d1;
-                    d2_f32_exact2(upoint(i), upoint(i + kThreads), s_center, ds, d0, d1);
+                    const int ia = i, ib = i + kThreads;
+                    d2_f32_pieces2([&](int q) { return upiece(ia, q); }, [&](int q) { return upiece(ib, q); }, s_center, ds,
+                                   d0, d1);
                     d0 = fminf(d0, s_d2[i]);
                     d1 = fminf(d1, s_d2[i + kThreads]);
                     s_d2[i] = d0;
@@ -392,7 +414,10 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
                 }
             }
             for (; i < cnt; i += kThreads) {
-                const float d = fminf(d2_f32_exact(upoint(i), s_center, ds), s_d2[i]);
+                const int ia = i;
+                const float d = fminf(vec_ok ? d2_f32_pieces([&](int q) { return upiece(ia, q); }, s_center, ds)
+                                             : d2_f32_exact(point(i0 + i), s_center, ds),
+                                      s_d2[i]);
                 s_d2[i] = d;
                 if (!solo) D2c[i0 + i] = d;
                 part += weight(d, sh, any);
