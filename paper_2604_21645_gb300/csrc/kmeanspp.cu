@@ -33,6 +33,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kPer = 5;              // block sums per lane in the owner search
 constexpr int kMaxBps = 32 * kPer;   // blocks per group
 constexpr int64_t kDynSmemCap = 200 * 1024;  // dynamic shared memory of a block
+constexpr int kTagStride = 32;       // one 128-byte line per block's tag and sum: every block polls every tag
 
 struct KppArgs {
     const float *X;               // rows, stride ld floats
@@ -43,8 +44,8 @@ struct KppArgs {
     int64_t nmax;                 // largest point count of a group
     float *C;                     // [n_chunks][M][Ks][ds]
     unsigned *bars;               // [groups][2]
-    unsigned long long *bsum;     // [2][groups][bps] block weight sums
-    unsigned *tags;               // [2][groups][bps] round of the published sum
+    unsigned *tags;               // [2][groups][bps] 128-byte lines: word 0 the round of the published
+                                  // block weight sum, words 2-3 that sum
     float *d2;                    // [2][groups][nmax]
     unsigned *dmax_bits;          // [groups]
     int *err;
@@ -272,8 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
     const int groups = a.n_chunks * a.M;
     const size_t plane = (size_t)groups * a.nmax;  // one D2 buffer
     float *d2m = a.d2 + (size_t)grp * a.nmax;      // + buffer * plane
-    unsigned long long *bs = a.bsum + (size_t)grp * a.bps;
-    unsigned *tags = a.tags + (size_t)grp * a.bps;
+    unsigned *tags = a.tags + (size_t)grp * a.bps * kTagStride;
     const size_t bplane = (size_t)groups * a.bps;
 
     // ---- round 0: first seed; D2 of every point; the cached points are copied --------
@@ -429,23 +429,24 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
         if (tid == 0) {
             uint64_t tot = 0;
             for (int w = 0; w < kWarps; ++w) tot += s_warp[w];
-            bs[(size_t)cur * bplane + b] = tot;
+            unsigned *line = tags + ((size_t)cur * bplane + b) * kTagStride;
+            *reinterpret_cast<unsigned long long *>(line + 2) = tot;
             // publishes the sum and (ordered before it by the __syncthreads above) the block's D2 copy
-            st_release_u32(tags + (size_t)cur * bplane + b, (unsigned)t);
+            st_release_u32(line, (unsigned)t);
         }
 
         // every block: wait for all round-t sums of its group, then find the owner block and
         // threshold.  Lane l polls and holds the sums of blocks [l*kPer, (l+1)*kPer).
         const uint64_t r = rng_draw(seed, (uint64_t)m, (uint64_t)t) >> 11;
         if (tid < 32) {
-            const unsigned *tg = tags + (size_t)cur * bplane;
+            const unsigned *tg = tags + (size_t)cur * bplane * kTagStride;
             bool ok = true;
             for (unsigned it = 0;; ++it) {
                 bool mine = true;
 #pragma unroll
                 for (int q = 0; q < kPer; ++q) {
                     const int bi = tid * kPer + q;
-                    if (bi < a.bps) mine &= ld_acquire_u32(tg + bi) == (unsigned)t;
+                    if (bi < a.bps) mine &= ld_acquire_u32(tg + (size_t)bi * kTagStride) == (unsigned)t;
                 }
                 if (__all_sync(0xffffffffu, mine)) break;
                 // warp-uniform decision to give up (bounded wait)
@@ -457,13 +458,14 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
                 }
             }
             if (tid == 0) s_fail = !ok;
-            const volatile unsigned long long *bv = bs + (size_t)cur * bplane;
+            // each block's sum sits in its tag's line, read after the acquire that saw the tag
             uint64_t v[kPer];
             uint64_t tot = 0;
 #pragma unroll
             for (int q = 0; q < kPer; ++q) {
                 const int bi = tid * kPer + q;
-                v[q] = bi < a.bps ? bv[bi] : 0ull;
+                v[q] = bi < a.bps ? *reinterpret_cast<const volatile unsigned long long *>(tg + (size_t)bi * kTagStride + 2)
+                                  : 0ull;
                 tot += v[q];
             }
             const uint64_t incl = warp_incl_scan(tot);
@@ -654,8 +656,7 @@ int launch_kmeanspp_chunks(const float *X, int64_t ld, const SeedChunk *chunks, 
     a.sub_rows = n_sub ? ws.get<int64_t>((size_t)n_sub * cap) : nullptr;
     a.C = C;
     a.bars = ws.get<unsigned>(2 * (size_t)groups, true);
-    a.bsum = ws.get<unsigned long long>(2 * (size_t)groups * bps, true);
-    a.tags = ws.get<unsigned>(2 * (size_t)groups * bps, true);
+    a.tags = ws.get<unsigned>(2 * (size_t)groups * bps * kTagStride, true);
     if (a.ustride > 0) a.gpts = ws.get<float>((size_t)groups * bps * a.ustride * ds);
     a.d2 = ws.get<float>(2 * (size_t)groups * a.nmax);
     a.dmax_bits = ws.get<unsigned>((size_t)groups, true);
