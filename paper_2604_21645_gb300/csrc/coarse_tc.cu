@@ -450,8 +450,17 @@ __global__ void __launch_bounds__(kThreads, 1) coarse_tc_kernel(const __grid_con
                 ib = (sv[q2] == best) ? q2 : ib;
                 nin += (sv[q2] >= theta) ? 1 : 0;
             }
-            if (row < a.N) {
-                if (nin == 1 && cm2 < theta) {
+            // the warp's uncertain rows take consecutive queue slots from one atomic
+            const bool valid = row < a.N, cert = nin == 1 && cm2 < theta;
+            const unsigned need = __ballot_sync(0xffffffffu, valid && !cert);
+            unsigned long long base = 0;
+            if (need) {
+                const int leader = __ffs(need) - 1;
+                if (lane == leader) base = atomicAdd(a.qlen, (unsigned long long)__popc(need));
+                base = __shfl_sync(0xffffffffu, base, leader);
+            }
+            if (valid) {
+                if (cert) {
                     const int l = bestj * 32 + ib;
                     // a padded centroid scores -3e38 and can never be certified; should one be,
                     // the scores were corrupt: report it instead of passing on an invalid list
@@ -468,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1) coarse_tc_kernel(const __grid_con
                         for (int c = 0; c < NB * 8; ++c) mask |= (cmx[c * TM + r] >= theta ? 1u : 0u) << c;
                     }
                     a.list_of_row[row] = -1;
-                    const unsigned long long slot = atomicAdd(a.qlen, 1ull);
+                    const unsigned long long slot = base + (unsigned)__popc(need & ((1u << lane) - 1u));
                     a.queue[slot] = row;
                     a.qmask[slot] = mask;  // 0: every centroid is a candidate
                 }
