@@ -95,3 +95,14 @@ def test_argument_errors_before_any_launch(lib):
 def test_launch_counter_starts_at_zero(lib):
     lib.pq_launch_count.restype = C.c_int64
     assert lib.pq_launch_count() >= 0
+
+
+def test_host_input_call_checks_its_tensors_before_any_launch():
+    import torch
+
+    from paper_2604_21645_gb300 import pqgb
+    X = torch.zeros((512, 32), dtype=torch.float32)  # pageable CPU memory
+    with pytest.raises(ValueError):
+        pqgb.fit_encode_host(X, 4, 16)
+    with pytest.raises(TypeError):
+        pqgb.fit_encode_host(X.numpy(), 4, 16)
