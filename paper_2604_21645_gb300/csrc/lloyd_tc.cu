@@ -794,27 +794,29 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
     }
 }
 
+// One thread per (chunk, subspace, codeword, dimension): the FP64 sum of the CTAs' partials in
+// block order, then the codeword moves by the mean residual of its members.
 __global__ void pq_finalize_residual_kernel(const double *__restrict__ part, const int *__restrict__ part_cnt, int gx,
                                             int M, int Ks, int ds, float *C, unsigned long long *empties, int n_chunks,
                                             const int *__restrict__ chunk_blk)
 {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n_chunks * M * Ks) return;
-    const int c = idx / (M * Ks), m = (idx / Ks) % M, k = idx % Ks;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n_chunks * M * Ks * ds) return;
+    const int j = (int)(idx % ds);
+    const int64_t cw = idx / ds;
+    const int c = (int)(cw / ((int64_t)M * Ks)), m = (int)((cw / Ks) % M), k = (int)(cw % Ks);
     const int b0 = chunk_blk ? chunk_blk[c] : 0, b1 = chunk_blk ? chunk_blk[c + 1] : gx;
     C += (size_t)c * M * Ks * ds;
     long long n = 0;
     for (int b = b0; b < b1; ++b) n += part_cnt[((size_t)b * M + m) * Ks + k];
     if (n == 0) {
-        if (empties) atomicAdd(empties, 1ull);
+        if (empties && j == 0) atomicAdd(empties, 1ull);
         return;
     }
-    for (int j = 0; j < ds; ++j) {
-        double s = 0.0;
-        for (int b = b0; b < b1; ++b) s = __dadd_rn(s, part[(((size_t)b * M + m) * Ks + k) * ds + j]);
-        float *c = C + ((size_t)m * Ks + k) * ds + j;
-        *c = __double2float_rn(__dadd_rn((double)*c, __ddiv_rn(s, (double)n)));
-    }
+    double sum = 0.0;
+    for (int b = b0; b < b1; ++b) sum = __dadd_rn(sum, part[(((size_t)b * M + m) * Ks + k) * ds + j]);
+    float *cp = C + ((size_t)m * Ks + k) * ds + j;
+    *cp = __double2float_rn(__dadd_rn((double)*cp, __ddiv_rn(sum, (double)n)));
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode()
@@ -896,10 +898,10 @@ int launch_pq_pass_tc(PqPass &p, cudaStream_t s)
 int launch_pq_finalize_residual(const double *part, const int *part_cnt, int gx, int M, int Ks, int ds, float *C,
                                 unsigned long long *empties, cudaStream_t s, int n_chunks, const int *chunk_blk)
 {
-    const int n = n_chunks * M * Ks;
+    const int64_t n = (int64_t)n_chunks * M * Ks * ds;
     ProfScope ps("pq_finalize", s);
-    pq_finalize_residual_kernel<<<(n + 127) / 128, 128, 0, s>>>(part, part_cnt, gx, M, Ks, ds, C, empties, n_chunks,
-                                                                chunk_blk);
+    pq_finalize_residual_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, part_cnt, gx, M, Ks, ds, C, empties,
+                                                                           n_chunks, chunk_blk);
     count_launch();
     PQ_TRY_CUDA(cudaGetLastError());
     return PQ_OK;
