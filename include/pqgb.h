@@ -119,7 +119,7 @@ int pq_init_kmeanspp(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks
  *                   written asynchronously; the host buffers must stay valid
  *                   until then.
  * Returns PQ_EINVAL if X_host is not page-locked host memory of this device's
- * context, PQ_ENOMEM if the device scratch (N*D*4 + N*M bytes) cannot be
+ * context, PQ_ENOMEM if the device scratch (about N*D*4 + N*M bytes) cannot be
  * allocated.
  */
 int pq_fit_encode_host(const float *X_host, int64_t N, int32_t D, int32_t M, int32_t Ks, int32_t iters,
