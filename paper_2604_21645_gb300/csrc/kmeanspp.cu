@@ -260,10 +260,11 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
     // points past the shared-memory cache, gathered into a contiguous copy at round 0
     float *gp0 = (a.gpts && vec_ok) ? a.gpts + ((size_t)grp * a.bps + b) * a.ustride * ds : nullptr;
     // piece q (a float4) of point i past the cache: in the gathered copy, piece-major ([ds/4][ustride]),
-    // so that consecutive threads read consecutive addresses
+    // so that consecutive threads read consecutive addresses.  The copy is written by this kernel
+    // (round 0), so it is read through L2 (ld.global.cg), not the read-only cache path.
     float4 *gp4 = reinterpret_cast<float4 *>(gp0);
     auto upiece = [&](int i, int q) -> float4 {
-        return gp0 ? __ldg(gp4 + (size_t)q * a.ustride + (i - ncache))
+        return gp0 ? __ldcg(gp4 + (size_t)q * a.ustride + (i - ncache))
                    : __ldg(reinterpret_cast<const float4 *>(point(i0 + i)) + q);
     };
     const float4 *pts4 = s_dyn + a.nb_pad / 4;
