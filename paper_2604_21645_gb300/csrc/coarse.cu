@@ -21,7 +21,7 @@ namespace pqgb {
 namespace {
 
 constexpr int BM = 64, BN = 64, BK = 32;
-constexpr int kTileRows = 2048;  // rows per bucketing tile
+constexpr int kTileRows = 512;   // rows per bucketing tile
 
 __global__ void coarse_norms_kernel(const float *C, int nlist, int D, float *half_norm, float *maxes)
 {
