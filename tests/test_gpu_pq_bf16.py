@@ -113,3 +113,34 @@ def test_bf16_unsupported_shape(pq):
     with pytest.raises(pq.PqError) as e:
         pq.encode(X, cb, prec="bf16")
     assert e.value.status == pq.PQ_ENOTSUP
+
+
+@pytest.mark.slow
+def test_full_size_bf16_benchmarked_config(pq):
+    """1M x 128, M=16, Ks=256, BF16 -- the configuration the benchmark times: one lock-step BF16
+    Lloyd iteration over all rows against the oracle, codes bit-exact on 50k sampled rows, and the
+    BF16 coarse index after its 25 iterations: every sampled row sits in the list of its exact
+    (FP64, ties to the lower list) nearest coarse centroid."""
+    w = datagen.IVF_MEDIUM
+    X = w.data()
+    Xd = dev(X)
+    init = orc.kmeanspp(X, w.m, w.ks, w.init_seed)
+    ref, sse_ref = orc.pq_fit(X, w.m, w.ks, 1, 0, init=init)
+    got, st = pq.fit(Xd, w.m, w.ks, iters=1, init=dev(init), prec="bf16", stats=True)
+    assert_codebooks_close(got.cpu().numpy(), ref)
+    assert abs(st["sse"][0] - sse_ref[0]) <= 1e-5 * sse_ref[0]
+    rng = np.random.default_rng(11)
+    rows = rng.choice(w.n, 50_000, replace=False)
+    codes = pq.encode(Xd, dev(ref), prec="bf16")
+    assert np.array_equal(codes.cpu().numpy()[rows], orc.pq_encode(X[rows], ref))
+    idx = pq.IVFIndex.build(Xd, codes, w.nlist, iters=w.ivf_iters, seed=w.coarse_seed, prec="bf16")
+    coarse = idx.coarse().cpu().numpy()
+    off, ids, _ = (t.cpu().numpy() for t in idx.lists())
+    idx.close()
+    assert off[0] == 0 and off[-1] == w.n and np.array_equal(np.sort(ids), np.arange(w.n))
+    list_of = np.empty(w.n, dtype=np.int64)
+    for l in range(w.nlist):
+        list_of[ids[off[l]:off[l + 1]]] = l
+    sample = rng.choice(w.n, 2_000, replace=False)
+    nearest, _ = orc.exact_knn(coarse, X[sample], 1)
+    assert np.array_equal(list_of[sample], nearest[:, 0])
