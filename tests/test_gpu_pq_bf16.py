@@ -144,3 +144,21 @@ def test_full_size_bf16_benchmarked_config(pq):
     sample = rng.choice(w.n, 2_000, replace=False)
     nearest, _ = orc.exact_knn(coarse, X[sample], 1)
     assert np.array_equal(list_of[sample], nearest[:, 0])
+
+
+@pytest.mark.slow
+def test_full_size_precision_form(pq):
+    """10M x 128, M=16, Ks=256, 20 iterations -- the precision form as the benchmark runs it: the BF16
+    and FP32 forms reach the same RMSE (within 1e-4), and the BF16 codes are exact on 50k sampled
+    rows against the oracle's encode under the BF16 codebooks."""
+    w = datagen.PQ_10M
+    X = w.data()
+    Xd = dev(X)
+    cb16 = pq.fit(Xd, w.m, w.ks, iters=w.iters, seed=w.init_seed, prec="bf16")
+    codes16 = pq.encode(Xd, cb16, prec="bf16")
+    _, r16 = pq.decode_rmse(codes16, cb16, Xd)
+    cb32 = pq.fit(Xd, w.m, w.ks, iters=w.iters, seed=w.init_seed, prec="fp32")
+    _, r32 = pq.decode_rmse(pq.encode(Xd, cb32), cb32, Xd)
+    assert abs(r16 - r32) <= RMSE_RTOL * r32
+    rows = np.random.default_rng(13).choice(w.n, 50_000, replace=False)
+    assert np.array_equal(codes16.cpu().numpy()[rows], orc.pq_encode(X[rows], cb16.cpu().numpy()))
