@@ -107,3 +107,21 @@ def test_autotuned_chunked_matches_oracle(pq, case, prec):
     assert_codebooks_close(cb.cpu().numpy(), gC)
     assert abs(rmse - rmse_ref) <= RMSE_RTOL * rmse_ref
     pq.tune_clear()
+
+
+@pytest.mark.slow
+def test_full_size_batched_form(pq):
+    """64 lognormal chunks, 19.2M x 96, M=12, Ks=256, 20 iterations, BF16 -- the batched form as the
+    benchmark runs it: the global codes are exact on 50k sampled rows against the oracle's encode
+    under the global codebooks, and the returned RMSE is the RMSE those codes decode to."""
+    w = datagen.CHUNKED
+    off = datagen.chunk_offsets(w)
+    X = w.data(int(off[-1]))
+    Xd = dev(X)
+    pq.tune_chunked(Xd, off.tolist(), w.m, w.ks, prec="bf16")  # the tuned distribution the benchmark uses
+    cb, codes, r = pq.fit_chunked(Xd, off.tolist(), w.m, w.ks, iters=w.iters, seed=w.init_seed, prec="bf16")
+    pq.tune_clear()
+    _, r_dec = pq.decode_rmse(codes, cb, Xd)
+    assert abs(r - r_dec) <= 1e-9 * r_dec
+    rows = np.random.default_rng(17).choice(int(off[-1]), 50_000, replace=False)
+    assert np.array_equal(codes.cpu().numpy()[rows], orc.pq_encode(X[rows], cb.cpu().numpy()))
