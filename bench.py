@@ -1,21 +1,29 @@
 """Benchmark of the PQ + IVF-ADC hot path on one GB300 (or N replicas).
 
-Default workload (1M x 128 integer-valued mixture, M=16, Ks=256): one step is
-the whole path -- PQ fit (k-means++ seeding + 25 Lloyd iterations), encode
-with the reconstruction error, inverted-index build (coarse k-means
-nlist=1024, 25 iterations, bucketing) and the IVF-ADC query of 10,000 queries
-(nprobe=16, top-100).  `--workload pq_10m_d128_m16` times the precision form
-(10M x 128, 20 iterations; fit + encode per step) and `--compare-fp32` adds
-the plain FP32 form of the same fit + encode beside it.
+Default workload (`pq_10m_d128_m16`): PQ fit + encode of 10M x 128 float32 rows
+(integer-valued 4,096-component mixture), M=16, Ks=256, k-means++ seeding and 20
+Lloyd iterations, in the BF16 tensor-core form with exact re-rank.  One step is
+fit + encode with the reconstruction error.  Beside it the same line carries
+
+fp32_form    the plain FP32 form of the same fit + encode (time, RMSE, ratio);
+ivf_10m      IVF-ADC search of 10k queries (nprobe=16 of 1024 lists, top-100) over
+             an index of the same 10M rows -- 160 MB of codes, larger than L2;
+ivf_1m       the medium workload's search (1M x 128, nlist=1024, nprobe=16,
+             top-100) with its recall against exhaustive FP64 neighbours.
+
+`--workload ivf_1m_d128_m16_nlist1024` times the whole medium pipeline per step
+(fit, encode, index build, search); `chunked_64x_d96_m12` and
+`softpq_1m_d256_m32` time the batched and the soft-refinement forms.
 
 value        fit+encode throughput, Mvec/s = N / (t_fit + t_encode), inputs
              resident in HBM, device time (CUDA events on the launch stream).
 e2e          the same metric through the C ABI from pinned host buffers
-             (pq_fit_encode_host for fit + encode): X copied in beside the seeding,
-             which reads its subsample rows from host memory, codes and codebooks
-             copied out, all inside the timed region.
-roofline     the kernel with the largest share of step time, its algorithmic
-             work per launch over its measured average launch time.
+             (pq_fit_encode_host: X copied in beside the seeding, which reads its
+             subsample rows from host memory; codes and codebooks copied out),
+             all inside the timed region.
+roofline     the kernel with the largest share of the timed step, its
+             algorithmic bytes (or flops) per launch over its measured average
+             launch time.
 cpu_baseline the FP64 oracle on the host cores, fit+encode on a bounded row
              sample of the same workload.
 `--impl reference` times that oracle as the reference arm.
@@ -58,11 +66,6 @@ def load_peaks():
 def fp32_peak_tflops(peaks):
     # 152 SMs x 128 FP32 lanes x 2 flop per FFMA x max SM clock
     return SMS * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-
-
-def compare_peak_t(peaks):
-    # 152 SMs x 128 FP32 lanes x one FMNMX per lane per clock x max SM clock (Tcmp/s)
-    return SMS * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
 
 
 def source_hash(*names):
@@ -131,24 +134,22 @@ class ClockSampler:
 
 
 # algorithmic work per launch of each kernel, for the roofline of the dominant one:
-# (bound, work, unit, peak kind)
-def kernel_work(name, w, n_launch_rows):
+# (bound, work, unit, peak kind).  `launch_rows` is the average number of rows one launch
+# of the PQ pass processes; `encode_share` the fraction of those launches that also write codes.
+def kernel_work(name, w, launch_rows, encode_share=0.0):
     D, M, Ks = w.d, w.m, w.ks
     if name == "pq_pass_f32":
         # the plain form evaluates every (row, subspace, codeword) distance with Ds FFMAs
-        return "alu", 2.0 * n_launch_rows * Ks * D, "TFLOP/s", "fp32"
+        return "alu", 2.0 * launch_rows * Ks * D, "TFLOP/s", "fp32"
     if name == "pq_pass_tc":
-        # the argmin over Ks tensor-core scores needs one FP32 compare per score
-        return "alu", float(n_launch_rows) * M * Ks, "Tcmp/s", "cmp"
+        # HBM: each pass reads X once (D floats per row); the encode pass also writes M code bytes
+        return "hbm", float(launch_rows) * (4.0 * D + encode_share * M), "GB/s", "hbm"
     if name == "coarse_assign_tc":
         return "tensor", 2.0 * w.n * w.nlist * D, "TFLOP/s", "bf16_sustained"
     if name == "coarse_assign":
         return "alu", 2.0 * w.n * w.nlist * D, "TFLOP/s", "fp32"
     if name == "list_mean":
         return "hbm", float(w.n) * (4 * D + 8), "GB/s", "hbm"
-    if name == "adc_scan":
-        # codes of the probed lists (uniform-list expectation)
-        return "hbm", float(w.nq) * w.nprobe * (w.n / w.nlist) * M, "GB/s", "hbm"
     return None, None, None, None
 
 
@@ -180,35 +181,40 @@ def measured_traffic(kernel, workload):
     return None
 
 
-def roofline(kern, w, peaks, peak_src):
+def roofline_record(name, bound, work, unit, kind, avg_s, peaks, peak_src, workload, share=None):
+    """{bound, achieved, peak, unit, frac, traffic} of one kernel from its algorithmic work per launch."""
+    if kind == "hbm":
+        achieved, peak, src = work / avg_s / 1e9, peaks["hbm_gbs"], f"{peak_src} HBM copy bandwidth"
+    elif kind == "bf16_sustained":
+        achieved, peak, src = work / avg_s / 1e12, peaks["bf16_tflops_sustained"], f"{peak_src} sustained bf16"
+    else:
+        achieved, peak = work / avg_s / 1e12, fp32_peak_tflops(peaks)
+        src = "derived: 152 SMs x 128 FP32 lanes x 2 flop per FFMA x max SM clock"
+    rec = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+           "traffic": measured_traffic(name, workload), "peak_source": src, "avg_launch_ms": avg_s * 1e3,
+           "work_per_launch": work}
+    if share is not None:
+        rec["share"] = share
+    return rec
+
+
+def roofline(kern, w, peaks, peak_src, launch_rows=None, encode_share=0.0):
     """Roofline record of the kernel with the largest share of the timed region."""
     if not kern:
         return None
     dominant = max(kern, key=lambda n: kern[n]["ms"])
     k = kern[dominant]
     avg_s = k["ms"] / max(k["launches"], 1) / 1e3
-    bound, work, unit, kind = kernel_work(dominant, w, w.n)
+    bound, work, unit, kind = kernel_work(dominant, w, w.n if launch_rows is None else launch_rows, encode_share)
     share = k["ms"] / max(sum(v["ms"] for v in kern.values()), 1e-9)
     if work is None:
         return {"kernel": dominant, "bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
                 "traffic": None, "avg_launch_ms": avg_s * 1e3, "share": share}
-    if kind == "hbm":
-        achieved, peak, src = work / avg_s / 1e9, peaks["hbm_gbs"], peak_src
-    elif kind == "bf16_sustained":
-        achieved, peak, src = work / avg_s / 1e12, peaks["bf16_tflops_sustained"], peak_src
-    elif kind == "cmp":
-        achieved, peak = work / avg_s / 1e12, compare_peak_t(peaks)
-        src = "152 SMs x 128 FP32 lanes x 1 compare per clock x max SM clock"
-    else:
-        achieved, peak = work / avg_s / 1e12, fp32_peak_tflops(peaks)
-        src = "152 SMs x 128 FP32 lanes x 2 flop per FFMA x max SM clock"
-    traffic = measured_traffic(dominant, w.name)
-    return {"kernel": dominant, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": traffic, "peak_source": src, "avg_launch_ms": avg_s * 1e3,
-            "share": share}
+    return roofline_record(dominant, bound, work, unit, kind, avg_s, peaks, peak_src, w.name, share)
 
 
-def run_gpu(args):
+def run_gpu_pipeline(args):
+    """The medium workload's whole path per step: fit, encode, index build and search."""
     import torch
     import torch.distributed as dist
 
@@ -352,13 +358,236 @@ def run_gpu(args):
                 "d2h_bytes_per_step": int(codes_h.numel() + cbs_h.numel() * 4)},
         "gpu_launches": int(launches),
         "kernels": kern,
-        "roofline": roofline(kern, w, peaks, peak_src),
+        "roofline": roofline(kern, w, peaks, peak_src, encode_share=1.0 / (w.iters + 1)),
         "clocks": clk.summary(),
     }
     if ivf:
         line["queries_per_s"] = world * w.nq / t_search
     if fp32_form:
         line["fp32_form"] = fp32_form
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_rows)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _probe_bytes(torch, Qd, coarse, offsets, nprobe, M):
+    """Code bytes the scan of each query reads: the sizes of its nprobe nearest lists (FP32 distances
+    on the device; a near-tie at the cut can swap two lists, which moves the count negligibly)."""
+    qn = (Qd * Qd).sum(1, keepdim=True)
+    cn = (coarse * coarse).sum(1)[None, :]
+    dist = qn - 2.0 * Qd @ coarse.T + cn
+    probes = torch.topk(dist, nprobe, dim=1, largest=False).indices
+    sizes = (offsets[1:] - offsets[:-1])[probes]
+    return float(sizes.sum().item()) * M
+
+
+def _exact_nn(torch, Xd, Qs):
+    """Exhaustive FP64 nearest neighbour of each query row, on the device (FP64 distances
+    ||x||^2 - 2 x.q + ||q||^2 in batches of 100 queries)."""
+    X64 = Xd.double()
+    xn = (X64 * X64).sum(1)
+    out = []
+    for b in range(0, Qs.shape[0], 100):
+        q = Qs[b:b + 100].double()
+        d = xn[None, :] - 2.0 * (q @ X64.T) + (q * q).sum(1, keepdim=True)
+        out.append(torch.argmin(d, dim=1).cpu().numpy())
+    del X64
+    return np.concatenate(out)
+
+
+def _time_search(torch, pqgb, idx, cbs, Qd, w, steps, warmup, flush):
+    out_ids = torch.empty((Qd.shape[0], w.topk), dtype=torch.int64, device="cuda")
+    out_d = torch.empty((Qd.shape[0], w.topk), dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        idx.search(cbs, Qd, w.nprobe, w.topk, out_ids=out_ids, out_d=out_d)
+    torch.cuda.synchronize()
+    pqgb.profile_enable(True)
+    ms = _timed_steps(torch, lambda: idx.search(cbs, Qd, w.nprobe, w.topk, out_ids=out_ids, out_d=out_d), steps,
+                      flush)
+    kern = pqgb.profile_collect()
+    pqgb.profile_enable(False)
+    return float(np.mean(ms)), kern, out_ids, out_d
+
+
+def run_gpu(args):
+    """The precision form (10M x 128 fit + encode) and, beside it, the IVF-ADC search figures."""
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2604_21645_gb300 import pqgb
+
+    w = datagen.WORKLOADS[args.workload]
+    prec = args.prec
+    X = w.data()
+    Xd = torch.from_numpy(X).cuda()
+    cbs = torch.empty((w.m, w.ks, w.d // w.m), dtype=torch.float32, device="cuda")
+    codes = torch.empty((w.n, w.m), dtype=torch.uint8, device="cuda")
+    sse = torch.zeros(1, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def step(p):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        pqgb.fit(Xd, w.m, w.ks, iters=w.iters, seed=w.init_seed, prec=p, out=cbs)
+        ev[1].record(stream)
+        pqgb.encode(Xd, cbs, prec=p, out=codes, sse=sse)
+        ev[2].record(stream)
+        return ev
+
+    def timed(p, steps):
+        ph = np.zeros(2)
+        for _ in range(steps):
+            flush.zero_()
+            ev = step(p)
+            torch.cuda.synchronize()
+            ph += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])]
+        return ph / steps
+
+    for _ in range(args.warmup):
+        step(prec)
+    torch.cuda.synchronize()
+    launches0 = pqgb.launch_count()
+    pqgb.profile_enable(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        per_step = timed(prec, args.steps)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    launches = pqgb.launch_count() - launches0
+    kern = pqgb.profile_collect()
+    pqgb.profile_enable(False)
+    _, rmse = pqgb.decode_rmse(codes, cbs, Xd)
+    _, est = pqgb.encode(Xd, cbs, prec=prec, stats=True)
+    t_fe = slowest_rank([(per_step[0] + per_step[1]) / 1e3], world)[0]
+    value = replica_throughput(w.n, t_fe, world) / 1e6
+    peaks, peak_src = load_peaks()
+    codes_main = codes.clone()
+    cbs_main = cbs.clone()
+
+    # the plain FP32 form of the same fit + encode
+    fp32_form = None
+    if not args.no_compare_fp32 and prec != "fp32":
+        step("fp32")
+        torch.cuda.synchronize()
+        pqgb.profile_enable(True)
+        ph = timed("fp32", args.steps)
+        kern32 = pqgb.profile_collect()
+        pqgb.profile_enable(False)
+        _, rmse32 = pqgb.decode_rmse(codes, cbs, Xd)
+        t32 = slowest_rank([(ph[0] + ph[1]) / 1e3], world)[0]
+        v32 = replica_throughput(w.n, t32, world) / 1e6
+        fp32_form = {"value": v32, "unit": "Mvec/s", "ms_fit": ph[0], "ms_encode": ph[1], "rmse": rmse32,
+                     "rmse_rel_diff": abs(rmse - rmse32) / rmse32, "bf16_over_fp32": value / v32,
+                     "roofline": roofline(kern32, w, peaks, peak_src)}
+
+    # end-to-end through the C ABI from pinned host buffers
+    Xh = torch.from_numpy(X).pin_memory()
+    codes_h = torch.empty((w.n, w.m), dtype=torch.uint8).pin_memory()
+    cbs_h = torch.empty_like(cbs, device="cpu").pin_memory()
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pqgb.fit_encode_host(Xh, w.m, w.ks, iters=w.iters, seed=w.init_seed, prec=prec, codebooks=cbs_h,
+                             codes=codes_h, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    t_e2e = slowest_rank([float(np.mean(e2e_ms)) / 1e3], world)[0]
+    del Xh
+
+    cfg = {"workload": w.name, "N": w.n, "D": w.d, "M": w.m, "Ks": w.ks, "iters": w.iters, "prec": prec,
+           "parallelism": f"replicas{world}",
+           "l2": f"256 MB buffer written between steps; X ({X.nbytes // 10**6} MB) exceeds L2"}
+    line = {
+        "metric": "PQ fit+encode Mvec/s (IVF-ADC queries/s reported beside it)",
+        "value": value,
+        "unit": "Mvec/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_fe * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if prec == "fp32" else "bf16",
+        "data": "synthetic (seeded Gaussian mixture standing in for the paper's data)",
+        "config": cfg,
+        "phases_ms": {"fit": per_step[0], "encode": per_step[1]},
+        "rmse": rmse,
+        "exact_rerank_fraction": est["fp64_rechecks"] / (w.n * w.m),
+        "e2e": {"value": replica_throughput(w.n, t_e2e, world) / 1e6, "unit": "Mvec/s",
+                # X copied once, plus the seeding's subsample rows read from host memory
+                "h2d_bytes_per_step": int(X.nbytes + min(w.n, 100 * w.ks) * w.d * 4),
+                "d2h_bytes_per_step": int(codes_h.numel() + cbs_h.numel() * 4)},
+        "gpu_launches": int(launches),
+        "kernels": kern,
+        "roofline": roofline(kern, w, peaks, peak_src, encode_share=1.0 / (w.iters + 1)),
+        "clocks": clk.summary(),
+    }
+    if fp32_form:
+        line["fp32_form"] = fp32_form
+
+    if not args.no_search:
+        # IVF-ADC search over the same 10M rows: 160 MB of codes, more than L2 holds
+        wi = datagen.IVF_10M
+        t0 = time.perf_counter()
+        idx = pqgb.IVFIndex.build(Xd, codes_main, wi.nlist, iters=wi.ivf_iters, seed=wi.coarse_seed, prec=prec)
+        torch.cuda.synchronize()
+        t_build = time.perf_counter() - t0
+        Qd = torch.from_numpy(wi.queries()).cuda()
+        ms, kern_s, _, _ = _time_search(torch, pqgb, idx, cbs_main, Qd, wi, args.steps, args.warmup, flush)
+        off, _, _ = idx.lists()
+        scanned = _probe_bytes(torch, Qd, idx.coarse(), off, wi.nprobe, wi.m)
+        ivf10 = {"workload": wi.name, "queries_per_s": world * wi.nq / (ms / 1e3), "ms": ms, "build_s": t_build,
+                 "nlist": wi.nlist, "nprobe": wi.nprobe, "topk": wi.topk, "nq": wi.nq,
+                 "code_bytes_scanned": scanned, "kernels": kern_s}
+        if "adc_scan" in kern_s:
+            avg = kern_s["adc_scan"]["ms"] / max(kern_s["adc_scan"]["launches"], 1) / 1e3
+            ivf10["roofline"] = roofline_record("adc_scan", "hbm", scanned, "GB/s", "hbm", avg, peaks, peak_src,
+                                                wi.name)
+        idx.close()
+        del Qd
+        line["ivf_10m"] = ivf10
+        # the medium workload's index (1M x 128, 1,000 components) and its recall
+        del Xd
+        torch.cuda.empty_cache()
+        wm = datagen.IVF_MEDIUM
+        Xm = torch.from_numpy(wm.data()).cuda()
+        cm = pqgb.fit(Xm, wm.m, wm.ks, iters=wm.iters, seed=wm.init_seed, prec=prec)
+        codes_m = pqgb.encode(Xm, cm, prec=prec)
+        idx = pqgb.IVFIndex.build(Xm, codes_m, wm.nlist, iters=wm.ivf_iters, seed=wm.coarse_seed, prec=prec)
+        Qd = torch.from_numpy(wm.queries()).cuda()
+        ms, kern_s, ids, _ = _time_search(torch, pqgb, idx, cm, Qd, wm, args.steps, args.warmup, flush)
+        sample = np.random.default_rng(0).choice(wm.nq, 1000, replace=False)
+        nn = _exact_nn(torch, Xm, Qd[torch.from_numpy(sample).cuda()])
+        got = ids.cpu().numpy()[sample]
+        recall = {f"recall@{r}": float(np.mean([nn[i] in got[i, :r] for i in range(len(sample))]))
+                  for r in (1, 10, 100)}
+        off, _, _ = idx.lists()
+        scanned = _probe_bytes(torch, Qd, idx.coarse(), off, wm.nprobe, wm.m)
+        ivf1 = {"workload": wm.name, "queries_per_s": world * wm.nq / (ms / 1e3), "ms": ms, "nlist": wm.nlist,
+                "nprobe": wm.nprobe, "topk": wm.topk, "nq": wm.nq, "code_bytes_scanned": scanned,
+                "recall": recall, "recall_sample": "exact FP64 1-NN of 1,000 sampled queries (torch on the device)",
+                "l2_note": "the 16 MB code array is L2-resident"}
+        idx.close()
+        line["ivf_1m"] = ivf1
+        line["queries_per_s"] = ivf10["queries_per_s"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_rows)
     if rank == 0:
@@ -443,15 +672,12 @@ def run_gpu_chunked(args):
     if pname in kern:
         # rows through the pass: every local iteration covers all N rows, the global fit the
         # n_chunks * Ks pooled codewords, the final encode N rows again
+        n_launch = max(kern[pname]["launches"] // args.steps, 1)
         rows = w.iters * N + w.iters * len(offl[:-1]) * w.ks + N
-        bound, work, unit, kind = kernel_work(pname, w, rows)
-        secs = kern[pname]["ms"] / 1e3 / args.steps
-        ach = work / secs / 1e12
-        peak = compare_peak_t(peaks) if kind == "cmp" else fp32_peak_tflops(peaks)
-        roof = {"kernel": pname, "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-                "traffic": measured_traffic(pname, w.name), "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (derived)",
-                "avg_launch_ms": kern[pname]["ms"] / max(kern[pname]["launches"], 1),
-                "share": kern[pname]["ms"] / max(sum(v["ms"] for v in kern.values()), 1e-9)}
+        bound, work, unit, kind = kernel_work(pname, w, rows / n_launch, 1.0 / n_launch)
+        secs = kern[pname]["ms"] / 1e3 / max(kern[pname]["launches"], 1)
+        roof = roofline_record(pname, bound, work, unit, kind, secs, peaks, peak_src, w.name,
+                               kern[pname]["ms"] / max(sum(v["ms"] for v in kern.values()), 1e-9))
     cfg = {"workload": w.name, "N": N, "n_chunks": w.n_chunks, "D": w.d, "M": w.m, "Ks": w.ks, "iters": w.iters,
            "chunk_rows": {"min": int(np.diff(off).min()), "median": int(np.median(np.diff(off))),
                           "max": int(np.diff(off).max())},
@@ -622,7 +848,7 @@ def run_reference(args):
     else:
         rows = args.cpu_rows
         sample = lambda: (rows, oracle_fit_encode(w, rows), f"pq_fit + pq_encode on the first {rows} rows")
-        metric = "PQ fit+encode Mvec/s" + (" (IVF-ADC queries/s reported beside it)" if w.nlist else "")
+        metric = "PQ fit+encode Mvec/s (IVF-ADC queries/s reported beside it)"
         cores = orc.num_threads()
     for _ in range(args.warmup):
         sample()
@@ -647,10 +873,12 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default=datagen.IVF_MEDIUM.name,
-                    choices=[datagen.IVF_MEDIUM.name, datagen.PQ_10M.name, datagen.CHUNKED.name, datagen.SOFTPQ.name])
+    ap.add_argument("--workload", default=datagen.PQ_10M.name,
+                    choices=[datagen.PQ_10M.name, datagen.IVF_MEDIUM.name, datagen.CHUNKED.name, datagen.SOFTPQ.name])
     ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16"])
-    ap.add_argument("--compare-fp32", action="store_true", help="also time the plain FP32 form of fit + encode")
+    ap.add_argument("--compare-fp32", action="store_true", help="medium pipeline: also time the plain FP32 form")
+    ap.add_argument("--no-compare-fp32", action="store_true", help="precision form: skip the plain FP32 form")
+    ap.add_argument("--no-search", action="store_true", help="precision form: skip the IVF-ADC search figures")
     ap.add_argument("--cpu-rows", type=int, default=50_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -662,6 +890,8 @@ def main():
         run_gpu_chunked(args)
     elif args.workload == datagen.SOFTPQ.name:
         run_gpu_softpq(args)
+    elif args.workload == datagen.IVF_MEDIUM.name:
+        run_gpu_pipeline(args)
     else:
         run_gpu(args)
 

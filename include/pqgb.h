@@ -159,10 +159,13 @@ int pq_decode_rmse(const uint8_t *codes, const float *codebooks, const float *X,
  * summation order of the member sums.  Scratch is a fixed 8 MiB array inside
  * the library that every GPU loading it keeps until exit; shapes needing more
  * than that for one block per subspace, M*Ks*(8*D/M + 4) > 8 MiB, are rejected
- * with PQ_EINVAL.  The first call on each device looks up the array's device
- * address (make that first call before any stream capture).  All calls share
- * the array: calls whose work overlaps on the GPU (other streams, other host
- * threads) race and must be serialized by the caller.
+ * with PQ_EINVAL, and subspace widths other than 1, 2, 4, 8, 16, 32 with
+ * PQ_ENOTSUP, before anything is enqueued.  The first call on each device
+ * looks up the array's device address and caches it (make that first call
+ * before any stream capture; the cache assumes the device's primary context is
+ * not reset while the library is loaded).  All calls share the array: calls
+ * whose work overlaps on the GPU (other streams, other host threads) race and
+ * must be serialized by the caller.
  */
 int pq_lloyd_noalloc(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, int32_t iters,
                      const float *init_codebooks, float *codebooks, void *stream);
@@ -269,6 +272,23 @@ int pq_sync_status(void *stream);
 const char *pq_last_error(void);
 /* Kernels launched by this library since load (a monotone counter). */
 int64_t pq_launch_count(void);
+
+/*
+ * Failure injection for tests of the failure handling (no counterpart in the
+ * paper).  Process-wide settings; they exercise error paths without faulting
+ * or hanging the GPU.
+ * pq_test_set_spin_limit -- poll budget of the k-means++ seeding's waits on
+ *   other blocks (its group barrier and its per-round sum polls), normally
+ *   2^22 polls.  A small budget makes a wait run out: the block records
+ *   PQ_ETIMEOUT in the device error word and the kernel's blocks return (the
+ *   seeding has no bulk copies in flight to wait for); pq_sync_status then
+ *   returns PQ_ETIMEOUT and clears the word.  0 restores the default.
+ * pq_test_fail_alloc_after -- the (n+1)-th scratch allocation from now fails
+ *   as if the device were out of memory: the call returns PQ_ENOMEM at that
+ *   point, releasing the scratch it already took.  n < 0 turns this off.
+ */
+int pq_test_set_spin_limit(uint32_t polls);
+int pq_test_fail_alloc_after(int32_t n);
 
 /*
  * Per-kernel timing for measurement (no counterpart in the paper).

@@ -33,6 +33,14 @@ int fail(int status, const char *fmt, ...)
     return status;
 }
 
+void clear_error() { g_msg[0] = 0; }
+
+// Failure-injection hooks for tests (pq_test_*): the seeding's poll budget, and an
+// allocation that fails after a given number of successful ones (-1: never).
+static std::atomic<unsigned> g_seed_spin{kSpinLimit};
+static std::atomic<int> g_fail_alloc_after{-1};
+unsigned seeding_spin_limit() { return g_seed_spin.load(std::memory_order_relaxed); }
+
 int cuda_check(cudaError_t e, const char *what)
 {
     if (e == cudaErrorMemoryAllocation) return fail(PQ_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
@@ -109,6 +117,16 @@ void *Scratch::raw(size_t bytes, bool zero)
     if (status) return nullptr;
     void *p = nullptr;
     const size_t b = (bytes + 255) & ~size_t(255);
+    for (int left = g_fail_alloc_after.load(); left >= 0;) {
+        if (left == 0) {
+            if (g_fail_alloc_after.compare_exchange_weak(left, -1)) {
+                status = fail(PQ_ENOMEM, "cudaMallocAsync: injected allocation failure");
+                return nullptr;
+            }
+        } else if (g_fail_alloc_after.compare_exchange_weak(left, left - 1)) {
+            break;
+        }
+    }
     cudaError_t e = cudaMallocAsync(&p, b ? b : 256, s);
     if (e != cudaSuccess) { status = cuda_check(e, "cudaMallocAsync"); return nullptr; }
     ptrs.push_back(p);
@@ -701,6 +719,18 @@ int pq_sync_status(void *stream)
 const char *pq_last_error(void) { return g_msg; }
 
 int64_t pq_launch_count(void) { return g_launches.load(); }
+
+int pq_test_set_spin_limit(uint32_t polls)
+{
+    g_seed_spin.store(polls == 0 ? kSpinLimit : polls);
+    return PQ_OK;
+}
+
+int pq_test_fail_alloc_after(int32_t n)
+{
+    g_fail_alloc_after.store(n < 0 ? -1 : n);
+    return PQ_OK;
+}
 
 int pq_profile_enable(int on)
 {

@@ -13,6 +13,7 @@ namespace pqgb {
 // ---------------------------------------------------------------------------
 void count_launch(int n = 1);
 int fail(int status, const char *fmt, ...);
+void clear_error();  // empties this thread's last-error message (done on entry by every call)
 int cuda_check(cudaError_t e, const char *what);
 #define PQ_TRY_CUDA(expr)                                        \
     do {                                                         \
@@ -125,6 +126,9 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
 // Spin budget of every device-side wait: ~2^22 polls (each an L2 round trip or
 // an mbarrier try-wait) is a few seconds at most on a healthy GPU.
 constexpr unsigned kSpinLimit = 1u << 22;
+// Budget the k-means++ seeding's inter-block waits use: kSpinLimit unless a test
+// has lowered it (pq_test_set_spin_limit) to make those waits run out on purpose.
+unsigned seeding_spin_limit();
 
 // Barrier over the `nblk` blocks sharing `bar` ({arrive count, generation}).
 // Blocks must be co-resident (cooperative launch).  Returns false, after
@@ -142,7 +146,8 @@ __device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned *p, unsigned v
 // writes (ordered before thread 0 by the first __syncthreads) are visible to every block
 // after the barrier.  The wait is bounded: false (PQ_ETIMEOUT recorded) if it ran out
 // or another block already failed.
-__device__ __forceinline__ bool block_group_barrier(unsigned *bar, unsigned nblk, int *err)
+__device__ __forceinline__ bool block_group_barrier(unsigned *bar, unsigned nblk, int *err,
+                                                    unsigned limit = kSpinLimit)
 {
     __shared__ int s_ok;
     __syncthreads();
@@ -156,7 +161,7 @@ __device__ __forceinline__ bool block_group_barrier(unsigned *bar, unsigned nblk
                 st_release_u32(bar + 1, gen + 1);
             } else {
                 for (unsigned it = 0; ld_acquire_u32(bar + 1) == gen; ++it) {
-                    if (it > kSpinLimit || ((it & 255) == 255 && *(volatile int *)err != 0)) {
+                    if (it >= limit || ((it & 255) == 255 && *(volatile int *)err != 0)) {
                         atomicCAS(err, 0, PQ_ETIMEOUT);
                         ok = 0;
                         break;

@@ -276,9 +276,12 @@ __global__ void __launch_bounds__(kScanThreads) adc_scan_kernel(const float *__r
                     }
                 }
                 if (stream) {
+                    // one block-uniform snapshot of the count: every thread takes the same branch,
+                    // and no thread adds to the buffer before all of them have read it
                     __syncthreads();
-                    if (s_count > kSelCap - kScanThreads) {
-                        const int cnt = s_count;
+                    const int cnt = s_count;
+                    __syncthreads();
+                    if (cnt > kSelCap - kScanThreads) {
                         for (int i = cnt + threadIdx.x; i < kSelCap; i += kScanThreads) {
                             buf[i].d = FLT_MAX;
                             buf[i].id = 0x7fffffff;

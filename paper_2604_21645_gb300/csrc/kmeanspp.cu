@@ -49,6 +49,7 @@ struct KppArgs {
     float *d2;                    // [2][groups][nmax]
     unsigned *dmax_bits;          // [groups]
     int *err;
+    unsigned spin;                // poll budget of the inter-block waits
     int bps;
     int ncache;                   // points per block kept in shared memory
     int nb_pad;                   // floats of the per-block D2 copy (multiple of 4)
@@ -337,7 +338,7 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
         for (int w = 0; w < kWarps; ++w) v = fmaxf(v, s_fmax[w]);
         atomicMax(a.dmax_bits + grp, __float_as_uint(v));  // non-negative floats order as integers
     }
-    if (!block_group_barrier(bar, a.bps, a.err)) return;
+    if (!block_group_barrier(bar, a.bps, a.err, a.spin)) return;
     const float dmax = __uint_as_float(ld_acquire_u32(a.dmax_bits + grp));
     const bool any = dmax > 0.0f;
     int L = 0;
@@ -451,7 +452,7 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
                 }
                 if (__all_sync(0xffffffffu, mine)) break;
                 // warp-uniform decision to give up (bounded wait)
-                const bool give_up = it > kSpinLimit || ((it & 255) == 255 && *(volatile int *)a.err != 0);
+                const bool give_up = it >= a.spin || ((it & 255) == 255 && *(volatile int *)a.err != 0);
                 if (__any_sync(0xffffffffu, give_up)) {
                     if (tid == 0) atomicCAS(a.err, 0, PQ_ETIMEOUT);
                     ok = false;
@@ -663,6 +664,7 @@ int launch_kmeanspp_chunks(const float *X, int64_t ld, const SeedChunk *chunks, 
     a.dmax_bits = ws.get<unsigned>((size_t)groups, true);
     if (ws.status) return ws.status;
     a.err = err;
+    a.spin = seeding_spin_limit();
     if (n_sub) {
         ProfScope ps("subsample_rows", s);
         subsample_rows_kernel<<<dim3((unsigned)((cap + 255) / 256), n_chunks), 256, 0, s>>>(a, cap,

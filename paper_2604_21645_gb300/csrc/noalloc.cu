@@ -15,7 +15,10 @@
 // this code until the process exits).  Host code cannot pass the array's
 // name to a kernel -- on the host that name is only a stand-in, not a device
 // address -- so the first call on each device looks the address up with
-// cudaGetSymbolAddress, with that device current, and caches it.
+// cudaGetSymbolAddress, with that device current, and caches it.  The cache
+// assumes the device's primary context lives as long as the library: after a
+// cudaDeviceReset the cached address is stale, and the library must not be
+// called on that device again in this process.
 #include <mutex>
 
 #include "common.cuh"
@@ -52,6 +55,7 @@ using namespace pqgb;
 extern "C" int pq_lloyd_noalloc(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, int32_t iters,
                                 const float *init_codebooks, float *codebooks, void *stream)
 {
+    clear_error();
     if (!X || !init_codebooks || !codebooks) return fail(PQ_EINVAL, "null pointer");
     if (N < 1 || D <= 0 || M <= 0 || D % M != 0) return fail(PQ_EINVAL, "need N >= 1 and D a multiple of M");
     if (Ks < 1 || Ks > 256 || N < Ks) return fail(PQ_EINVAL, "need 1 <= Ks <= 256 and N >= Ks");
@@ -59,6 +63,9 @@ extern "C" int pq_lloyd_noalloc(const float *X, int64_t N, int32_t D, int32_t M,
                                                              PQ_STATS_MAX_ITERS);
     if (reinterpret_cast<uintptr_t>(X) & 15) return fail(PQ_EINVAL, "X must be 16-byte aligned");
     const int ds = D / M;
+    // the subspace widths the FP32 pass is compiled for; checked before anything is enqueued
+    if (ds != 1 && ds != 2 && ds != 4 && ds != 8 && ds != 16 && ds != 32)
+        return fail(PQ_ENOTSUP, "subspace width Ds=%d not supported (1, 2, 4, 8, 16 or 32)", ds);
     // One block-subspace slot holds Ks*ds FP64 sums and Ks int32 counts.
     const size_t slot = (size_t)Ks * ds * sizeof(double) + (size_t)Ks * sizeof(int);
     const size_t per_gx = slot * (size_t)M;

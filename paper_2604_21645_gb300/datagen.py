@@ -141,13 +141,18 @@ IVF_MEDIUM = Workload("ivf_1m_d128_m16_nlist1024", 1_000_000, 128, 16, 256, 25, 
                       BASE_SEED + 2, nlist=1024, ivf_iters=25, nq=10_000, nprobe=16, topk=100)
 # Precision form, 10M x 128 integer-valued, 4,096 components, M=16, Ks=256, 20 iterations.
 PQ_10M = Workload("pq_10m_d128_m16", 10_000_000, 128, 16, 256, 20, 4096, "int255", BASE_SEED + 3)
+# Search over the precision form's rows: the 10M x 128 rows above (same seed, same mixture) in an
+# inverted index of nlist=1024 lists, 10k queries from the mixture, nprobe=16, top-100.  Its 160 MB
+# of codes exceed the 129 MB L2, so the scan reads them from HBM.
+IVF_10M = Workload("ivf_10m_d128_m16_nlist1024", 10_000_000, 128, 16, 256, 20, 4096, "int255", BASE_SEED + 3,
+                   nlist=1024, ivf_iters=25, nq=10_000, nprobe=16, topk=100)
 # Batched chunked form: 64 lognormal chunks (median 200k), D=96, M=12, Ks=256, 20 iterations.
 CHUNKED = Workload("chunked_64x_d96_m12", 0, 96, 12, 256, 20, 256, "cont", BASE_SEED + 4, n_chunks=64,
                    extra={"median": 200_000, "log_sigma": 1.0, "lo": 10_000, "hi": 2_000_000})
 # Differentiable refinement: 1M x 256, M=32, Ks=256, tau=0.1.
 SOFTPQ = Workload("softpq_1m_d256_m32", 1_000_000, 256, 32, 256, 0, 256, "cont", BASE_SEED + 5, tau=0.1)
 
-WORKLOADS = {w.name: w for w in (PQ_SMALL, IVF_MEDIUM, PQ_10M, CHUNKED, SOFTPQ)}
+WORKLOADS = {w.name: w for w in (PQ_SMALL, IVF_MEDIUM, PQ_10M, IVF_10M, CHUNKED, SOFTPQ)}
 
 
 def chunk_offsets(w: Workload, n_chunks: int | None = None) -> np.ndarray:

@@ -23,7 +23,8 @@ STATS_MAX_ITERS = 64
 EXPORTS = ("pq_fit", "pq_init_kmeanspp", "pq_encode", "pq_decode_rmse", "ivf_build", "ivf_search", "ivf_get_info",
            "ivf_copy_coarse", "ivf_copy_lists", "ivf_free", "pq_sync_status", "pq_last_error", "pq_launch_count",
            "pq_profile_enable", "pq_profile_collect", "pq_profile_names", "pq_lloyd_noalloc", "pq_fit_chunked",
-           "softpq_forward", "softpq_backward", "pq_tune_chunked", "pq_tune_clear", "pq_fit_encode_host")
+           "softpq_forward", "softpq_backward", "pq_tune_chunked", "pq_tune_clear", "pq_fit_encode_host",
+           "pq_test_set_spin_limit", "pq_test_fail_alloc_after")
 
 
 class PqStats(C.Structure):
@@ -71,6 +72,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "pq_tune_clear": (i32, []),
         "softpq_backward": (i32, [p, i64, i32, i32, i32, p, C.c_float, p, p, p, p]),
         "pq_fit_encode_host": (i32, [p, i64, i32, i32, i32, i32, u64, i32, p, p, p]),
+        "pq_test_set_spin_limit": (i32, [C.c_uint32]),
+        "pq_test_fail_alloc_after": (i32, [i32]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)

@@ -174,3 +174,39 @@ def test_full_size_medium_config_recall(pq):
     # farther than the 1st and the PQ error per dimension is about sigma, so even exhaustive FP64 ADC
     # finds the 1-NN in its top-100 for about a third of the queries.  Chance level is 1e-4.
     assert rec[100] >= 0.1
+
+
+@pytest.mark.slow
+def test_full_size_search_matches_oracle(pq):
+    """The benchmarked search (1M x 128, nlist=1024, nprobe=16, top-100) against the oracle's search
+    on 256 sampled queries.  The oracle works lock-step from the GPU's coarse centroids and PQ
+    codebooks: its own FP64 nearest-list decisions (orc.assign) give the lists, which must equal the
+    GPU's bit for bit, and its own encode gives the codes; then its search must agree with the GPU's
+    (ids exact except counted near-ties, distances within 1e-5 relative)."""
+    w = datagen.IVF_MEDIUM
+    X = w.data()
+    Xd = dev(X)
+    cbs = pq.fit(Xd, w.m, w.ks, iters=w.iters, seed=w.init_seed, prec="bf16")
+    cb = cbs.cpu().numpy()
+    codes = pq.encode(Xd, cbs, prec="bf16")
+    ocodes = orc.pq_encode(X, cb)
+    assert np.array_equal(codes.cpu().numpy(), ocodes)
+    idx = pq.IVFIndex.build(Xd, codes, w.nlist, iters=w.ivf_iters, seed=w.coarse_seed, prec="bf16")
+    coarse = idx.coarse().cpu().numpy()
+    off, ids, lcodes = (t.cpu().numpy() for t in idx.lists())
+    lists, _, _ = orc.assign(X, coarse[None])
+    lists = lists[:, 0]
+    ref_off = np.concatenate([[0], np.cumsum(np.bincount(lists, minlength=w.nlist))]).astype(np.int64)
+    ref_ids = np.argsort(lists, kind="stable").astype(np.int64)
+    assert np.array_equal(off, ref_off)
+    assert np.array_equal(ids, ref_ids)
+    ref = {"coarse": coarse, "offsets": ref_off, "ids": ref_ids, "list_codes": np.ascontiguousarray(ocodes[ref_ids])}
+    assert np.array_equal(lcodes, ref["list_codes"])
+    Q = w.queries()
+    sample = np.sort(np.random.default_rng(21).choice(w.nq, 256, replace=False))
+    got_ids, got_d = idx.search(cbs, dev(Q), w.nprobe, w.topk)
+    idx.close()
+    o_ids, o_d, _ = orc.ivf_search(ref, cb, Q[sample], w.nprobe, w.topk)
+    ties = check_topk(got_ids.cpu().numpy()[sample], got_d.cpu().numpy()[sample], o_ids, o_d)
+    print("near-tie id differences", ties, "of", o_ids.size)
+    assert ties <= 0.01 * o_ids.size

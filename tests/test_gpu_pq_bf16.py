@@ -149,8 +149,9 @@ def test_full_size_bf16_benchmarked_config(pq):
 @pytest.mark.slow
 def test_full_size_precision_form(pq):
     """10M x 128, M=16, Ks=256, 20 iterations -- the precision form as the benchmark runs it: the BF16
-    and FP32 forms reach the same RMSE (within 1e-4), and the BF16 codes are exact on 50k sampled
-    rows against the oracle's encode under the BF16 codebooks."""
+    and FP32 forms reach the same RMSE (within 1e-4), each form's RMSE equals the FP64 oracle's over
+    all 10M rows (within 1e-4), and both forms' codes are exact on 50k sampled rows against the
+    oracle's encode under their codebooks."""
     w = datagen.PQ_10M
     X = w.data()
     Xd = dev(X)
@@ -158,7 +159,15 @@ def test_full_size_precision_form(pq):
     codes16 = pq.encode(Xd, cb16, prec="bf16")
     _, r16 = pq.decode_rmse(codes16, cb16, Xd)
     cb32 = pq.fit(Xd, w.m, w.ks, iters=w.iters, seed=w.init_seed, prec="fp32")
-    _, r32 = pq.decode_rmse(pq.encode(Xd, cb32), cb32, Xd)
+    codes32 = pq.encode(Xd, cb32)
+    _, r32 = pq.decode_rmse(codes32, cb32, Xd)
     assert abs(r16 - r32) <= RMSE_RTOL * r32
+    # each form's RMSE against the FP64 oracle's, over all 10M rows, with that form's codes and codebooks
+    o16 = orc.pq_rmse(X, codes16.cpu().numpy(), cb16.cpu().numpy())
+    o32 = orc.pq_rmse(X, codes32.cpu().numpy(), cb32.cpu().numpy())
+    print(f"RMSE relative error against the oracle: bf16 {abs(r16 - o16) / o16:.3e}, fp32 {abs(r32 - o32) / o32:.3e}")
+    assert abs(r16 - o16) <= RMSE_RTOL * o16
+    assert abs(r32 - o32) <= RMSE_RTOL * o32
     rows = np.random.default_rng(13).choice(w.n, 50_000, replace=False)
     assert np.array_equal(codes16.cpu().numpy()[rows], orc.pq_encode(X[rows], cb16.cpu().numpy()))
+    assert np.array_equal(codes32.cpu().numpy()[rows], orc.pq_encode(X[rows], cb32.cpu().numpy()))

@@ -301,6 +301,32 @@ def test_chunked_single_chunk_reduces_to_plain_fit():
     np.testing.assert_allclose(r, orc.pq_rmse(X, codes_local, local[0]), rtol=1e-12)
 
 
+def test_chunked_multi_chunk_decomposes_into_plain_fits():
+    """Sec. 3 divide and conquer, step by step on four uneven chunks: chunk c's codebooks are the
+    plain fit of its own rows seeded with draw c of the chunk stream; the global model is the plain
+    fit, seeded with the caller's seed, of the centroid dataset whose row c*Ks + k concatenates
+    codeword k of every subspace of chunk c; codes and RMSE are the global model's.  Catches a wrong
+    chunk row offset, a wrong per-chunk seed and a wrong pooled-row layout."""
+    X = datagen.mixture(9000, 12, 30, "cont", 22)
+    off = np.array([0, 1700, 2300, 6100, 9000], dtype=np.int64)
+    M, Ks, iters, seed = 3, 32, 4, 0x1234ABCD
+    gC, codes, r, local = orc.pq_fit_chunked(X, off, M, Ks, iters, seed)
+    n_chunks = len(off) - 1
+    for c in range(n_chunks):
+        seed_c = orc.draw(seed, 0xFFFFFFFE, c)
+        want, _ = orc.pq_fit(X[off[c]:off[c + 1]], M, Ks, iters, seed_c)
+        assert np.array_equal(local[c], want), f"chunk {c}"
+    # the centroid dataset, assembled here from the local codebooks: [n_chunks*Ks][D]
+    pooled = np.concatenate([np.concatenate([local[c, m] for m in range(M)], axis=1) for c in range(n_chunks)])
+    assert pooled.shape == (n_chunks * Ks, X.shape[1])
+    want_g, _ = orc.pq_fit(pooled, M, Ks, iters, seed)
+    assert np.array_equal(gC, want_g)
+    assert np.array_equal(codes, orc.pq_encode(X, want_g))
+    assert r == orc.pq_rmse(X, codes, want_g)
+    # chunks fitted on their own rows differ from one another (the offsets matter)
+    assert not np.array_equal(local[0], local[1])
+
+
 def test_chunked_rmse_close_to_single_fit():
     """Sec. 3: the global model fitted on pooled chunk codewords reconstructs about as well as one fit."""
     X = datagen.mixture(12000, 8, 24, "cont", 21)
@@ -333,6 +359,69 @@ def test_softpq_gradients_match_finite_differences():
             arr[i] = old
             num[i] = (lp - lm) / (2 * h)
         np.testing.assert_allclose(grad, num, rtol=1e-6, atol=1e-9)
+
+
+def _fd4(f, x0, h):
+    """Fourth-order central difference of f at x0 (truncation error O(h^4))."""
+    return (f(x0 - 2 * h) - 8 * f(x0 - h) + 8 * f(x0 + h) - f(x0 + 2 * h)) / (12 * h)
+
+
+@pytest.mark.slow
+def test_softpq_gradients_match_finite_differences_at_refinement_size():
+    """The refinement workload's shape (N=1000, D=256, M=32, Ks=256, tau=0.1) in FP64: 200
+    seeded-random entries each of dL/dC and dL/dX against central finite differences, relative
+    error below 1e-6.  L is a sum over subspaces and rows of the same function, so the
+    difference quotient of an entry of subspace m is taken on that subspace's slice (and, for
+    X, on its row: L = (1/N) sum_n L_n); eight entries are also checked on the full loss."""
+    N, D, M, Ks, tau = 1000, 256, 32, 256, 0.1
+    ds = D // M
+    X = datagen.mixture(N, D, 256, "cont", 99).astype(np.float64)
+    rng = np.random.default_rng(1)
+    cb = X[rng.integers(0, N, Ks)].reshape(Ks, M, ds).transpose(1, 0, 2).copy()
+    cb += 0.01 * rng.standard_normal(cb.shape)
+    dC, dX = orc.softpq_backward(X, cb, tau)
+    h = 1e-3
+    worst = 0.0
+
+    def check(num, ana):
+        nonlocal worst
+        err = abs(num - ana)
+        assert err <= 1e-6 * abs(ana) + 1e-13, (num, ana)
+        worst = max(worst, err / max(abs(ana), 1e-300))
+
+    for _ in range(200):
+        m, k, j = int(rng.integers(M)), int(rng.integers(Ks)), int(rng.integers(ds))
+        Xs = np.ascontiguousarray(X[:, m * ds:(m + 1) * ds])
+
+        def f_c(v):
+            c = cb[m].copy()
+            c[k, j] = v
+            return orc.softpq_forward(Xs, c[None], tau)
+        check(_fd4(f_c, cb[m, k, j], h), dC[m, k, j])
+    for _ in range(200):
+        n, d = int(rng.integers(N)), int(rng.integers(D))
+        m = d // ds
+        cm = cb[m][None].copy()
+
+        def f_x(v):
+            x = X[n:n + 1, m * ds:(m + 1) * ds].copy()
+            x[0, d - m * ds] = v
+            return orc.softpq_forward(x, cm, tau) / N
+        check(_fd4(f_x, X[n, d], h), dX[n, d])
+    # a few entries through the whole loss (all rows and subspaces)
+    for e in range(8):
+        arr, grad = (cb, dC) if e % 2 == 0 else (X, dX)
+        i = tuple(int(rng.integers(s)) for s in arr.shape)
+        old = arr[i]
+
+        def f_full(v):
+            arr[i] = v
+            try:
+                return orc.softpq_forward(X, cb, tau)
+            finally:
+                arr[i] = old
+        check(_fd4(f_full, old, h), grad[i])
+    print("largest relative error", worst)
 
 
 def test_softpq_limits():
