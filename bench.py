@@ -879,7 +879,7 @@ def main():
     ap.add_argument("--compare-fp32", action="store_true", help="medium pipeline: also time the plain FP32 form")
     ap.add_argument("--no-compare-fp32", action="store_true", help="precision form: skip the plain FP32 form")
     ap.add_argument("--no-search", action="store_true", help="precision form: skip the IVF-ADC search figures")
-    ap.add_argument("--cpu-rows", type=int, default=50_000)
+    ap.add_argument("--cpu-rows", type=int, default=300_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
