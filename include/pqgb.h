@@ -90,8 +90,15 @@ typedef struct pq_stats {
  *   codebooks       [M][Ks][Ds] output (may alias init_codebooks).
  *   stats           host pq_stats or NULL; non-NULL makes the call synchronize.
  * Each iteration assigns every (row, subspace) to its nearest codeword, then
- * replaces every codeword by the mean of its members (FP32 compensated sums,
- * FP64 final reduction); a codeword without members keeps its value.
+ * replaces every codeword by the mean of its members; a codeword without
+ * members keeps its value.  The member sums are exact integer sums of the
+ * residuals x - c in a fixed-point format scaled to the codebook (each element's
+ * quantisation error below 2^-(62 - 2b) of twice the largest codeword norm about
+ * the codeword mean, b = bit length of the rows one block or CTA handles), plus
+ * FP32 sums of the rare residuals beyond that format; blocks are combined in
+ * int64 and the mean is taken in float-float (compensated FP32) arithmetic, so
+ * no FP64 arithmetic is involved and the result does not depend on the order of
+ * the additions.
  */
 int pq_fit(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, int32_t iters, uint64_t seed,
            int32_t prec, const float *init_codebooks, float *codebooks, pq_stats *stats, void *stream);

@@ -217,17 +217,14 @@ int lloyd(const float *X, int64_t N, int D, int M, int Ks, int iters, int prec, 
     p.C = C;
     const bool tc = prec == PQ_PREC_BF16;
     p.gx = tc ? pq_pass_tc_blocks(p) : pq_pass_blocks_per_subspace(p);
-    p.part = ws.get<double>((size_t)p.gx * M * Ks * p.ds);
-    p.part_cnt = ws.get<int>((size_t)p.gx * M * Ks);
+    void *pb = ws.raw(Partials::bytes(p.gx, M, Ks, p.ds, 1), false);
     if (ws.status) return ws.status;
+    p.part.carve(pb, p.gx, M, Ks, p.ds);
     p.rechecks = counters;
     for (int t = 0; t < iters; ++t) {
         p.sse = sse_dev ? sse_dev + t : nullptr;
         PQ_TRY(run_pass(p, prec, s));
-        if (tc)
-            PQ_TRY(launch_pq_finalize_residual(p.part, p.part_cnt, p.gx, M, Ks, p.ds, C, counters + 1, s));
-        else
-            PQ_TRY(launch_pq_finalize(p.part, p.part_cnt, p.gx, M, Ks, p.ds, C, counters + 1, s));
+        PQ_TRY(launch_pq_finalize(p.part, p.gx, M, Ks, p.ds, C, counters + 1, s));
     }
     return PQ_OK;
 }

@@ -151,9 +151,9 @@ int run_pq_fit_chunked(const float *X, const int64_t *off, int n_chunks, int D, 
     p.ds = ds;
     p.C = Cl;
     p.gx = gx;
-    p.part = ws.get<double>((size_t)gx * M * Ks * ds);
-    p.part_cnt = ws.get<int>((size_t)gx * M * Ks);
+    void *pb = ws.raw(Partials::bytes(gx, M, Ks, ds, n_chunks), false);
     if (ws.status) return ws.status;
+    p.part.carve(pb, gx, M, Ks, ds);
     {
         const int n = std::max(n_chunks + 1, gx);
         ProfScope ps("chunk_tables", s);
@@ -166,13 +166,11 @@ int run_pq_fit_chunked(const float *X, const int64_t *off, int n_chunks, int D, 
     p.chunk_blk = d_blk;
     p.n_chunks = n_chunks;
     for (int t = 0; t < iters; ++t) {
-        if (tc) {
+        if (tc)
             PQ_TRY(launch_pq_pass_tc(p, s));
-            PQ_TRY(launch_pq_finalize_residual(p.part, p.part_cnt, gx, M, Ks, ds, Cl, nullptr, s, n_chunks, d_blk));
-        } else {
+        else
             PQ_TRY(launch_pq_pass_f32(p, s));
-            PQ_TRY(launch_pq_finalize(p.part, p.part_cnt, gx, M, Ks, ds, Cl, nullptr, s, n_chunks, d_blk));
-        }
+        PQ_TRY(launch_pq_finalize(p.part, gx, M, Ks, ds, Cl, nullptr, s, n_chunks, d_blk));
     }
 
     // (3) centroid dataset of the pooled codewords, (4) global fit, (5) global encode + error
@@ -236,8 +234,7 @@ int run_pq_tune_chunked(const float *X, const int64_t *off, int n_chunks, int D,
     int64_t *d_off = ws.get<int64_t>((size_t)n_chunks + 1);
     int *d_blk = ws.get<int>((size_t)n_chunks + 1);
     int *d_bc = ws.get<int>((size_t)gmax);
-    double *part = ws.get<double>((size_t)gmax * M * Ks * ds);
-    int *part_cnt = ws.get<int>((size_t)gmax * M * Ks);
+    void *pb = ws.raw(Partials::bytes(gmax, M, Ks, ds, n_chunks), false);
     if (ws.status) return ws.status;
     cudaEvent_t e0, e1;
     PQ_TRY_CUDA(cudaEventCreate(&e0));
@@ -258,8 +255,7 @@ int run_pq_tune_chunked(const float *X, const int64_t *off, int n_chunks, int D,
         p.ds = ds;
         p.C = Cl;
         p.gx = gx;
-        p.part = part;
-        p.part_cnt = part_cnt;
+        p.part.carve(pb, gx, M, Ks, ds);
         p.blk_chunk = d_bc;
         p.chunk_off = d_off;
         p.chunk_blk = d_blk;

@@ -100,6 +100,85 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
 }
 
+// Fast TwoSum (Dekker): s + e == a + b exactly when |a| >= |b| or a == 0.
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    e = __fadd_rn(b, __fsub_rn(a, s));
+}
+
+// TwoProduct: p + e == a * b exactly (the FMA returns the rounding error of the product).
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// Float-float ("double-float") sum of (ah + al) and (bh + bl), normalised.
+__device__ __forceinline__ void ff_add(float ah, float al, float bh, float bl, float &sh, float &sl)
+{
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e = __fadd_rn(e, __fadd_rn(al, bl));
+    fast_two_sum(s, e, sh, sl);
+}
+
+// Float-float quotient (ah + al) / (bh + bl): one correction step of the FP32 quotient.
+__device__ __forceinline__ void ff_div(float ah, float al, float bh, float bl, float &qh, float &ql)
+{
+    const float q1 = __fdiv_rn(ah, bh);
+    float p, pe;
+    two_prod(q1, bh, p, pe);
+    float r = __fsub_rn(__fsub_rn(ah, p), pe);
+    r = __fadd_rn(r, al);
+    r = __fsub_rn(r, __fmul_rn(q1, bl));
+    fast_two_sum(q1, __fdiv_rn(r, bh), qh, ql);
+}
+
+// Exact float-float value of a 64-bit integer: v == hi + lo with |lo| <= ulp(hi)/2 (the
+// remainder v - hi is below 2^40 in magnitude, so its conversion loses at most 2^-24 of it).
+__device__ __forceinline__ void ll_to_ff(long long v, float &hi, float &lo)
+{
+    hi = __ll2float_rn(v);
+    lo = __ll2float_rn(v - __float2ll_rn(hi));
+}
+
+// ---------------------------------------------------------------------------
+// Centroid update in exact fixed point (both forms of the Lloyd pass).
+//
+// Each member adds its residual r = x - c_code.  An element becomes the integer
+// q = rint(r * 2^F) and is added into a block's shared sums as two int32 parts,
+// q >> L and q & (2^L - 1); with at most 2^b rows per block (b = bit length of
+// the row bound), L = 31 - b keeps the low sum below 2^31 and |q| < 2^(61 - 2b)
+// keeps the high sum below 2^31.  F puts the residual scale r0 at that limit:
+// elements whose magnitude reaches 2^(61 - 2b - F) (beyond r0) go to an FP32 sum
+// instead.  The integer sums do not depend on the order of the additions; each
+// block writes hi * 2^L + lo as one int64 per (subspace, codeword, dimension),
+// and the finalise kernel adds the blocks in int64 (exact), converts the total to
+// a float-float value, adds the FP32 sums with TwoSum and moves the codeword by
+// the float-float mean residual.  An element's quantisation error is at most
+// 2^-(F+1), i.e. 2^-(62 - 2b) of r0 (rows per block of 2^16: 2^-30 of r0).
+// ---------------------------------------------------------------------------
+struct FixFmt {
+    int L, F;
+    float scale, lim;
+};
+__host__ __device__ __forceinline__ FixFmt fix_format(int64_t rows, float r0)
+{
+    int b = 0;
+    while (b < 62 && ((int64_t)1 << b) <= rows) ++b;  // bit length of the row bound
+    FixFmt f;
+    f.L = 31 - b;
+    const int qb = 61 - 2 * b;  // |q| < 2^qb
+    int e = 0;
+    (void)frexpf(r0 > 0.0f ? r0 : 1.0f, &e);  // r0 < 2^e
+    f.F = qb - e;
+    f.F = f.F < -100 ? -100 : (f.F > 100 ? 100 : f.F);
+    f.scale = ldexpf(1.0f, f.F);
+    f.lim = ldexpf(1.0f, qb);
+    return f;
+}
+
 // gamma_n = n u / (1 - n u), u = 2^-24: the classical bound on the relative
 // error of an n-term FP32 sum of products.
 __host__ __device__ __forceinline__ float gamma_f32(int n)

@@ -42,6 +42,34 @@ int launch_gather_subsample(const float *X, int64_t N, int D, int Ks, uint64_t s
 int launch_kmeanspp(const float *X, int64_t N, int D, int M, int Ks, uint64_t seed, float *C, Scratch &ws, int *err,
                     cudaStream_t s, const char *tag = "kmeanspp");
 
+// ---- centroid update partials (both forms of the Lloyd pass) ------------------
+// Per-block member sums of one Lloyd pass, in the exact fixed-point format of
+// common.cuh (FixFmt): residual sums as int64 per (block, subspace, codeword,
+// dimension), the FP32 sums of the rare residual elements beyond that format, member
+// counts, and the format's exponent F per (chunk, subspace).
+struct Partials {
+    long long *q = nullptr;  // [gx][M][Ks][ds]
+    float *o = nullptr;      // [gx][M][Ks][ds]
+    int *cnt = nullptr;      // [gx][M][Ks]
+    int *F = nullptr;        // [n_chunks][M]
+    static size_t bytes(int gx, int M, int Ks, int ds, int n_chunks)
+    {
+        const size_t e = (size_t)gx * M * Ks * ds;
+        return e * 8 + e * 4 + (size_t)gx * M * Ks * 4 + (size_t)n_chunks * M * 4 + 64;
+    }
+    // lays the four arrays out in `base` (256-byte aligned, Partials::bytes(...) long)
+    void carve(void *base, int gx, int M, int Ks, int ds)
+    {
+        const size_t e = (size_t)gx * M * Ks * ds;
+        unsigned char *b = static_cast<unsigned char *>(base);
+        q = reinterpret_cast<long long *>(b);
+        o = reinterpret_cast<float *>(b + e * 8);
+        cnt = reinterpret_cast<int *>(b + e * 12);
+        F = reinterpret_cast<int *>(b + e * 12 + (size_t)gx * M * Ks * 4);
+    }
+    __host__ __device__ bool active() const { return q != nullptr; }
+};
+
 // ---- PQ Lloyd pass, FP32 SIMT form (lloyd_simt.cu) ------------------------
 struct PqPass {
     const float *X = nullptr;
@@ -49,8 +77,7 @@ struct PqPass {
     int D = 0, M = 0, Ks = 0, ds = 0;
     const float *C = nullptr;      // [M][Ks][ds]
     uint8_t *codes = nullptr;      // [N][M] or null
-    double *part = nullptr;        // [gx][M][Ks][ds] per-block member sums, or null (no update)
-    int *part_cnt = nullptr;       // [gx][M][Ks]
+    Partials part;                 // per-block member sums, or inactive (no update)
     double *sse = nullptr;         // device scalar accumulator or null
     unsigned long long *rechecks = nullptr;
     int gx = 0;                    // blocks per subspace (set by the launcher)
@@ -64,9 +91,10 @@ struct PqPass {
 };
 int pq_pass_blocks_per_subspace(const PqPass &p);
 int launch_pq_pass_f32(PqPass &p, cudaStream_t s);
-int launch_pq_finalize(const double *part, const int *part_cnt, int gx, int M, int Ks, int ds, float *C,
-                       unsigned long long *empties, cudaStream_t s, int n_chunks = 1,
-                       const int *chunk_blk = nullptr);
+// Adds the blocks' partials of every (chunk, subspace, codeword) and moves the codeword by
+// its members' mean residual; a codeword without members keeps its value (counted in empties).
+int launch_pq_finalize(const Partials &part, int gx, int M, int Ks, int ds, float *C, unsigned long long *empties,
+                       cudaStream_t s, int n_chunks = 1, const int *chunk_blk = nullptr);
 int launch_decode_rmse(const uint8_t *codes, const float *C, const float *X, int64_t N, int D, int M, int Ks,
                        float *Xhat, double *sse, cudaStream_t s);
 
@@ -74,11 +102,8 @@ int launch_decode_rmse(const uint8_t *codes, const float *C, const float *X, int
 bool tc_pass_supported(int D, int M, int Ks);
 int tc_pass_group();  // subspaces per CTA of the tensor-core pass
 int pq_pass_tc_blocks(const PqPass &p);
-// writes per-CTA residual sums (x - c_code) into p.part; finalise with the residual kernel
+// writes per-CTA residual sums (x - c_code) into p.part; finalise with launch_pq_finalize
 int launch_pq_pass_tc(PqPass &p, cudaStream_t s);
-int launch_pq_finalize_residual(const double *part, const int *part_cnt, int gx, int M, int Ks, int ds, float *C,
-                                unsigned long long *empties, cudaStream_t s, int n_chunks = 1,
-                                const int *chunk_blk = nullptr);
 
 // ---- coarse quantizer and inverted lists (coarse.cu) ----------------------
 struct CoarseBound {

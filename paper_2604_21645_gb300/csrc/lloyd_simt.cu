@@ -15,10 +15,11 @@
 // CPU reference) and the lowest-index minimum wins.  Codes are therefore
 // exact, not approximate.
 //
-// Update.  Members are added into per-block FP64 shared-memory sums (the
-// FP64 adds are a rounding error next to the FP32 distance work of this
-// form); each block writes its sums once, and the finalise kernel adds the
-// blocks in a fixed order in FP64 and divides by the member count.
+// Update.  Each member adds its residual x - c_code to its codeword's sums in
+// the exact fixed-point format of common.cuh (int32 shared-memory atomics,
+// independent of the order of the additions); each block writes its sums as
+// int64, and the finalise kernel adds the blocks in int64 and moves every
+// codeword by the float-float mean residual of its members.
 #include <algorithm>
 #include <cfloat>
 
@@ -30,13 +31,16 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// shared sums: row stride DS + 1 words, so that the atomics of a warp's random codes spread over the banks
+template <int DS>
+constexpr int acc_stride() { return DS + 1; }
+
 template <int DS>
 struct SmemLayout {
     static size_t bytes(int Ks, bool fit)
     {
-        size_t b = (size_t)Ks * DS * sizeof(double);  // sums first: 8-byte aligned
-        b += (size_t)Ks * DS * sizeof(float) + (size_t)Ks * sizeof(float);
-        if (fit) b += (size_t)Ks * sizeof(int);
+        size_t b = (size_t)Ks * DS * sizeof(float) + (size_t)Ks * sizeof(float);
+        if (fit) b += 3 * (size_t)Ks * acc_stride<DS>() * sizeof(int) + (size_t)Ks * sizeof(int);
         return b;
     }
 };
@@ -89,7 +93,7 @@ __global__ void __launch_bounds__(kThreads) pq_pass_f32_kernel(const PqPass a, c
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int m = blockIdx.y, Ks = a.Ks, tid = threadIdx.x;
-    const bool fit = a.part != nullptr;
+    const bool fit = a.part.active();
     // chunk of this block (batched form) and its rows
     int chunk = 0, lb = blockIdx.x, gxc = gridDim.x;
     int64_t r0 = 0, r1 = a.N;
@@ -100,20 +104,48 @@ __global__ void __launch_bounds__(kThreads) pq_pass_f32_kernel(const PqPass a, c
         r0 = a.chunk_off[chunk];
         r1 = a.chunk_off[chunk + 1];
     }
-    double *acc = reinterpret_cast<double *>(smem_raw);
-    float *cb = reinterpret_cast<float *>(acc + Ks * DS);
+    constexpr int AS = acc_stride<DS>();
+    float *cb = reinterpret_cast<float *>(smem_raw);
     float *cn = cb + Ks * DS;
-    int *cnt = reinterpret_cast<int *>(cn + Ks);
+    int *acch = reinterpret_cast<int *>(cn + Ks);  // [Ks][AS] high parts, then low parts, FP32 sums, counts
+    int *accl = acch + Ks * AS;
+    float *accf = reinterpret_cast<float *>(accl + Ks * AS);
+    int *cnt = reinterpret_cast<int *>(accf + Ks * AS);
     __shared__ float s_red[kThreads / 32];
     __shared__ double s_sse[kThreads / 32];
+    __shared__ float s_mu[DS];
+    __shared__ unsigned s_r0;
 
     const float *Cm = a.C + ((size_t)chunk * a.M + m) * Ks * DS;
-    for (int e = tid; e < Ks * DS; e += kThreads) {
-        cb[e] = Cm[e];
-        if (fit) acc[e] = 0.0;
-    }
-    if (fit)
+    for (int e = tid; e < Ks * DS; e += kThreads) cb[e] = Cm[e];
+    if (fit) {
+        for (int e = tid; e < Ks * AS; e += kThreads) {
+            acch[e] = 0;
+            accl[e] = 0;
+            accf[e] = 0.0f;
+        }
         for (int k = tid; k < Ks; k += kThreads) cnt[k] = 0;
+    }
+    if (tid == 0) s_r0 = 0u;
+    __syncthreads();
+    if (fit) {
+        // residual scale of the fixed-point sums: twice the largest codeword norm about the codeword mean
+        if (tid < DS) {
+            float mu = 0.0f;
+            for (int k = 0; k < Ks; ++k) mu += cb[k * DS + tid];
+            s_mu[tid] = mu / (float)Ks;
+        }
+        __syncthreads();
+        for (int k = tid; k < Ks; k += kThreads) {
+            float n = 0.0f;
+#pragma unroll
+            for (int j = 0; j < DS; ++j) {
+                const float t = cb[k * DS + j] - s_mu[j];
+                n = fmaf(t, t, n);
+            }
+            atomicMax(&s_r0, __float_as_uint(sqrtf(n)));
+        }
+    }
     __syncthreads();
     float lmax = 0.0f;
     for (int k = tid; k < Ks; k += kThreads) {
@@ -137,6 +169,9 @@ __global__ void __launch_bounds__(kThreads) pq_pass_f32_kernel(const PqPass a, c
     double sse = 0.0;
     unsigned rechecks = 0;
     const int64_t stride = (int64_t)gxc * kThreads;
+    // every block of a chunk uses the same format: the row bound is the busiest block's rows
+    const FixFmt fx = fix_format(((r1 - r0 + stride - 1) / stride) * kThreads,
+                                 2.0f * __uint_as_float(s_r0) * (1.0f + 1e-6f));
     for (int bi = 0;; ++bi) {
         const int64_t base = r0 + (int64_t)bi * stride + (int64_t)lb * kThreads;
         if (base >= r1) break;
@@ -174,18 +209,35 @@ __global__ void __launch_bounds__(kThreads) pq_pass_f32_kernel(const PqPass a, c
             sse += (double)e;
             if (a.codes) a.codes[row * a.M + m] = (uint8_t)code;
             if (fit) {
+                bool big = false;
 #pragma unroll
-                for (int j = 0; j < DS; ++j) atomicAdd(acc + code * DS + j, (double)x[j]);
+                for (int j = 0; j < DS; ++j) big |= !(fabsf(__fmul_rn(x[j] - cb[code * DS + j], fx.scale)) < fx.lim);
+                const int o = code * AS;
+                if (!big) {
+#pragma unroll
+                    for (int j = 0; j < DS; ++j) {
+                        const long long q = __float2ll_rn(__fmul_rn(x[j] - cb[code * DS + j], fx.scale));
+                        atomicAdd(acch + o + j, (int)(q >> fx.L));
+                        atomicAdd(accl + o + j, (int)(q & ((1LL << fx.L) - 1)));
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < DS; ++j) atomicAdd(accf + o + j, x[j] - cb[code * DS + j]);
+                }
                 atomicAdd(cnt + code, 1);
             }
         }
     }
     if (fit) {
         __syncthreads();
-        double *dst = a.part + ((size_t)blockIdx.x * a.M + m) * Ks * DS;
-        for (int e = tid; e < Ks * DS; e += kThreads) dst[e] = acc[e];
-        int *dc = a.part_cnt + ((size_t)blockIdx.x * a.M + m) * Ks;
-        for (int k = tid; k < Ks; k += kThreads) dc[k] = cnt[k];
+        const size_t base = ((size_t)blockIdx.x * a.M + m) * Ks;
+        for (int e = tid; e < Ks * DS; e += kThreads) {
+            const int k = e / DS, j = e % DS;
+            a.part.q[base * DS + e] = (long long)acch[k * AS + j] * (1LL << fx.L) + (long long)accl[k * AS + j];
+            a.part.o[base * DS + e] = accf[k * AS + j];
+        }
+        for (int k = tid; k < Ks; k += kThreads) a.part.cnt[base + k] = cnt[k];
+        if (lb == 0 && tid == 0) a.part.F[chunk * a.M + m] = fx.F;
     }
     if (a.sse) {
         sse = warp_sum(sse);
@@ -203,28 +255,46 @@ __global__ void __launch_bounds__(kThreads) pq_pass_f32_kernel(const PqPass a, c
     }
 }
 
-__global__ void pq_finalize_kernel(const double *__restrict__ part, const int *__restrict__ part_cnt, int gx, int M,
-                                   int Ks, int ds, float *C, unsigned long long *empties, int n_chunks,
-                                   const int *__restrict__ chunk_blk)
+// One thread per (chunk, subspace, codeword, dimension): the blocks' int64 sums added
+// exactly, the FP32 sums added with TwoSum (block order), the total scaled to a float-float
+// value, divided by the member count in float-float, and added to the codeword.
+__global__ void pq_finalize_kernel(const Partials part, int gx, int M, int Ks, int ds, float *C,
+                                   unsigned long long *empties, int n_chunks, const int *__restrict__ chunk_blk)
 {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n_chunks * M * Ks) return;
-    const int c = idx / (M * Ks), m = (idx / Ks) % M, k = idx % Ks;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n_chunks * M * Ks * ds) return;
+    const int j = (int)(idx % ds);
+    const int64_t cw = idx / ds;
+    const int c = (int)(cw / ((int64_t)M * Ks)), m = (int)((cw / Ks) % M), k = (int)(cw % Ks);
     const int b0 = chunk_blk ? chunk_blk[c] : 0, b1 = chunk_blk ? chunk_blk[c + 1] : gx;
-    C += (size_t)c * M * Ks * ds;
-    long long cnt = 0;
-    for (int b = b0; b < b1; ++b) cnt += part_cnt[((size_t)b * M + m) * Ks + k];
-    if (cnt == 0) {
-        if (empties) atomicAdd(empties, 1ull);
+    long long n = 0, q = 0;
+    float oh = 0.0f, ol = 0.0f;
+    for (int b = b0; b < b1; ++b) {
+        const size_t e = ((size_t)b * M + m) * Ks + k;
+        n += part.cnt[e];
+        q += part.q[e * ds + j];
+        float s, err;
+        two_sum(oh, part.o[e * ds + j], s, err);
+        oh = s;
+        ol = __fadd_rn(ol, err);
+    }
+    if (n == 0) {
+        if (empties && j == 0) atomicAdd(empties, 1ull);
         return;
     }
-    for (int j = 0; j < ds; ++j) {
-        double s = 0.0;
-        for (int b = b0; b < b1; ++b) {
-            s = __dadd_rn(s, part[(((size_t)b * M + m) * Ks + k) * ds + j]);
-        }
-        C[((size_t)m * Ks + k) * ds + j] = __double2float_rn(__ddiv_rn(s, (double)cnt));
-    }
+    const int F = part.F[c * M + m];
+    float sh, sl;
+    ll_to_ff(q, sh, sl);
+    sh = ldexpf(sh, -F);
+    sl = ldexpf(sl, -F);
+    ff_add(sh, sl, oh, ol, sh, sl);
+    float nh, nl, mh, ml;
+    ll_to_ff(n, nh, nl);
+    ff_div(sh, sl, nh, nl, mh, ml);
+    float *cp = C + (size_t)c * M * Ks * ds + ((size_t)m * Ks + k) * ds + j;
+    float t, e;
+    two_sum(*cp, mh, t, e);
+    *cp = __fadd_rn(t, __fadd_rn(e, ml));
 }
 
 // One thread per (row, subspace): reconstruction and/or squared error.
@@ -269,7 +339,7 @@ __global__ void decode_rmse_kernel(const uint8_t *__restrict__ codes, const floa
 template <int DS>
 int launch_ds(PqPass &p, cudaStream_t s)
 {
-    const bool fit = p.part != nullptr;
+    const bool fit = p.part.active();
     const size_t smem = SmemLayout<DS>::bytes(p.Ks, fit);
     PQ_TRY_CUDA(cudaFuncSetAttribute(pq_pass_f32_kernel<DS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const bool vec = (p.D % 4 == 0) && ((reinterpret_cast<uintptr_t>(p.X) & 15) == 0);
@@ -309,13 +379,13 @@ int launch_pq_pass_f32(PqPass &p, cudaStream_t s)
     }
 }
 
-int launch_pq_finalize(const double *part, const int *part_cnt, int gx, int M, int Ks, int ds, float *C,
-                       unsigned long long *empties, cudaStream_t s, int n_chunks, const int *chunk_blk)
+int launch_pq_finalize(const Partials &part, int gx, int M, int Ks, int ds, float *C, unsigned long long *empties,
+                       cudaStream_t s, int n_chunks, const int *chunk_blk)
 {
-    const int n = n_chunks * M * Ks;
+    const int64_t n = (int64_t)n_chunks * M * Ks * ds;
     ProfScope ps("pq_finalize", s);
-    pq_finalize_kernel<<<(n + 127) / 128, 128, 0, s>>>(part, part_cnt, gx, M, Ks, ds, C, empties, n_chunks,
-                                                       chunk_blk);
+    pq_finalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, gx, M, Ks, ds, C, empties, n_chunks,
+                                                                  chunk_blk);
     count_launch();
     PQ_TRY_CUDA(cudaGetLastError());
     return PQ_OK;

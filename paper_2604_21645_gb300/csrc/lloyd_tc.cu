@@ -28,9 +28,9 @@
 // Codes are exact.
 //
 // Update.  Residuals x - c_code are added with shared-memory int32 atomics, in
-// an exact fixed-point format (FixFmt below), into per-CTA sums; the finalise
-// kernel adds the CTAs in a fixed order in FP64 and moves every codeword by the
-// mean residual of its members.
+// the exact fixed-point format of common.cuh (FixFmt), into per-CTA sums that
+// each CTA writes as int64; the finalise kernel adds the CTAs in int64 and moves
+// every codeword by the float-float mean residual of its members.
 //
 // Pipeline (one CTA per SM, a group of 2 subspaces, persistent over row tiles
 // of 128).  Warp 0 issues TMA loads of 128 x 16 float tiles (64B swizzle) into
@@ -115,8 +115,7 @@ struct TcArgs {
     int tiles;
     const float *C;
     uint8_t *codes;
-    double *part;
-    int *part_cnt;
+    Partials part;
     double *sse;
     unsigned long long *rechecks;
     int *err;
@@ -357,32 +356,6 @@ __device__ __forceinline__ void decide_exact_warp(bool unsure, float4 v0, float4
     }
 }
 
-// Fixed-point format of the residual sums of one CTA and subspace.  A residual
-// element r becomes q = rint(r * 2^F) and is added as two int32 parts,
-// q >> L and q & (2^L - 1), so that neither running sum can overflow over the
-// CTA's at most n rows: with b = bit length of n, L = 31 - b keeps the low sum
-// below 2^31 and |q| < 2^(61 - 2b) keeps the high sum below 2^31.  F puts twice
-// the largest centred codeword norm R0 at that limit; the rare element beyond it
-// goes to an FP32 sum instead.  The integer sums are exact and independent of
-// the order of the additions.
-struct FixFmt {
-    int L, F;
-    float scale, lim;
-};
-__device__ __forceinline__ FixFmt fix_format(int64_t rows, float r0)
-{
-    const int b = 64 - __clzll((unsigned long long)rows);  // bit length of the row count
-    FixFmt f;
-    f.L = 31 - b;
-    const int qb = min(61 - 2 * b, 30);
-    int e = 0;
-    (void)frexpf(r0 > 0.0f ? r0 : 1.0f, &e);  // r0 < 2^e
-    f.F = max(-100, min(100, qb - e));
-    f.scale = ldexpf(1.0f, f.F);
-    f.lim = ldexpf(1.0f, qb);
-    return f;
-}
-
 __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                   const TcArgs a)
 {
@@ -391,7 +364,7 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int grp = blockIdx.y, m0 = grp * G;
     const int Ks = a.Ks;
-    const bool fit = a.part != nullptr;
+    const bool fit = a.part.active();
     // chunk of this CTA (batched form): its rows, its share of the CTAs, its codebooks
     int chunk = 0, lb = blockIdx.x, gxc = gridDim.x;
     int64_t r0 = 0, r1 = a.N;
@@ -626,7 +599,9 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
         float4 *svs = reinterpret_cast<float4 *>(sm + OFF_SV) + te * 8;  // 16-byte pieces swizzled by te & 7
         float sse_s = 0.0f, sse_c = 0.0f;  // Kahan pair
         unsigned rechecks = 0;
-        const FixFmt fx = fix_format((int64_t)n_my * TM, 2.0f * __uint_as_float(bnd[g * 2 + 1]));
+        // one format for every CTA of the chunk: the row bound is the busiest CTA's rows
+        const int64_t rows_bound = (int64_t)((tiles_c + gxc - 1) / gxc) * TM;
+        const FixFmt fx = fix_format(rows_bound, 2.0f * __uint_as_float(bnd[g * 2 + 1]));
         for (int i = 0; i < n_my; ++i) {
             const int s = i % NXS;
             const int64_t row = r0 + (int64_t)(lb + i * gxc) * TM + r;
@@ -739,19 +714,19 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
                 sse_s = t2;
                 if (fit) {
                     const int o = (g * KSMAX + code) * ACC_STRIDE;
-                    int q[DS];
+                    long long q[DS];
                     bool big = false;
 #pragma unroll
                     for (int d = 0; d < DS; ++d) {
-                        const float t = res[d] * fx.scale;
+                        const float t = __fmul_rn(res[d], fx.scale);
                         big |= !(fabsf(t) < fx.lim);
-                        q[d] = __float2int_rn(t);
+                        q[d] = __float2ll_rn(t);
                     }
                     if (!big) {
 #pragma unroll
                         for (int d = 0; d < DS; ++d) {
-                            atomicAdd(acch + o + d, q[d] >> fx.L);
-                            atomicAdd(accl + o + d, q[d] & ((1 << fx.L) - 1));
+                            atomicAdd(acch + o + d, (int)(q[d] >> fx.L));
+                            atomicAdd(accl + o + d, (int)(q[d] & ((1LL << fx.L) - 1)));
                         }
                     } else {
 #pragma unroll
@@ -765,18 +740,20 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
         // ---- results of this CTA -------------------------------------------
         asm volatile("bar.sync 1, 256;" ::: "memory");
         if (fit) {
+            const int64_t rows_bound = (int64_t)((tiles_c + gxc - 1) / gxc) * TM;
             for (int e = tid - kEpi0; e < G * KSMAX; e += 256) {
                 const int gg = e / KSMAX, k = e % KSMAX;
                 if (k >= Ks) continue;
                 const size_t base = ((size_t)blockIdx.x * a.M + m0 + gg) * Ks + k;
-                const FixFmt f = fix_format((int64_t)n_my * TM, 2.0f * __uint_as_float(bnd[gg * 2 + 1]));
+                const FixFmt f = fix_format(rows_bound, 2.0f * __uint_as_float(bnd[gg * 2 + 1]));
                 const int o = (gg * KSMAX + k) * ACC_STRIDE;
 #pragma unroll
                 for (int d = 0; d < DS; ++d) {
-                    const long long qs = (long long)acch[o + d] * (1LL << f.L) + (long long)accl[o + d];
-                    a.part[base * DS + d] = ldexp((double)qs, -f.F) + (double)accf[o + d];
+                    a.part.q[base * DS + d] = (long long)acch[o + d] * (1LL << f.L) + (long long)accl[o + d];
+                    a.part.o[base * DS + d] = accf[o + d];
                 }
-                a.part_cnt[base] = cnt[gg * KSMAX + k];
+                a.part.cnt[base] = cnt[gg * KSMAX + k];
+                if (lb == 0 && k == 0) a.part.F[chunk * a.M + m0 + gg] = f.F;
             }
         }
         double tot = (double)sse_s - (double)sse_c;
@@ -792,31 +769,6 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
         __syncwarp();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
     }
-}
-
-// One thread per (chunk, subspace, codeword, dimension): the FP64 sum of the CTAs' partials in
-// block order, then the codeword moves by the mean residual of its members.
-__global__ void pq_finalize_residual_kernel(const double *__restrict__ part, const int *__restrict__ part_cnt, int gx,
-                                            int M, int Ks, int ds, float *C, unsigned long long *empties, int n_chunks,
-                                            const int *__restrict__ chunk_blk)
-{
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)n_chunks * M * Ks * ds) return;
-    const int j = (int)(idx % ds);
-    const int64_t cw = idx / ds;
-    const int c = (int)(cw / ((int64_t)M * Ks)), m = (int)((cw / Ks) % M), k = (int)(cw % Ks);
-    const int b0 = chunk_blk ? chunk_blk[c] : 0, b1 = chunk_blk ? chunk_blk[c + 1] : gx;
-    C += (size_t)c * M * Ks * ds;
-    long long n = 0;
-    for (int b = b0; b < b1; ++b) n += part_cnt[((size_t)b * M + m) * Ks + k];
-    if (n == 0) {
-        if (empties && j == 0) atomicAdd(empties, 1ull);
-        return;
-    }
-    double sum = 0.0;
-    for (int b = b0; b < b1; ++b) sum = __dadd_rn(sum, part[(((size_t)b * M + m) * Ks + k) * ds + j]);
-    float *cp = C + ((size_t)m * Ks + k) * ds + j;
-    *cp = __double2float_rn(__dadd_rn((double)*cp, __ddiv_rn(sum, (double)n)));
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode()
@@ -879,7 +831,6 @@ int launch_pq_pass_tc(PqPass &p, cudaStream_t s)
     a.C = p.C;
     a.codes = p.codes;
     a.part = p.part;
-    a.part_cnt = p.part_cnt;
     a.sse = p.sse;
     a.rechecks = p.rechecks;
     a.err = err;
@@ -890,18 +841,6 @@ int launch_pq_pass_tc(PqPass &p, cudaStream_t s)
     dim3 grid(p.gx, p.M / G);
     ProfScope ps("pq_pass_tc", s);
     pq_pass_tc_kernel<<<grid, kThreads, SMEM_BYTES, s>>>(map, a);
-    count_launch();
-    PQ_TRY_CUDA(cudaGetLastError());
-    return PQ_OK;
-}
-
-int launch_pq_finalize_residual(const double *part, const int *part_cnt, int gx, int M, int Ks, int ds, float *C,
-                                unsigned long long *empties, cudaStream_t s, int n_chunks, const int *chunk_blk)
-{
-    const int64_t n = (int64_t)n_chunks * M * Ks * ds;
-    ProfScope ps("pq_finalize", s);
-    pq_finalize_residual_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, part_cnt, gx, M, Ks, ds, C, empties,
-                                                                           n_chunks, chunk_blk);
     count_launch();
     PQ_TRY_CUDA(cudaGetLastError());
     return PQ_OK;

@@ -66,13 +66,12 @@ extern "C" int pq_lloyd_noalloc(const float *X, int64_t N, int32_t D, int32_t M,
     // the subspace widths the FP32 pass is compiled for; checked before anything is enqueued
     if (ds != 1 && ds != 2 && ds != 4 && ds != 8 && ds != 16 && ds != 32)
         return fail(PQ_ENOTSUP, "subspace width Ds=%d not supported (1, 2, 4, 8, 16 or 32)", ds);
-    // One block-subspace slot holds Ks*ds FP64 sums and Ks int32 counts.
-    const size_t slot = (size_t)Ks * ds * sizeof(double) + (size_t)Ks * sizeof(int);
-    const size_t per_gx = slot * (size_t)M;
-    if (per_gx > kNoAllocScratchBytes)
+    // One block needs, per subspace, Ks*ds int64 and Ks*ds FP32 sums and Ks int32 counts.
+    const size_t need1 = Partials::bytes(1, M, Ks, ds, 1);
+    if (need1 > kNoAllocScratchBytes)
         return fail(PQ_EINVAL,
-                    "pq_lloyd_noalloc: M*Ks*(8*D/M + 4) = %zu bytes exceeds its fixed scratch of %zu bytes",
-                    per_gx, kNoAllocScratchBytes);
+                    "pq_lloyd_noalloc: M*Ks*(12*D/M + 4) + 4*M + 64 = %zu bytes exceeds its fixed scratch of %zu bytes",
+                    need1, kNoAllocScratchBytes);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int dev = 0;
     PQ_TRY_CUDA(cudaGetDevice(&dev));
@@ -88,20 +87,17 @@ extern "C" int pq_lloyd_noalloc(const float *X, int64_t N, int32_t D, int32_t M,
     p.ds = ds;
     p.C = codebooks;
     p.gx = pq_pass_blocks_per_subspace(p);
-    const int gx_fit = (int)(kNoAllocScratchBytes / per_gx);
-    if (p.gx > gx_fit) p.gx = gx_fit;
-    // Layout: [gx][M][Ks][ds] doubles, then [gx][M][Ks] ints.  Every pass
-    // overwrites all of it before the finalise kernel reads it, so nothing
-    // left by an earlier call needs clearing.
-    p.part = static_cast<double *>(base);
-    p.part_cnt = reinterpret_cast<int *>(static_cast<unsigned char *>(base) +
-                                         (size_t)p.gx * M * Ks * ds * sizeof(double));
+    while (p.gx > 1 && Partials::bytes(p.gx, M, Ks, ds, 1) > kNoAllocScratchBytes) --p.gx;
+    // Layout (Partials::carve): [gx][M][Ks][ds] int64 and FP32 sums, [gx][M][Ks] counts,
+    // [M] exponents.  Every pass overwrites all of it before the finalise kernel reads it,
+    // so nothing left by an earlier call needs clearing.
+    p.part.carve(base, p.gx, M, Ks, ds);
     if (init_codebooks != codebooks)
         PQ_TRY_CUDA(cudaMemcpyAsync(codebooks, init_codebooks, (size_t)M * Ks * ds * sizeof(float),
                                     cudaMemcpyDeviceToDevice, s));
     for (int t = 0; t < iters; ++t) {
         PQ_TRY(launch_pq_pass_f32(p, s));
-        PQ_TRY(launch_pq_finalize(p.part, p.part_cnt, p.gx, M, Ks, ds, codebooks, nullptr, s));
+        PQ_TRY(launch_pq_finalize(p.part, p.gx, M, Ks, ds, codebooks, nullptr, s));
     }
     return PQ_OK;
 }
