@@ -67,6 +67,12 @@ def _load():
                 "orc_softpq_forward": (dbl, [p, i64, i32, i32, i32, p, dbl]),
                 "orc_softpq_backward": (None, [p, i64, i32, i32, i32, p, dbl, p, p]),
                 "orc_num_threads": (i32, []),
+                "orc_sdc_table": (None, [p, i32, i32, i32, p]),
+                "orc_pick_distinct": (i32, [i64, i32, u64, p]),
+                "orc_assign_codes": (None, [p, i64, i32, i32, p, p, i32, p, p]),
+                "orc_update_centers": (i32, [p, i64, i32, i32, p, p, i32, p]),
+                "orc_ivf_build_codes": (i32, [p, i64, i32, i32, i32, p, i32, i32, u64, p, p, p, p, p, p]),
+                "orc_ivf_search_codes": (i32, [p, p, p, p, i32, i32, i32, i32, p, p, i64, i32, i32, p, p, p]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -227,6 +233,83 @@ def exact_knn(X, Q, k: int):
     dist = np.empty((nq, k), dtype=np.float64)
     _check(_load().orc_exact_knn(_ptr(X), N, D, _ptr(Q), nq, k, _ptr(ids), _ptr(dist)), "exact_knn")
     return ids, dist
+
+
+# -- code-space coarse quantizer (Rii, Sec. 3.1) ---------------------------------
+
+def sdc_table(codebooks) -> np.ndarray:
+    """DT[m][k][j] = ||c_{m,k} - c_{m,j}||^2 (FP64)."""
+    cb = _f32(codebooks)
+    M, Ks, ds = cb.shape
+    DT = np.empty((M, Ks, Ks), dtype=np.float64)
+    _load().orc_sdc_table(_ptr(cb), M, Ks, ds, _ptr(DT))
+    return DT
+
+
+def pick_distinct(N: int, nlist: int, seed: int) -> np.ndarray:
+    out = np.empty(nlist, dtype=np.int64)
+    _check(_load().orc_pick_distinct(N, nlist, seed & (2**64 - 1), _ptr(out)), "pick_distinct")
+    return out
+
+
+def assign_codes(codes, DT, centers):
+    """Nearest centre code of every row code by symmetric distance: (lists int32, SDC float64)."""
+    codes = np.ascontiguousarray(codes, dtype=np.uint8)
+    centers = np.ascontiguousarray(centers, dtype=np.uint8)
+    DT = np.ascontiguousarray(DT, dtype=np.float64)
+    N, M = codes.shape
+    Ks = DT.shape[1]
+    lst = np.empty(N, dtype=np.int32)
+    dist = np.empty(N, dtype=np.float64)
+    _load().orc_assign_codes(_ptr(codes), N, M, Ks, _ptr(DT), _ptr(centers), centers.shape[0], _ptr(lst), _ptr(dist))
+    return lst, dist
+
+
+def update_centers(codes, DT, lists, centers):
+    codes = np.ascontiguousarray(codes, dtype=np.uint8)
+    out = np.ascontiguousarray(centers, dtype=np.uint8).copy()
+    DT = np.ascontiguousarray(DT, dtype=np.float64)
+    lists = np.ascontiguousarray(lists, dtype=np.int32)
+    N, M = codes.shape
+    _check(_load().orc_update_centers(_ptr(codes), N, M, DT.shape[1], _ptr(DT), _ptr(lists), out.shape[0],
+                                      _ptr(out)), "update_centers")
+    return out
+
+
+def ivf_build_codes(codes, codebooks, nlist: int, iters: int, seed: int):
+    """Code-space index.  Returns dict(centers, offsets, ids, list_codes, list_of_row, obj)."""
+    codes = np.ascontiguousarray(codes, dtype=np.uint8)
+    cb = _f32(codebooks)
+    N, M = codes.shape
+    _, Ks, ds = cb.shape
+    centers = np.empty((nlist, M), dtype=np.uint8)
+    offsets = np.empty(nlist + 1, dtype=np.int64)
+    ids = np.empty(N, dtype=np.int64)
+    lc = np.empty((N, M), dtype=np.uint8)
+    lor = np.empty(N, dtype=np.int32)
+    obj = np.zeros(max(iters, 1), dtype=np.float64)
+    _check(_load().orc_ivf_build_codes(_ptr(codes), N, M, Ks, ds, _ptr(cb), nlist, iters, seed & (2**64 - 1),
+                                       _ptr(centers), _ptr(offsets), _ptr(ids), _ptr(lc), _ptr(lor), _ptr(obj)),
+           "ivf_build_codes")
+    return {"centers": centers, "offsets": offsets, "ids": ids, "list_codes": lc, "list_of_row": lor,
+            "obj": obj[:iters]}
+
+
+def ivf_search_codes(index, codebooks, Q, nprobe: int, k: int):
+    """Returns (ids int64 [nq][k], ADC distances float64 [nq][k], probed lists int32 [nq][nprobe])."""
+    Q = _f32(Q)
+    cb = _f32(codebooks)
+    nq, D = Q.shape
+    M, Ks, _ = cb.shape
+    centers = np.ascontiguousarray(index["centers"], dtype=np.uint8)
+    nlist = centers.shape[0]
+    ids = np.empty((nq, k), dtype=np.int64)
+    dist = np.empty((nq, k), dtype=np.float64)
+    probes = np.empty((nq, nprobe), dtype=np.int32)
+    _check(_load().orc_ivf_search_codes(_ptr(centers), _ptr(index["offsets"]), _ptr(index["ids"]),
+                                        _ptr(index["list_codes"]), nlist, D, M, Ks, _ptr(cb), _ptr(Q), nq, nprobe,
+                                        k, _ptr(ids), _ptr(dist), _ptr(probes)), "ivf_search_codes")
+    return ids, dist, probes
 
 
 # -- chunked divide and conquer (Sec. 3) -----------------------------------------

@@ -647,6 +647,227 @@ void orc_softpq_backward(const double *X, int64_t N, int D, int M, int Ks, const
     free(r);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Code-space coarse quantizer: Rii's inverted index over the PQ codes       */
+/* (Sec. 3.1: an IVFPQ-style index built from the codes themselves).         */
+/* ------------------------------------------------------------------------ */
+
+#define ORC_STREAM_CENTERS 0xFFFFFFFDull
+
+/*
+ * Symmetric distance table of the codebooks: DT[m][k][j] = ||c_{m,k} - c_{m,j}||^2
+ * in FP64 by direct differences in dimension order.  The symmetric distance of
+ * two codes a, b is SDC(a, b) = sum over m (in order) of DT[m][a_m][b_m]: the
+ * squared distance of the two reconstructions, taken subspace by subspace.
+ */
+void orc_sdc_table(const float *C, int M, int Ks, int ds, double *DT)
+{
+    for (int m = 0; m < M; ++m)
+        for (int k = 0; k < Ks; ++k)
+            for (int j = 0; j < Ks; ++j)
+                DT[((size_t)m * Ks + k) * Ks + j] =
+                    d2_f64(C + ((size_t)m * Ks + k) * ds, C + ((size_t)m * Ks + j) * ds, ds);
+}
+
+static double sdc(const double *DT, int M, int Ks, const uint8_t *a, const uint8_t *b)
+{
+    double s = 0.0;
+    for (int m = 0; m < M; ++m) s += DT[((size_t)m * Ks + a[m]) * Ks + b[m]];
+    return s;
+}
+
+/*
+ * nlist distinct row indices of [0, N) by Floyd's sampling algorithm (Bentley &
+ * Floyd, "A sample of brilliance", CACM 1987): for j = N - nlist .. N - 1 draw t
+ * uniform in [0, j]; take t unless it was taken already, else take j.  Draw i
+ * is floor(u * (j + 1)) with u the 53-bit output i of the centre stream of
+ * `seed`.  out[nlist] in the order taken.
+ */
+int orc_pick_distinct(int64_t N, int nlist, uint64_t seed, int64_t *out)
+{
+    if (nlist < 1 || nlist > N) return ORC_EINVAL;
+    for (int i = 0; i < nlist; ++i) {
+        int64_t j = N - nlist + i;
+        int64_t t = orc_scale53(orc_draw(seed, ORC_STREAM_CENTERS, (uint64_t)i) >> 11, j + 1);
+        int taken = 0;
+        for (int q = 0; q < i; ++q) taken |= out[q] == t;
+        out[i] = taken ? j : t;
+    }
+    return ORC_OK;
+}
+
+/* Nearest centre code of every row code by SDC (ties to the lower centre); its SDC in dist (nullable). */
+void orc_assign_codes(const uint8_t *codes, int64_t N, int M, int Ks, const double *DT, const uint8_t *centers,
+                      int nlist, int32_t *lst, double *dist)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < N; ++n) {
+        double best = INFINITY;
+        int32_t bl = 0;
+        for (int l = 0; l < nlist; ++l) {
+            double d = sdc(DT, M, Ks, codes + n * M, centers + (size_t)l * M);
+            if (d < best) { best = d; bl = l; }
+        }
+        lst[n] = bl;
+        if (dist) dist[n] = best;
+    }
+}
+
+/*
+ * Centre update (the "sparse voting" step of k-means over PQ codes): for every
+ * list l and subspace m, with h[j] the number of members whose code in m is j,
+ * the new centre code is argmin over k of cost(k) = sum over j (ascending) of
+ * h[j] * DT[m][k][j] -- the code minimising the summed SDC term of that
+ * subspace to the members -- ties to the lower k.  A list without members keeps
+ * its centre.
+ */
+int orc_update_centers(const uint8_t *codes, int64_t N, int M, int Ks, const double *DT, const int32_t *lst,
+                       int nlist, uint8_t *centers)
+{
+    int64_t *h = (int64_t *)calloc((size_t)nlist * M * Ks, sizeof(int64_t));
+    int64_t *n_l = (int64_t *)calloc((size_t)nlist, sizeof(int64_t));
+    if (!h || !n_l) { free(h); free(n_l); return ORC_ENOMEM; }
+    for (int64_t n = 0; n < N; ++n) {
+        n_l[lst[n]] += 1;
+        for (int m = 0; m < M; ++m) h[((size_t)lst[n] * M + m) * Ks + codes[n * M + m]] += 1;
+    }
+    for (int l = 0; l < nlist; ++l) {
+        if (n_l[l] == 0) continue;
+        for (int m = 0; m < M; ++m) {
+            const int64_t *hm = h + ((size_t)l * M + m) * Ks;
+            double best = INFINITY;
+            int bk = 0;
+            for (int k = 0; k < Ks; ++k) {
+                double cost = 0.0;
+                for (int j = 0; j < Ks; ++j) cost += (double)hm[j] * DT[((size_t)m * Ks + k) * Ks + j];
+                if (cost < best) { best = cost; bk = k; }
+            }
+            centers[(size_t)l * M + m] = (uint8_t)bk;
+        }
+    }
+    free(h);
+    free(n_l);
+    return ORC_OK;
+}
+
+/*
+ * Build: centre codes by k-means over the PQ codes (nlist rows picked by
+ * orc_pick_distinct as the starting centres, `iters` rounds of
+ * orc_assign_codes + orc_update_centers), then every row in the list of its
+ * nearest centre, CSR lists with ids ascending.  obj[t] (nullable) is the total
+ * SDC of round t's assignment to the centres it started from.
+ */
+int orc_ivf_build_codes(const uint8_t *codes, int64_t N, int M, int Ks, int ds, const float *C, int nlist,
+                        int iters, uint64_t seed, uint8_t *centers, int64_t *offsets, int64_t *ids,
+                        uint8_t *list_codes, int32_t *list_of_row, double *obj)
+{
+    if (nlist < 1 || nlist > N || Ks < 1 || Ks > 256 || iters < 0) return ORC_EINVAL;
+    double *DT = (double *)malloc((size_t)M * Ks * Ks * sizeof(double));
+    int64_t *pick = (int64_t *)malloc((size_t)nlist * sizeof(int64_t));
+    int32_t *lst = (int32_t *)malloc((size_t)N * sizeof(int32_t));
+    double *dist = (double *)malloc((size_t)N * sizeof(double));
+    int64_t *fill = (int64_t *)malloc((size_t)nlist * sizeof(int64_t));
+    int rc = ORC_OK;
+    if (!DT || !pick || !lst || !dist || !fill) { rc = ORC_ENOMEM; goto done; }
+    orc_sdc_table(C, M, Ks, ds, DT);
+    orc_pick_distinct(N, nlist, seed, pick);
+    for (int l = 0; l < nlist; ++l) memcpy(centers + (size_t)l * M, codes + pick[l] * M, (size_t)M);
+    for (int t = 0; t < iters; ++t) {
+        orc_assign_codes(codes, N, M, Ks, DT, centers, nlist, lst, dist);
+        if (obj) {
+            double s = 0.0;
+            for (int64_t n = 0; n < N; ++n) s += dist[n];
+            obj[t] = s;
+        }
+        rc = orc_update_centers(codes, N, M, Ks, DT, lst, nlist, centers);
+        if (rc) goto done;
+    }
+    orc_assign_codes(codes, N, M, Ks, DT, centers, nlist, lst, NULL);
+    for (int l = 0; l <= nlist; ++l) offsets[l] = 0;
+    for (int64_t n = 0; n < N; ++n) offsets[lst[n] + 1] += 1;
+    for (int l = 0; l < nlist; ++l) offsets[l + 1] += offsets[l];
+    for (int l = 0; l < nlist; ++l) fill[l] = offsets[l];
+    for (int64_t n = 0; n < N; ++n) {
+        int64_t p = fill[lst[n]]++;
+        ids[p] = n;
+        memcpy(list_codes + p * M, codes + n * M, (size_t)M);
+    }
+    if (list_of_row) memcpy(list_of_row, lst, (size_t)N * sizeof(int32_t));
+done:
+    free(DT);
+    free(pick);
+    free(lst);
+    free(dist);
+    free(fill);
+    return rc;
+}
+
+/*
+ * Query of the code-space index: the per-query table LUT[m][k] = ||q_m - c_{m,k}||^2
+ * (FP64) scores both the centre codes (probe: the nprobe lowest sum over m of
+ * LUT[m][centre_m], ties to the lower list) and the stored codes of the probed
+ * lists; the k best by (score, id), missing results id -1 and +inf.
+ */
+int orc_ivf_search_codes(const uint8_t *centers, const int64_t *offsets, const int64_t *ids,
+                         const uint8_t *list_codes, int nlist, int D, int M, int Ks, const float *C, const float *Q,
+                         int64_t nq, int nprobe, int k, int64_t *out_ids, double *out_d, int32_t *probes)
+{
+    if (nprobe < 1 || nprobe > nlist || k < 1 || D % M != 0) return ORC_EINVAL;
+    int ds = D / M;
+    int rc = ORC_OK;
+    #pragma omp parallel
+    {
+        orc_cand *cl = (orc_cand *)malloc((size_t)nlist * sizeof(orc_cand));
+        double *lut = (double *)malloc((size_t)M * Ks * sizeof(double));
+        size_t cap = 1024;
+        orc_cand *cand = (orc_cand *)malloc(cap * sizeof(orc_cand));
+        if (!cl || !lut || !cand) rc = ORC_ENOMEM;
+        #pragma omp for schedule(dynamic, 16)
+        for (int64_t q = 0; q < nq; ++q) {
+            if (rc) continue;
+            const float *qv = Q + q * D;
+            for (int m = 0; m < M; ++m)
+                for (int kk = 0; kk < Ks; ++kk)
+                    lut[m * Ks + kk] = d2_f64(qv + m * ds, C + ((size_t)m * Ks + kk) * ds, ds);
+            for (int l = 0; l < nlist; ++l) {
+                double s = 0.0;
+                for (int m = 0; m < M; ++m) s += lut[m * Ks + centers[(size_t)l * M + m]];
+                cl[l].d = s;
+                cl[l].id = l;
+            }
+            qsort(cl, (size_t)nlist, sizeof(orc_cand), cand_cmp);
+            size_t nc = 0;
+            for (int p = 0; p < nprobe; ++p) {
+                int l = (int)cl[p].id;
+                if (probes) probes[q * nprobe + p] = l;
+                for (int64_t e = offsets[l]; e < offsets[l + 1]; ++e) {
+                    const uint8_t *code = list_codes + e * M;
+                    double s = 0.0;
+                    for (int m = 0; m < M; ++m) s += lut[m * Ks + code[m]];
+                    if (nc == cap) {
+                        cap *= 2;
+                        orc_cand *nb = (orc_cand *)realloc(cand, cap * sizeof(orc_cand));
+                        if (!nb) { rc = ORC_ENOMEM; break; }
+                        cand = nb;
+                    }
+                    cand[nc].d = s;
+                    cand[nc].id = ids[e];
+                    ++nc;
+                }
+            }
+            qsort(cand, nc, sizeof(orc_cand), cand_cmp);
+            for (int r = 0; r < k; ++r) {
+                out_ids[q * k + r] = (size_t)r < nc ? cand[r].id : -1;
+                out_d[q * k + r] = (size_t)r < nc ? cand[r].d : INFINITY;
+            }
+        }
+        free(cl);
+        free(lut);
+        free(cand);
+    }
+    return rc;
+}
+
 /* Threads the OpenMP regions above will use. */
 int orc_num_threads(void)
 {
