@@ -67,6 +67,9 @@ def _load():
                 "orc_softpq_forward": (dbl, [p, i64, i32, i32, i32, p, dbl]),
                 "orc_softpq_backward": (None, [p, i64, i32, i32, i32, p, dbl, p, p]),
                 "orc_num_threads": (i32, []),
+                "orc_pq_fit_counts": (i32, [p, i64, i32, i32, i32, i32, u64, p, p]),
+                "orc_pq_fit_weighted": (i32, [p, p, i64, i32, i32, i32, i32, u64, p]),
+                "orc_pq_fit_chunked_weighted": (i32, [p, p, i32, i32, i32, i32, i32, u64, p, p, p, p, p]),
                 "orc_sdc_table": (None, [p, i32, i32, i32, p]),
                 "orc_pick_distinct": (i32, [i64, i32, u64, p]),
                 "orc_assign_codes": (None, [p, i64, i32, i32, p, p, i32, p, p]),
@@ -328,6 +331,45 @@ def pq_fit_chunked(X, chunk_offsets, M: int, Ks: int, iters: int, seed: int):
     _check(_load().orc_pq_fit_chunked(_ptr(X), _ptr(off), n_chunks, D, M, Ks, iters, seed & (2**64 - 1), _ptr(gC),
                                       _ptr(codes), _ptr(rmse), _ptr(local)), "pq_fit_chunked")
     return gC, codes, float(rmse[0]), local
+
+
+def pq_fit_counts(X, M: int, Ks: int, iters: int, seed: int):
+    """PQ fit; returns (codebooks, member counts [M][Ks] of the last update)."""
+    X = _f32(X)
+    N, D = X.shape
+    out = np.empty((M, Ks, D // M), dtype=np.float32)
+    cnt = np.empty((M, Ks), dtype=np.int64)
+    _check(_load().orc_pq_fit_counts(_ptr(X), N, D, M, Ks, iters, seed & (2**64 - 1), _ptr(out), _ptr(cnt)),
+           "pq_fit_counts")
+    return out, cnt
+
+
+def pq_fit_weighted(P, W, M: int, Ks: int, iters: int, seed: int):
+    """Weighted PQ fit of points P [n][D] with weights W [n][M] (int64)."""
+    P = _f32(P)
+    W = np.ascontiguousarray(W, dtype=np.int64)
+    n, D = P.shape
+    out = np.empty((M, Ks, D // M), dtype=np.float32)
+    _check(_load().orc_pq_fit_weighted(_ptr(P), _ptr(W), n, D, M, Ks, iters, seed & (2**64 - 1), _ptr(out)),
+           "pq_fit_weighted")
+    return out
+
+
+def pq_fit_chunked_weighted(X, chunk_offsets, M: int, Ks: int, iters: int, seed: int):
+    """Returns (global codebooks, codes, RMSE, local codebooks, weights [n_chunks*Ks][M])."""
+    X = _f32(X)
+    off = np.ascontiguousarray(chunk_offsets, dtype=np.int64)
+    n_chunks = off.shape[0] - 1
+    N, D = X.shape
+    gC = np.empty((M, Ks, D // M), dtype=np.float32)
+    codes = np.empty((N, M), dtype=np.uint8)
+    rmse = np.zeros(1, dtype=np.float64)
+    local = np.empty((n_chunks, M, Ks, D // M), dtype=np.float32)
+    W = np.empty((n_chunks * Ks, M), dtype=np.int64)
+    _check(_load().orc_pq_fit_chunked_weighted(_ptr(X), _ptr(off), n_chunks, D, M, Ks, iters, seed & (2**64 - 1),
+                                               _ptr(gC), _ptr(codes), _ptr(rmse), _ptr(local), _ptr(W)),
+           "pq_fit_chunked_weighted")
+    return gC, codes, float(rmse[0]), local, W
 
 
 # -- soft-assignment refinement ----------------------------------------------------

@@ -545,6 +545,125 @@ int orc_pq_fit_chunked(const float *X, const int64_t *chunk_offsets, int n_chunk
     return rc;
 }
 
+/*
+ * PQ fit that also returns the member counts of its last update:
+ * counts[M][Ks] = the number of rows whose nearest codeword (under the codebooks
+ * the last iteration started from) is k -- the rows whose mean the final
+ * codeword is.  With iters = 0 every count is 1.
+ */
+int orc_pq_fit_counts(const float *X, int64_t N, int D, int M, int Ks, int iters, uint64_t seed, float *C,
+                      int64_t *counts)
+{
+    int rc = orc_kmeanspp(X, N, D, M, Ks, seed, C);
+    if (rc) return rc;
+    for (int64_t i = 0; i < (int64_t)M * Ks; ++i) counts[i] = 1;
+    int32_t *codes = (int32_t *)malloc((size_t)N * M * sizeof(int32_t));
+    if (!codes) return ORC_ENOMEM;
+    for (int t = 0; t < iters && !rc; ++t) {
+        orc_assign(X, N, D, M, Ks, C, codes, NULL, NULL);
+        rc = orc_update(X, N, D, M, Ks, codes, C, counts);
+    }
+    free(codes);
+    return rc;
+}
+
+/*
+ * Weighted PQ fit of n points P[n][D] with per-(point, subspace) weights
+ * W[n][M]: k-means++ seeding of the points as they are (unweighted), then
+ * `iters` rounds of assignment (nearest codeword, as in orc_assign) and weighted
+ * update: codeword k of subspace m becomes sum_p W[p][m] x_{p,m} / sum_p W[p][m]
+ * over its members p (FP64 sums in point order, one rounding to float32); a
+ * codeword whose members weigh 0 keeps its value.
+ */
+int orc_pq_fit_weighted(const float *P, const int64_t *W, int64_t n, int D, int M, int Ks, int iters, uint64_t seed,
+                        float *C)
+{
+    if (M <= 0 || D % M != 0 || Ks <= 0 || n < Ks || iters < 0) return ORC_EINVAL;
+    int ds = D / M;
+    int rc = orc_kmeanspp(P, n, D, M, Ks, seed, C);
+    if (rc) return rc;
+    int32_t *codes = (int32_t *)malloc((size_t)n * M * sizeof(int32_t));
+    double *sum = (double *)malloc((size_t)M * Ks * ds * sizeof(double));
+    double *wt = (double *)malloc((size_t)M * Ks * sizeof(double));
+    if (!codes || !sum || !wt) { free(codes); free(sum); free(wt); return ORC_ENOMEM; }
+    for (int t = 0; t < iters; ++t) {
+        orc_assign(P, n, D, M, Ks, C, codes, NULL, NULL);
+        memset(sum, 0, (size_t)M * Ks * ds * sizeof(double));
+        memset(wt, 0, (size_t)M * Ks * sizeof(double));
+        for (int64_t p = 0; p < n; ++p) {
+            for (int m = 0; m < M; ++m) {
+                int32_t k = codes[p * M + m];
+                double w = (double)W[p * M + m];
+                const float *x = P + p * D + (int64_t)m * ds;
+                double *s = sum + ((size_t)m * Ks + k) * ds;
+                for (int j = 0; j < ds; ++j) s[j] += w * (double)x[j];
+                wt[(size_t)m * Ks + k] += w;
+            }
+        }
+        for (int m = 0; m < M; ++m)
+            for (int k = 0; k < Ks; ++k) {
+                double w = wt[(size_t)m * Ks + k];
+                if (w == 0.0) continue;
+                for (int j = 0; j < ds; ++j)
+                    C[((size_t)m * Ks + k) * ds + j] = (float)(sum[((size_t)m * Ks + k) * ds + j] / w);
+            }
+    }
+    free(codes);
+    free(sum);
+    free(wt);
+    return ORC_OK;
+}
+
+/*
+ * The divide-and-conquer fit with a weighted centroid dataset: as
+ * orc_pq_fit_chunked, except that pooled codeword k of subspace m of chunk c
+ * carries the weight W = its member count in the chunk's last Lloyd update (the
+ * number of the chunk's rows it is the mean of), and the global model is the
+ * weighted fit of the pooled codewords (orc_pq_fit_weighted).  weights
+ * [n_chunks*Ks][M] (optional) receives W.
+ */
+int orc_pq_fit_chunked_weighted(const float *X, const int64_t *chunk_offsets, int n_chunks, int D, int M, int Ks,
+                                int iters, uint64_t seed, float *global_C, uint8_t *codes, double *rmse,
+                                float *local_C, int64_t *weights)
+{
+    if (n_chunks < 1 || M <= 0 || D % M != 0 || Ks <= 0 || Ks > 256) return ORC_EINVAL;
+    int ds = D / M;
+    size_t cb = (size_t)M * Ks * ds;
+    int64_t npool = (int64_t)n_chunks * Ks;
+    float *Cc = (float *)malloc(cb * sizeof(float));
+    int64_t *cnt = (int64_t *)malloc((size_t)M * Ks * sizeof(int64_t));
+    float *pool = (float *)malloc((size_t)npool * D * sizeof(float));
+    int64_t *W = (int64_t *)malloc((size_t)npool * M * sizeof(int64_t));
+    int rc = ORC_OK;
+    if (!Cc || !cnt || !pool || !W) { rc = ORC_ENOMEM; goto done; }
+    for (int c = 0; c < n_chunks; ++c) {
+        int64_t r0 = chunk_offsets[c], r1 = chunk_offsets[c + 1];
+        uint64_t sc = orc_draw(seed, ORC_STREAM_CHUNK, (uint64_t)c);
+        rc = orc_pq_fit_counts(X + r0 * D, r1 - r0, D, M, Ks, iters, sc, Cc, cnt);
+        if (rc) goto done;
+        if (local_C) memcpy(local_C + (size_t)c * cb, Cc, cb * sizeof(float));
+        for (int k = 0; k < Ks; ++k)
+            for (int m = 0; m < M; ++m) {
+                memcpy(pool + ((size_t)c * Ks + k) * D + (size_t)m * ds, Cc + ((size_t)m * Ks + k) * ds,
+                       (size_t)ds * sizeof(float));
+                W[((size_t)c * Ks + k) * M + m] = cnt[(size_t)m * Ks + k];
+            }
+    }
+    if (weights) memcpy(weights, W, (size_t)npool * M * sizeof(int64_t));
+    rc = orc_pq_fit_weighted(pool, W, npool, D, M, Ks, iters, seed, global_C);
+    if (!rc) {
+        int64_t N = chunk_offsets[n_chunks];
+        rc = orc_pq_encode(X, N, D, M, Ks, global_C, codes);
+        if (!rc && rmse) *rmse = orc_pq_rmse(X, codes, N, D, M, Ks, global_C);
+    }
+done:
+    free(Cc);
+    free(cnt);
+    free(pool);
+    free(W);
+    return rc;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Soft-assignment codebook refinement (FP64 inputs).                        */
 /* ------------------------------------------------------------------------ */

@@ -439,3 +439,74 @@ def test_softpq_limits():
     big = orc.softpq_forward(X, cb, 1e12)
     mean_cw = np.concatenate([cb[m].mean(axis=0) for m in range(2)])
     np.testing.assert_allclose(big, ((X - mean_cw) ** 2).sum() / 50, rtol=1e-9)
+
+
+# -- weighted centroid dataset (Sec. 3 variant) ----------------------------------------------
+
+def test_pq_fit_counts_are_the_last_update_members():
+    X = datagen.mixture(4000, 8, 10, "cont", 60)
+    C, cnt = orc.pq_fit_counts(X, 2, 16, 5, 61)
+    ref, _ = orc.pq_fit(X, 2, 16, 5, 61)
+    assert np.array_equal(C, ref)
+    prev, _ = orc.pq_fit(X, 2, 16, 4, 61)
+    codes, _, _ = orc.assign(X, prev)
+    for m in range(2):
+        assert np.array_equal(cnt[m], np.bincount(codes[:, m], minlength=16))
+    upd, _ = orc.update(X, codes, prev)
+    assert np.array_equal(upd, C)
+    # each chunk codeword is the mean of its members: the count-weighted mean of the codewords is
+    # the mean of all rows
+    for m in range(2):
+        wmean = (cnt[m][:, None] * C[m].astype(np.float64)).sum(axis=0) / cnt[m].sum()
+        np.testing.assert_allclose(wmean, X[:, 4 * m:4 * m + 4].astype(np.float64).mean(axis=0), rtol=1e-6, atol=1e-7)
+
+
+def test_pq_fit_weighted_unit_weights_is_the_plain_fit():
+    X = datagen.mixture(3000, 12, 10, "cont", 62)
+    C = orc.pq_fit_weighted(X, np.ones((3000, 3), dtype=np.int64), 3, 16, 6, 63)
+    ref, _ = orc.pq_fit(X, 3, 16, 6, 63)
+    assert np.array_equal(C, ref)
+
+
+def test_pq_fit_weighted_update_is_a_weighted_mean_and_weights_are_multiplicities():
+    rng = np.random.default_rng(64)
+    P = datagen.mixture(600, 8, 6, "cont", 64)
+    W = rng.integers(0, 4, size=(600, 2)).astype(np.int64)
+    W[:, 1] = W[:, 0]  # the same multiplicity in both subspaces
+    C0 = orc.kmeanspp(P, 2, 8, 65)
+    C1 = orc.pq_fit_weighted(P, W, 2, 8, 1, 65)
+    codes, _, _ = orc.assign(P, C0)
+    for m in range(2):
+        for k in range(8):
+            sel = codes[:, m] == k
+            w = W[sel, m].astype(np.float64)
+            if w.sum() == 0:
+                assert np.array_equal(C1[m, k], C0[m, k])
+                continue
+            ref = (w[:, None] * P[sel, 4 * m:4 * m + 4].astype(np.float64)).sum(axis=0) / w.sum()
+            np.testing.assert_allclose(C1[m, k], ref, rtol=2e-7, atol=1e-7)
+    # the same step on the data with every point repeated W times (weight = multiplicity)
+    Pe = np.repeat(P, W[:, 0], axis=0)
+    ce = np.repeat(codes, W[:, 0], axis=0)
+    upd, _ = orc.update(Pe, ce, C0)
+    np.testing.assert_allclose(C1, upd, rtol=2e-7, atol=1e-7)
+
+
+def test_chunked_weighted_decomposes_into_weighted_fits():
+    X = datagen.mixture(8000, 12, 30, "cont", 66)
+    off = np.array([0, 1500, 4000, 8000], dtype=np.int64)
+    M, Ks, iters, seed = 3, 32, 4, 67
+    gC, codes, r, local, W = orc.pq_fit_chunked_weighted(X, off, M, Ks, iters, seed)
+    gu, _, ru, local_u = orc.pq_fit_chunked(X, off, M, Ks, iters, seed)
+    assert np.array_equal(local, local_u)  # the same local fits
+    for c in range(3):
+        Cc, cnt = orc.pq_fit_counts(X[off[c]:off[c + 1]], M, Ks, iters, orc.draw(seed, 0xFFFFFFFE, c))
+        assert np.array_equal(Cc, local[c])
+        assert np.array_equal(W[c * Ks:(c + 1) * Ks], cnt.T)
+        assert W[c * Ks:(c + 1) * Ks].sum(axis=0).tolist() == [off[c + 1] - off[c]] * M
+    pooled = np.concatenate([np.concatenate([local[c, m] for m in range(M)], axis=1) for c in range(3)])
+    want = orc.pq_fit_weighted(pooled, W, M, Ks, iters, seed)
+    assert np.array_equal(gC, want)
+    assert np.array_equal(codes, orc.pq_encode(X, want))
+    assert r == orc.pq_rmse(X, codes, want)
+    print("RMSE weighted", r, "unweighted", ru)
