@@ -255,6 +255,47 @@ int ivf_build(const float *X, const uint8_t *codes, int64_t N, int32_t D, int32_
               uint64_t seed, int32_t prec, ivf_index **out, void *stream);
 
 /*
+ * ivf_build_codes -- a code-space inverted index, Rii's reading of the index
+ * (Sec. 3.1: an IVFPQ-style index that Rii builds from the PQ codes, Sec. 2.2:
+ * the codes are hashed into lists).  The coarse centres are PQ codes:
+ *   codes      [N][M] uint8 PQ codes of the rows (device); no raw rows needed.
+ *   codebooks  [M][Ks][Ds] the codebooks of those codes (copied into the index).
+ *   nlist      1 <= nlist <= min(N, 16384) lists; D = M*Ds <= 256.
+ * Centres start as nlist distinct rows drawn by Floyd's algorithm from the
+ * centre stream (0xFFFFFFFD) of `seed`, then `iters` rounds of k-means over the
+ * codes: each row to its nearest centre by the symmetric distance
+ * SDC(a, b) = sum_m ||c_{m,a_m} - c_{m,b_m}||^2 (ties to the lower list), and
+ * each centre code, subspace by subspace, to the code k minimising the sum over
+ * members of ||c_{m,k} - c_{m,a_m}||^2 (ties to the lower k; a list without
+ * members keeps its centre).  Every decision is exact (FP32/BF16 bound, FP64
+ * re-check in the reference's order).  ivf_search then probes the lists whose
+ * centre codes have the lowest ADC distance to the query (sum over m of the
+ * query's table entries), and scans them as for a raw-space index.  The call
+ * synchronizes once.  Scratch: about N*D*4 bytes.
+ */
+int ivf_build_codes(const uint8_t *codes, const float *codebooks, int64_t N, int32_t D, int32_t M, int32_t Ks,
+                    int32_t nlist, int32_t iters, uint64_t seed, int32_t prec, ivf_index **out, void *stream);
+
+/*
+ * Growing an index without rebuilding it (Sec. 3.1: Rii adds and merges new
+ * codes; the paper builds its index in parallel chunks this way).  Lists keep
+ * ids ascending, so the result equals the lists a single build over all rows
+ * gives with the same coarse quantizer.
+ * ivf_clone_empty -- a new index (caller frees it with ivf_free) with src's
+ *   coarse quantizer (centroids or centre codes and codebooks) and no rows.
+ * ivf_add -- appends n rows, ids N .. N+n-1, to the lists of their nearest
+ *   coarse centre (exact decisions, as in the build).  X [n][D] (16-byte
+ *   aligned) is required for a raw-space index and ignored (may be NULL) for a
+ *   code-space one, which decides from the codes [n][M].  Synchronizes.
+ * ivf_merge -- appends every row of src to dst (ids shifted by dst's row
+ *   count); both must have the same kind, D, M, nlist and bit-identical coarse
+ *   quantizers (PQ_EINVAL otherwise).  src is unchanged.  Synchronizes.
+ */
+int ivf_clone_empty(const ivf_index *src, ivf_index **out);
+int ivf_add(ivf_index *index, const float *X, const uint8_t *codes, int64_t n, int32_t prec, void *stream);
+int ivf_merge(ivf_index *dst, const ivf_index *src, void *stream);
+
+/*
  * ivf_search -- k nearest neighbours by ADC over the probed lists (Sec. 2.2).
  *   codebooks [M][Ks][Ds] (the codebooks the stored codes were made with).
  *   Q         [nq][D] float32 queries.
@@ -271,6 +312,8 @@ int ivf_get_info(const ivf_index *index, int64_t *N, int32_t *D, int32_t *M, int
 int ivf_copy_coarse(const ivf_index *index, float *coarse /* [nlist][D] */, void *stream);
 int ivf_copy_lists(const ivf_index *index, int64_t *offsets /* [nlist+1] */, int64_t *ids /* [N] */,
                    uint8_t *list_codes /* [N][M] */, void *stream);
+/* centre codes [nlist][M] of a code-space index (PQ_EINVAL for a raw-space one) */
+int ivf_copy_centers(const ivf_index *index, uint8_t *centers, void *stream);
 void ivf_free(ivf_index *index);
 
 /* Synchronize `stream` and return (and clear) any recorded device failure. */

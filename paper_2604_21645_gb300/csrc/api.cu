@@ -150,9 +150,13 @@ struct ivf_index {
     int device = 0;
     int64_t N = 0;
     int D = 0, M = 0, nlist = 0;
-    float *coarse = nullptr;       // [nlist][D]
+    int kind = 0;                  // 0: raw-space coarse centroids; 1: centre codes (code-space)
+    int Ks = 0;                    // code-space: codewords per subspace of `cb`
+    float *coarse = nullptr;       // [nlist][D] (code-space: the decoded centre codes)
     float *half_norm = nullptr;    // [nlist]
     float *maxes = nullptr;        // [2]
+    uint8_t *centers = nullptr;    // code-space: [nlist][M] centre codes
+    float *cb = nullptr;           // code-space: [M][Ks][D/M] the codebooks the codes were made with
     int64_t *offsets = nullptr;    // [nlist+1]
     int64_t *ids = nullptr;        // [N]
     uint8_t *codes = nullptr;      // [N][M]
@@ -615,6 +619,69 @@ int ivf_build(const float *X, const uint8_t *codes, int64_t N, int32_t D, int32_
     return PQ_OK;
 }
 
+int ivf_build_codes(const uint8_t *codes, const float *codebooks, int64_t N, int32_t D, int32_t M, int32_t Ks,
+                    int32_t nlist, int32_t iters, uint64_t seed, int32_t prec, ivf_index **out, void *stream)
+{
+    g_msg[0] = 0;
+    if (!out) return fail(PQ_EINVAL, "null output handle");
+    *out = nullptr;
+    if (!codes || !codebooks) return fail(PQ_EINVAL, "null pointer");
+    if (N < 1 || N >= (1LL << 31)) return fail(PQ_EINVAL, "N=%lld must be in [1, 2^31)", (long long)N);
+    PQ_TRY(check_pq_shape(N, D, M, Ks, false));
+    if (nlist < 1 || nlist > N) return fail(PQ_EINVAL, "nlist=%d must be in [1, N]", nlist);
+    if (nlist > 16384) return fail(PQ_ENOTSUP, "nlist=%d exceeds 16384", nlist);
+    if (D > 256) return fail(PQ_ENOTSUP, "ivf_build_codes supports D <= 256");
+    if (iters < 0) return fail(PQ_EINVAL, "iters=%d must be >= 0", iters);
+    PQ_TRY(check_prec(prec));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    PQ_TRY_CUDA(cudaGetDevice(&dev));
+    int *err = device_error_word(dev);
+    if (!err) return fail(PQ_ENOMEM, "device error word");
+    ivf_index *idx = new ivf_index();
+    idx->device = dev;
+    idx->N = N;
+    idx->D = D;
+    idx->M = M;
+    idx->nlist = nlist;
+    idx->kind = 1;
+    idx->Ks = Ks;
+    auto cleanup = [&](int st) {
+        ivf_free(idx);
+        return st;
+    };
+    const size_t cbn = (size_t)M * Ks * (D / M);
+    if (cudaMalloc(&idx->coarse, (size_t)nlist * D * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&idx->half_norm, (size_t)nlist * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&idx->maxes, 2 * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&idx->centers, (size_t)nlist * M) != cudaSuccess ||
+        cudaMalloc(&idx->cb, cbn * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&idx->offsets, (size_t)(nlist + 1) * sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc(&idx->ids, (size_t)N * sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc(&idx->codes, (size_t)N * M) != cudaSuccess)
+        return cleanup(fail(PQ_ENOMEM, "index allocation"));
+    int st = PQ_OK;
+    {
+        Scratch ws(s);
+        if (cudaMemcpyAsync(idx->cb, codebooks, cbn * sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return cleanup(fail(PQ_ECUDA, "codebook copy"));
+        CoarseBound b{idx->half_norm, idx->maxes};
+        st = run_ivf_build_codes(codes, idx->cb, N, D, M, Ks, nlist, iters, seed, prec, idx->coarse, b, idx->centers,
+                                 idx->offsets, idx->ids, idx->codes, ws, s);
+        if (!st) st = ws.status;
+    }
+    if (st) return cleanup(st);
+    int herr = 0;
+    st = status_from_device(err, s, &herr);
+    if (st) return cleanup(st);
+    if (herr) {
+        cudaMemsetAsync(err, 0, sizeof(int), s);
+        return cleanup(fail(herr, "device-side failure %d during ivf_build_codes", herr));
+    }
+    *out = idx;
+    return PQ_OK;
+}
+
 int ivf_search(const ivf_index *index, const float *codebooks, int32_t Ks, const float *Q, int64_t nq,
                int32_t nprobe, int32_t k, int64_t *ids, float *dists, void *stream)
 {
@@ -639,6 +706,7 @@ int ivf_search(const ivf_index *index, const float *codebooks, int32_t Ks, const
     a.nprobe = nprobe;
     a.k = k;
     a.coarse = index->coarse;
+    a.probe_sub = index->kind == 1 ? index->D / index->M : 0;
     a.cb = &b;
     a.offsets = index->offsets;
     a.ids = index->ids;
@@ -668,6 +736,146 @@ int ivf_copy_coarse(const ivf_index *index, float *coarse, void *stream)
     return PQ_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Replaces the lists of `dst` by the merge of its lists and the CSR set (b_off, b_ids, b_codes)
+// of b_n rows, whose ids are shifted by dst->N.  Synchronizes the stream before freeing the old
+// arrays.
+int merge_into(ivf_index *dst, const int64_t *b_off, const int64_t *b_ids, const uint8_t *b_codes, int64_t b_n,
+               cudaStream_t s)
+{
+    const int64_t total = dst->N + b_n;
+    if (total >= (1LL << 31)) return fail(PQ_ENOTSUP, "an index holds fewer than 2^31 rows");
+    int64_t *off = nullptr, *ids = nullptr;
+    uint8_t *codes = nullptr;
+    if (cudaMalloc(&off, (size_t)(dst->nlist + 1) * sizeof(int64_t)) != cudaSuccess ||
+        (total > 0 && cudaMalloc(&ids, (size_t)total * sizeof(int64_t)) != cudaSuccess) ||
+        (total > 0 && cudaMalloc(&codes, (size_t)total * dst->M) != cudaSuccess)) {
+        cudaFree(off);
+        cudaFree(ids);
+        return fail(PQ_ENOMEM, "merged list allocation");
+    }
+    const int st = launch_merge_lists(dst->offsets, dst->ids, dst->codes, dst->N, b_off, b_ids, b_codes, b_n, dst->N,
+                                      dst->nlist, dst->M, off, ids, codes, s);
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (st != PQ_OK || e != cudaSuccess) {
+        cudaFree(off);
+        cudaFree(ids);
+        cudaFree(codes);
+        return st != PQ_OK ? st : cuda_check(e, "merge");
+    }
+    cudaFree(dst->offsets);
+    cudaFree(dst->ids);
+    cudaFree(dst->codes);
+    dst->offsets = off;
+    dst->ids = ids;
+    dst->codes = codes;
+    dst->N = total;
+    return PQ_OK;
+}
+
+int copy_device(void **dst, const void *src, size_t bytes)
+{
+    if (!src) return PQ_OK;
+    if (cudaMalloc(dst, bytes) != cudaSuccess) return fail(PQ_ENOMEM, "index allocation");
+    PQ_TRY_CUDA(cudaMemcpy(*dst, src, bytes, cudaMemcpyDeviceToDevice));
+    return PQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ivf_clone_empty(const ivf_index *src, ivf_index **out)
+{
+    g_msg[0] = 0;
+    if (!src || !out) return fail(PQ_EINVAL, "null pointer");
+    *out = nullptr;
+    ivf_index *idx = new ivf_index();
+    idx->device = src->device;
+    idx->N = 0;
+    idx->D = src->D;
+    idx->M = src->M;
+    idx->nlist = src->nlist;
+    idx->kind = src->kind;
+    idx->Ks = src->Ks;
+    const size_t cbn = (size_t)src->M * src->Ks * (src->D / src->M);
+    int st = copy_device((void **)&idx->coarse, src->coarse, (size_t)src->nlist * src->D * sizeof(float));
+    if (!st) st = copy_device((void **)&idx->half_norm, src->half_norm, (size_t)src->nlist * sizeof(float));
+    if (!st) st = copy_device((void **)&idx->maxes, src->maxes, 2 * sizeof(float));
+    if (!st && src->kind == 1) st = copy_device((void **)&idx->centers, src->centers, (size_t)src->nlist * src->M);
+    if (!st && src->kind == 1) st = copy_device((void **)&idx->cb, src->cb, cbn * sizeof(float));
+    if (!st && cudaMalloc(&idx->offsets, (size_t)(src->nlist + 1) * sizeof(int64_t)) != cudaSuccess)
+        st = fail(PQ_ENOMEM, "index allocation");
+    if (!st && cudaMemset(idx->offsets, 0, (size_t)(src->nlist + 1) * sizeof(int64_t)) != cudaSuccess)
+        st = fail(PQ_ECUDA, "cudaMemset");
+    if (st) {
+        ivf_free(idx);
+        return st;
+    }
+    *out = idx;
+    return PQ_OK;
+}
+
+int ivf_add(ivf_index *index, const float *X, const uint8_t *codes, int64_t n, int32_t prec, void *stream)
+{
+    g_msg[0] = 0;
+    if (!index || !codes) return fail(PQ_EINVAL, "null pointer");
+    if (n < 0) return fail(PQ_EINVAL, "n must be >= 0");
+    PQ_TRY(check_prec(prec));
+    if (index->kind == 0 && (!X || !aligned16(X))) return fail(PQ_EINVAL, "X (16-byte aligned) is required");
+    if (n == 0) return PQ_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int D = index->D, M = index->M, nlist = index->nlist;
+    Scratch ws(s);
+    int32_t *lst = ws.get<int32_t>((size_t)n);
+    int64_t *b_off = ws.get<int64_t>((size_t)nlist + 1);
+    int64_t *b_ids = ws.get<int64_t>((size_t)n);
+    uint8_t *b_codes = ws.get<uint8_t>((size_t)n * M);
+    if (ws.status) return ws.status;
+    CoarseBound b{index->half_norm, index->maxes};
+    if (index->kind == 0) {
+        PQ_TRY(coarse_assign(X, n, D, index->coarse, nlist, b, lst, ws, prec, s));
+    } else {
+        float *Xhat = ws.get<float>((size_t)n * D);
+        if (ws.status) return ws.status;
+        PQ_TRY(launch_decode_codes(codes, index->cb, n, D, M, index->Ks, Xhat, s));
+        PQ_TRY(coarse_assign(Xhat, n, D, index->coarse, nlist, b, lst, ws, prec, s, D / M));
+    }
+    PQ_TRY(bucket_rows(lst, n, nlist, codes, M, b_off, b_ids, b_codes, ws, s));
+    PQ_TRY(merge_into(index, b_off, b_ids, b_codes, n, s));
+    return ws.status;
+}
+
+int ivf_merge(ivf_index *dst, const ivf_index *src, void *stream)
+{
+    g_msg[0] = 0;
+    if (!dst || !src) return fail(PQ_EINVAL, "null pointer");
+    if (dst == src) return fail(PQ_EINVAL, "an index cannot be merged into itself");
+    if (dst->kind != src->kind || dst->D != src->D || dst->M != src->M || dst->nlist != src->nlist ||
+        dst->Ks != src->Ks)
+        return fail(PQ_EINVAL, "the indexes differ in kind, D, M, nlist or Ks");
+    // the two must share their coarse quantizer bit for bit
+    std::vector<float> ca((size_t)dst->nlist * dst->D), cb2((size_t)src->nlist * src->D);
+    PQ_TRY_CUDA(cudaMemcpy(ca.data(), dst->coarse, ca.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    PQ_TRY_CUDA(cudaMemcpy(cb2.data(), src->coarse, cb2.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    if (memcmp(ca.data(), cb2.data(), ca.size() * sizeof(float)) != 0)
+        return fail(PQ_EINVAL, "the indexes have different coarse quantizers");
+    if (src->N == 0) return PQ_OK;
+    return merge_into(dst, src->offsets, src->ids, src->codes, src->N, static_cast<cudaStream_t>(stream));
+}
+
+int ivf_copy_centers(const ivf_index *index, uint8_t *centers, void *stream)
+{
+    if (!index || !centers) return fail(PQ_EINVAL, "null pointer");
+    if (index->kind != 1) return fail(PQ_EINVAL, "the index has raw-space coarse centroids, not centre codes");
+    PQ_TRY_CUDA(cudaMemcpyAsync(centers, index->centers, (size_t)index->nlist * index->M, cudaMemcpyDeviceToDevice,
+                                static_cast<cudaStream_t>(stream)));
+    return PQ_OK;
+}
+
 int ivf_copy_lists(const ivf_index *index, int64_t *offsets, int64_t *ids, uint8_t *list_codes, void *stream)
 {
     if (!index) return fail(PQ_EINVAL, "null index");
@@ -689,6 +897,8 @@ void ivf_free(ivf_index *index)
     cudaFree(index->coarse);
     cudaFree(index->half_norm);
     cudaFree(index->maxes);
+    cudaFree(index->centers);
+    cudaFree(index->cb);
     cudaFree(index->offsets);
     cudaFree(index->ids);
     cudaFree(index->codes);

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256) coarse_scores_kernel(const float *__restr
 __global__ void coarse_recheck_kernel(const float *__restrict__ X, int D, const float *__restrict__ C, int nlist,
                                       const float *__restrict__ half_norm, const float *__restrict__ maxes,
                                       const int64_t *__restrict__ queue, const unsigned long long *queue_len,
-                                      int32_t *__restrict__ list_of_row)
+                                      int32_t *__restrict__ list_of_row, int sub)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -207,7 +207,7 @@ __global__ void coarse_recheck_kernel(const float *__restrict__ X, int D, const 
             float acc = 0.0f;
             for (int j = 0; j < D; ++j) acc = fmaf(x[j], C[(size_t)l * D + j], acc);
             if (half_norm[l] - acc <= lmin + win) {
-                const double d = d2_fp64(x, C + (size_t)l * D, D);
+                const double d = d2_fp64_sub(x, C + (size_t)l * D, D, sub);
                 if (d < best) { best = d; bl = l; }
             }
         }
@@ -254,7 +254,8 @@ __device__ __forceinline__ float d2_f32(const float *__restrict__ x, const float
 __global__ void coarse_recheck_masked_kernel(const float *__restrict__ X, int D, const float *__restrict__ C,
                                              int nlist, const int64_t *__restrict__ queue,
                                              const uint32_t *__restrict__ qmask,
-                                             const unsigned long long *queue_len, int32_t *__restrict__ list_of_row)
+                                             const unsigned long long *queue_len, int32_t *__restrict__ list_of_row,
+                                             int sub)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -299,7 +300,7 @@ __global__ void coarse_recheck_masked_kernel(const float *__restrict__ X, int D,
                 const float *cl = C + (size_t)l * D;
                 const float d = d2_f32(x, cl, D);
                 if (d <= d1 + margin) {
-                    const double e = d2_fp64(x, cl, D);
+                    const double e = d2_fp64_sub(x, cl, D, sub);
                     if (e < best || (e == best && l < bl)) { best = e; bl = l; }
                 }
             }
@@ -620,7 +621,7 @@ int launch_coarse_norms(const float *C, int nlist, int D, CoarseBound &b, cudaSt
 }
 
 int coarse_assign(const float *X, int64_t N, int D, const float *C, int nlist, const CoarseBound &b,
-                  int32_t *list_of_row, Scratch &ws, int prec, cudaStream_t s)
+                  int32_t *list_of_row, Scratch &ws, int prec, cudaStream_t s, int sub)
 {
     int64_t *queue = ws.get<int64_t>((size_t)N);
     unsigned long long *qlen = ws.get<unsigned long long>(1, true);
@@ -630,7 +631,7 @@ int coarse_assign(const float *X, int64_t N, int D, const float *C, int nlist, c
         if (ws.status) return ws.status;
         PQ_TRY(launch_coarse_tc(X, N, D, C, nlist, list_of_row, queue, qmask, qlen, ws, s));
         ProfScope ps("coarse_recheck", s);
-        coarse_recheck_masked_kernel<<<152 * 4, 256, 0, s>>>(X, D, C, nlist, queue, qmask, qlen, list_of_row);
+        coarse_recheck_masked_kernel<<<152 * 4, 256, 0, s>>>(X, D, C, nlist, queue, qmask, qlen, list_of_row, sub);
         count_launch();
         PQ_TRY_CUDA(cudaGetLastError());
         return PQ_OK;
@@ -643,7 +644,7 @@ int coarse_assign(const float *X, int64_t N, int D, const float *C, int nlist, c
     {
         ProfScope ps("coarse_recheck", s);
         coarse_recheck_kernel<<<152 * 4, 256, 0, s>>>(X, D, C, nlist, b.half_norm, b.maxes, queue, qlen,
-                                                      list_of_row);
+                                                      list_of_row, sub);
     }
     count_launch(2);
     PQ_TRY_CUDA(cudaGetLastError());

@@ -91,6 +91,17 @@ __device__ __forceinline__ double d2_fp64(const float *x, const float *c, int ds
     return acc;
 }
 
+// FP64 squared distance as a sum of subspace terms: each run of `ds` consecutive dimensions
+// summed in dimension order from zero, the terms then added in subspace order -- the way a PQ
+// distance table (one FP64 entry per subspace) adds up.  ds <= 0 means one run over all D.
+__device__ __forceinline__ double d2_fp64_sub(const float *x, const float *c, int D, int ds)
+{
+    if (ds <= 0 || ds >= D) return d2_fp64(x, c, D);
+    double acc = 0.0;
+    for (int m0 = 0; m0 < D; m0 += ds) acc = __dadd_rn(acc, d2_fp64(x + m0, c + m0, ds));
+    return acc;
+}
+
 // Error-free addition: s + e == a + b exactly (Knuth's TwoSum).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {

@@ -111,9 +111,12 @@ struct CoarseBound {
     float *maxes = nullptr;        // [2]: max half norm, max norm
 };
 int launch_coarse_norms(const float *C, int nlist, int D, CoarseBound &b, cudaStream_t s);
-// Nearest coarse centroid of every row (exact: FP32 bound + FP64 re-check).
+// Nearest coarse centroid of every row (exact: FP32 bound + FP64 re-check).  The FP64
+// re-check sums the squared differences in one run over the D dimensions (sub = 0), or as
+// per-subspace terms of width `sub` added in subspace order (the symmetric PQ distance of
+// two decoded codes, d2_fp64_sub).
 int coarse_assign(const float *X, int64_t N, int D, const float *C, int nlist, const CoarseBound &b,
-                  int32_t *list_of_row, Scratch &ws, int prec, cudaStream_t s);
+                  int32_t *list_of_row, Scratch &ws, int prec, cudaStream_t s, int sub = 0);
 // tensor-core scores (coarse_tc.cu): certified rows written, the rest queued for the FP64 re-check
 bool coarse_tc_supported(int D, int nlist);
 int launch_coarse_tc(const float *X, int64_t N, int D, const float *C, int nlist, int32_t *list_of_row,
@@ -129,6 +132,23 @@ int launch_x_exponent_range(const float *X, int64_t N, int D, unsigned *xrange, 
 int launch_list_mean(const float *X, int D, const int64_t *offsets, const int64_t *ids, int nlist,
                      const unsigned *xrange, float *C, cudaStream_t s);
 
+// ---- code-space coarse quantizer (codes_ivf.cu) ----------------------------
+// Centre codes [nlist][M] by k-means over the PQ codes (symmetric distance), the decoded
+// centres in `coarse` [nlist][D] with their bounds in b, and the CSR lists of all rows.
+int run_ivf_build_codes(const uint8_t *codes, const float *C, int64_t N, int D, int M, int Ks, int nlist, int iters,
+                        uint64_t seed, int prec, float *coarse, CoarseBound &b, uint8_t *centers,
+                        int64_t *offsets, int64_t *ids, uint8_t *list_codes, Scratch &ws, cudaStream_t s);
+// Xhat [N][D] = the codewords the codes select
+int launch_decode_codes(const uint8_t *codes, const float *C, int64_t N, int D, int M, int Ks, float *Xhat,
+                        cudaStream_t s);
+
+// ---- growing an index (ivf_merge.cu) ---------------------------------------
+// Merged CSR lists: list l = list l of set a, then list l of set b with ids + b_shift.
+int launch_merge_lists(const int64_t *a_off, const int64_t *a_ids, const uint8_t *a_codes, int64_t a_n,
+                       const int64_t *b_off, const int64_t *b_ids, const uint8_t *b_codes, int64_t b_n,
+                       int64_t b_shift, int nlist, int M, int64_t *out_off, int64_t *out_ids, uint8_t *out_codes,
+                       cudaStream_t s);
+
 // ---- chunked divide and conquer (chunked.cu) -------------------------------
 int run_pq_fit_chunked(const float *X, const int64_t *off, int n_chunks, int D, int M, int Ks, int iters,
                        uint64_t seed, int prec, float *global_cb, uint8_t *codes, double *rmse, cudaStream_t s);
@@ -140,6 +160,7 @@ struct SearchArgs {
     int D = 0, M = 0, Ks = 0, nlist = 0, nprobe = 0, k = 0;
     const float *coarse = nullptr;
     const CoarseBound *cb = nullptr;
+    int probe_sub = 0;             // FP64 probe re-rank: 0 = one run over D, else per-subspace terms
     const int64_t *offsets = nullptr;
     const int64_t *ids = nullptr;
     const uint8_t *list_codes = nullptr;

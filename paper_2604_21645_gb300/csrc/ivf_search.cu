@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kThreads) probe_select_kernel(const float *__r
                                                                 int D, int nlist, int nlist_p2, int nprobe,
                                                                 const float *__restrict__ coarse,
                                                                 const float *__restrict__ maxes,
-                                                                int32_t *__restrict__ probes)
+                                                                int32_t *__restrict__ probes, int sub)
 {
     extern __shared__ Cand s_c[];  // [nlist_p2]
     __shared__ float s_xx[kThreads / 32];
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kThreads) probe_select_kernel(const float *__r
         for (int i = lo + threadIdx.x; i < hi; i += kThreads) {
             const int l = s_c[i].id;
             s_c[i].d = __int_as_float(i);  // placeholder, overwritten below
-            const double d = d2_fp64(qv, coarse + (size_t)l * D, D);
+            const double d = d2_fp64_sub(qv, coarse + (size_t)l * D, D, sub);
             reinterpret_cast<double *>(s_c + nlist_p2)[i - lo] = d;
         }
         __syncthreads();
@@ -354,7 +354,7 @@ int run_search(const SearchArgs &a, Scratch &ws, cudaStream_t s)
     {
     ProfScope ps("probe_select", s);
     probe_select_kernel<<<(unsigned)a.nq, kThreads, smem, s>>>(S, a.Q, a.D, a.nlist, p2, a.nprobe, a.coarse,
-                                                              a.cb->maxes, probes);
+                                                              a.cb->maxes, probes, a.probe_sub);
     }
     count_launch();
     PQ_TRY_CUDA(cudaGetLastError());

@@ -17,38 +17,32 @@
 // absolute sum (the largest error measured on this GPU is 2.6e-7 of it), and
 // C1 = 7.5e-5, C2 = 2.7e-5 keep a 1.5x margin over the sum of those terms.
 //
-// Decision.  Two epilogue threads share a (row, subspace): thread h reads the
-// 128 scores of codeword half h from tensor memory in chunks of 16 (each load
-// also returns the chunk's maximum, tcgen05.ld.red) and keeps the chunk maxima
-// and the values of its best chunk.  Half 1 hands its maxima to half 0, which
-// takes the overall best chunk and accepts its argmax when no other score lies
-// within twice the error bound of it.  For the other rows (about 0.2% on
-// clustered data) every codeword that may be the nearest -- the best chunk's
-// scores within the bound, and all codewords of any other chunk whose maximum
-// reaches it -- is re-ranked exactly: FP32 direct differences, then FP64 among
-// the FP32 near-ties, the decision rule of the CPU reference.  Codes are exact.
+// Decision.  The epilogue reads each row's 256 scores from TMEM in chunks of
+// 32 (each load also returns the chunk's maximum, tcgen05.ld.red), keeps the
+// eight chunk maxima and the values of the best chunk, and accepts the argmax
+// when no other score lies within twice the error bound of it.  For the other rows (about 0.2% on clustered data) every codeword that
+// may be the nearest -- the saved chunk's scores within the bound, and all
+// codewords of any other chunk whose maximum reaches it -- is re-ranked exactly
+// from the FP32 codebook copy in shared memory: FP32 direct differences, then
+// FP64 among the FP32 near-ties, the decision rule of the CPU reference.
+// Codes are exact.
 //
-// Update.  Half 1 adds the residuals x - c_code of the tile before, with
-// shared-memory int32 atomics, in the exact fixed-point format of common.cuh
-// (FixFmt), into per-CTA sums that each CTA writes as int64; the finalise
-// kernel adds the CTAs in int64 and moves every codeword by the float-float
-// mean residual of its members.
+// Update.  Residuals x - c_code are added with shared-memory int32 atomics, in
+// the exact fixed-point format of common.cuh (FixFmt), into per-CTA sums that
+// each CTA writes as int64; the finalise kernel adds the CTAs in int64 and moves
+// every codeword by the float-float mean residual of its members.
 //
 // Pipeline (one CTA per SM, a group of 2 subspaces, persistent over row tiles
 // of 128).  Warp 0 issues TMA loads of 128 x 16 float tiles (64B swizzle) into
-// four stages.  Warps 3-4 (the operand warps) turn each tile into the bf16 A
-// operands of both subspaces and the error bound of every (row, subspace).
-// Warps 1 and 2 issue the MMAs of subspace 0 and 1.  Warps 5-20 are four
-// epilogue warpgroups, one per (subspace, codeword half) and its 128-column
-// TMEM accumulator (thread = row = TMEM lane): the MMA of a half is issued as
-// soon as its warpgroup has read the same half of the previous tile.  The two
-// warpgroups of a subspace meet once per tile at a named barrier: half 0 then
-// decides the tile's codes while half 1 updates the sums of the tile before,
-// whose row stage it releases to the TMA warp.  All other hand-offs are
-// mbarriers; every mbarrier wait is bounded, and after a timed-out wait
-// (PQ_ETIMEOUT recorded) a thread skips the remaining work but still takes
-// every named barrier, so the CTA unwinds (its copies and MMAs waited for, its
-// tensor memory freed).
+// five stages.  Warp 3 (the operand warp) turns each tile into the bf16 A
+// operands of both subspaces (two A stages, so the loads run three tiles ahead).  Warps 1 and 2 issue the MMAs of
+// subspace 0 and 1.  Warps 4-7 and 8-11 (the epilogue
+// warpgroups; thread = row = TMEM lane) own subspace 0 and 1 and two 128-column
+// TMEM buffers each, one per codeword half: the MMA of a half is issued as soon
+// as the epilogue has read the same half of the previous tile, so the tensor
+// core works while the epilogue runs.  All hand-offs are mbarriers; every wait
+// is bounded, and a timed-out wait records PQ_ETIMEOUT and lets the CTA unwind
+// (its copies and MMAs waited for, its tensor memory freed).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -66,55 +60,50 @@ namespace {
 constexpr int G = 2;        // subspaces per CTA
 constexpr int TM = 128;     // rows per tile
 constexpr int KSMAX = 256;  // codewords
-constexpr int NH = 128;     // codewords per MMA (one TMEM buffer, one epilogue warpgroup)
+constexpr int NH = 128;     // codewords per MMA (one TMEM buffer)
 constexpr int DS = 8;       // subspace width
-constexpr int CW = 16;      // codewords per TMEM load (chunk)
-constexpr int NCH = NH / CW;  // chunks per half
-constexpr int NXS = 4;      // X stages
+constexpr int NXS = 5;      // X stages
 constexpr int NAS = 2;      // A stages
-constexpr int kOpWarps = 2;                          // operand warps
-constexpr int kOpRows = TM / (32 * kOpWarps);        // rows per operand thread
-constexpr int kOp0 = 96;                             // first operand thread (after TMA and two MMA warps)
-constexpr int kEpi0 = kOp0 + 32 * kOpWarps;          // first epilogue thread
-constexpr int kThreads = kEpi0 + 4 * 128;            // four epilogue warpgroups
+// Warps per block must keep ceil(warps / 4) * 32 * registers within one SM sub-partition's
+// 16K registers: 12 warps leave room for the epilogue's double-buffered TMEM loads.
+constexpr int kOpWarps = 1;                         // operand warps
+constexpr int kOpRows = TM / (32 * kOpWarps);       // rows per operand thread
+constexpr int kThreads = 96 + 32 * kOpWarps + 256;  // TMA warp, two MMA warps, operand warps, two epilogue warpgroups
+constexpr int kOp0 = 96;                            // first operand thread
+constexpr int kEpi0 = kOp0 + 32 * kOpWarps;         // first epilogue thread
 
 constexpr int XS_BYTES = TM * G * DS * 4;  // 8 KB per stage (rows of 64 B)
 constexpr int A_K16 = TM * 16 * 2;         // 4 KB: 128 rows x K=16 bf16
 constexpr int A_SUB = 2 * A_K16;           // K = 32
 constexpr int B_K16 = KSMAX * 16 * 2;      // 8 KB: 256 codewords x K=16
 constexpr int B_SUB = 2 * B_K16;
+constexpr int CB_STRIDE = 12;  // FP32 codeword rows: 16-byte aligned, spread over bank groups
 constexpr int ACC_STRIDE = 9;  // update sums: conflict-free scalar atomics
-constexpr int SLOT_BYTES = CW * 4;  // one saved chunk: 16 FP32 scores
-constexpr int XCH_BYTES = 32;       // half 1 -> half 0: {best, second chunk max, chunk, -} + 8 bf16 maxima
 constexpr int OFF_XS = 0;
 constexpr int OFF_A = OFF_XS + NXS * XS_BYTES;  // [stage][g]
 constexpr int OFF_B = OFF_A + NAS * G * A_SUB;  // [g]
+constexpr int OFF_CBF = OFF_B + G * B_SUB;
 constexpr int ACC_BYTES = G * KSMAX * ACC_STRIDE * 4;
-constexpr int OFF_ACC = OFF_B + G * B_SUB;             // int32 [2][G][KSMAX][ACC_STRIDE]: high, low
-constexpr int OFF_CNT = OFF_ACC + 2 * ACC_BYTES;
-constexpr int OFF_SLOT0 = OFF_CNT + G * KSMAX * 4;      // [G][TM] half 0's saved chunk
-constexpr int OFF_SLOT1 = OFF_SLOT0 + G * TM * SLOT_BYTES;  // [2][G][TM] half 1's, by tile parity
-constexpr int OFF_XCH = OFF_SLOT1 + 2 * G * TM * SLOT_BYTES;  // [2][G][TM]
-constexpr int OFF_CODE = OFF_XCH + 2 * G * TM * XCH_BYTES;    // [2][G][TM] int: decided codes
-constexpr int OFF_WIN = OFF_CODE + 2 * G * TM * 4;            // [NXS][G][TM] float: error window
-constexpr int OFF_MISC = OFF_WIN + NXS * G * TM * 4;
+constexpr int OFF_ACC = OFF_CBF + G * KSMAX * CB_STRIDE * 4;  // int32 [3][G][KSMAX][ACC_STRIDE]: high, low, float
+constexpr int OFF_CNT = OFF_ACC + 3 * ACC_BYTES;
+constexpr int OFF_SV = OFF_CNT + G * KSMAX * 4;        // [256 epilogue threads][32] best-chunk scores
+constexpr int OFF_MISC = OFF_SV + 256 * 32 * 4;
 constexpr int MISC_BYTES = 512;
 constexpr int SMEM_BYTES = OFF_MISC + MISC_BYTES + 1024;  // + alignment slack
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory of the tensor-core pass exceeds one CTA's limit");
 
 // mbarrier slots in the misc area
-constexpr int MB_FULL = 0;                       // [NXS]  TMA -> operand warps (and epilogue readers)
-constexpr int MB_EMPTY = MB_FULL + NXS;          // [NXS]  half-1 warps (update done) -> TMA
-constexpr int MB_WREADY = MB_EMPTY + NXS;        // [NXS]  operand warps (error windows written) -> half 0
-constexpr int MB_AREADY = MB_WREADY + NXS;       // [NAS][G] operand warps -> MMA warp g
-constexpr int MB_AFREE = MB_AREADY + NAS * G;    // [NAS][G] MMA completion -> operand warps
-constexpr int MB_MMAF = MB_AFREE + NAS * G;      // [G][2]  MMA completion of a half -> its epilogue warpgroup
-constexpr int MB_TFREE = MB_MMAF + G * 2;        // [G][2]  epilogue warpgroup (4 warps) -> MMA warp g
+constexpr int MB_FULL = 0;                       // [NXS]  TMA -> operand + epilogue warps
+constexpr int MB_EMPTY = MB_FULL + NXS;          // [NXS]  operand + epilogue warps -> TMA
+constexpr int MB_AREADY = MB_EMPTY + NXS;        // [NAS][G] operand warp -> MMA warp g
+constexpr int MB_AFREE = MB_AREADY + NAS * G;    // [NAS][G] MMA completion -> operand warp
+constexpr int MB_MMAF = MB_AFREE + NAS * G;      // [G][2]  MMA completion of a half -> epilogue warpgroup g
+constexpr int MB_TFREE = MB_MMAF + G * 2;        // [G][2]  epilogue warpgroup g (4 warps) -> MMA warp g
 constexpr int MB_DRAIN = MB_TFREE + G * 2;       // [G]     final commit of MMA warp g
 constexpr int MB_COUNT = MB_DRAIN + G;
 constexpr int MISC_TSLOT = 8 * MB_COUNT;
-constexpr int MISC_MU = 256;                     // [G][8] floats
-constexpr int MISC_BND = 320;                    // [G][4] float bits
+constexpr int MISC_MU = 320;                     // [G][8] floats
+constexpr int MISC_BND = 384;                    // [G][4] float bits
 static_assert(MISC_TSLOT + 4 <= MISC_MU, "mbarriers overlap the misc data");
 
 constexpr float kC1 = 7.5e-5f;
@@ -160,8 +149,7 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity)
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the phase with the given parity; false (PQ_ETIMEOUT recorded) if it ran out
-// or another thread already recorded a failure.
+// Bounded wait for the phase with the given parity; false (PQ_ETIMEOUT recorded) if it ran out.
 __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int *err)
 {
     for (unsigned it = 0;; ++it) {
@@ -186,8 +174,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-// named barrier of the two epilogue warpgroups of subspace g (256 threads)
-__device__ __forceinline__ void pair_sync(int g) { asm volatile("bar.sync %0, 256;" ::"r"(1 + g) : "memory"); }
 
 // no-swizzle K-major shared-memory matrix descriptor: core matrices of 8 rows x 16 B,
 // LBO = distance between the two K core matrices, SBO = distance between 8-row groups
@@ -218,23 +204,46 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
 
-// 16 consecutive columns of this thread's TMEM lane and their maximum (tcgen05.ld.red), so a
-// chunk's maximum needs no instructions of its own.
-#define TC_LDMAX16(base, v, m)                                                                                     \
-    asm volatile("tcgen05.ld.red.sync.aligned.32x32b.x16.max.f32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13," \
-                 "%14,%15}, %16, [%17];"                                                                           \
-                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]),  \
-                   "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]),        \
-                   "=f"(v[15]), "=f"(m)                                                                            \
+#define TC_LD32(base, v)                                                                                            \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16," \
+                 "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                             \
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]),   \
+                   "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]),         \
+                   "=f"(v[15]), "=f"(v[16]), "=f"(v[17]), "=f"(v[18]), "=f"(v[19]), "=f"(v[20]), "=f"(v[21]),       \
+                   "=f"(v[22]), "=f"(v[23]), "=f"(v[24]), "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]),       \
+                   "=f"(v[29]), "=f"(v[30]), "=f"(v[31])                                                            \
                  : "r"(base))
 // tcgen05.ld writes its registers asynchronously: the wait names them as in/out operands so that
 // the compiler cannot move a use of the loaded values above it.
-#define TC_WAITMAX16(v, m)                                                                                       \
-    asm volatile("tcgen05.wait::ld.sync.aligned;"                                                                \
-                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]), \
-                   "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]),        \
-                   "+f"(v[15]), "+f"(m)                                                                           \
-                 :                                                                                               \
+#define TC_WAIT32(v)                                                                                              \
+    asm volatile("tcgen05.wait::ld.sync.aligned;"                                                                 \
+                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]),  \
+                   "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]),         \
+                   "+f"(v[15]), "+f"(v[16]), "+f"(v[17]), "+f"(v[18]), "+f"(v[19]), "+f"(v[20]), "+f"(v[21]),       \
+                   "+f"(v[22]), "+f"(v[23]), "+f"(v[24]), "+f"(v[25]), "+f"(v[26]), "+f"(v[27]), "+f"(v[28]),       \
+                   "+f"(v[29]), "+f"(v[30]), "+f"(v[31])                                                            \
+                 :                                                                                                \
+                 : "memory")
+
+// The same load with a max reduction: m receives the largest of the 32 values this thread loads
+// (one row's 32 consecutive columns), so a chunk's maximum needs no instructions of its own.
+#define TC_LDMAX32(base, v, m)                                                                                      \
+    asm volatile("tcgen05.ld.red.sync.aligned.32x32b.x32.max.f32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"  \
+                 "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, %32, [%33];"             \
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]),   \
+                   "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]),         \
+                   "=f"(v[15]), "=f"(v[16]), "=f"(v[17]), "=f"(v[18]), "=f"(v[19]), "=f"(v[20]), "=f"(v[21]),       \
+                   "=f"(v[22]), "=f"(v[23]), "=f"(v[24]), "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]),       \
+                   "=f"(v[29]), "=f"(v[30]), "=f"(v[31]), "=f"(m)                                                   \
+                 : "r"(base))
+#define TC_WAITMAX32(v, m)                                                                                        \
+    asm volatile("tcgen05.wait::ld.sync.aligned;"                                                                 \
+                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]),  \
+                   "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]),         \
+                   "+f"(v[15]), "+f"(v[16]), "+f"(v[17]), "+f"(v[18]), "+f"(v[19]), "+f"(v[20]), "+f"(v[21]),       \
+                   "+f"(v[22]), "+f"(v[23]), "+f"(v[24]), "+f"(v[25]), "+f"(v[26]), "+f"(v[27]), "+f"(v[28]),       \
+                   "+f"(v[29]), "+f"(v[30]), "+f"(v[31]), "+f"(m)                                                   \
+                 :                                                                                                \
                  : "memory")
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
@@ -249,24 +258,13 @@ __device__ __forceinline__ const float4 *xs_chunk(const float *stage, int r, int
     return reinterpret_cast<const float4 *>(stage + r * 16 + ((c ^ ((r >> 1) & 3)) << 2));
 }
 
-// 16-byte piece c (0..3) of the saved chunk of row r: pieces swizzled so that the 8 lanes of a
-// quarter-warp access spread over all 32 banks
-__device__ __forceinline__ float4 *slot_piece(unsigned char *slots, int r, int c)
+// FP32 squared distance of one subspace row to a codeword, direct differences in dimension order.
+__device__ __forceinline__ float d2_fp32(const float *x, const float *c)
 {
-    return reinterpret_cast<float4 *>(slots + r * SLOT_BYTES + ((c ^ ((r >> 1) & 3)) << 4));
-}
-
-// FP32 squared distance of one subspace row to a codeword (global memory), direct differences in
-// dimension order.
-__device__ __forceinline__ float d2_fp32(const float (&x)[DS], const float *c)
-{
-    const float4 c0 = __ldg(reinterpret_cast<const float4 *>(c));
-    const float4 c1 = __ldg(reinterpret_cast<const float4 *>(c + 4));
-    const float cv[DS] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
     float d = 0.0f;
 #pragma unroll
     for (int j = 0; j < DS; ++j) {
-        const float t = x[j] - cv[j];
+        const float t = x[j] - c[j];
         d = fmaf(t, t, d);
     }
     return d;
@@ -284,48 +282,36 @@ __device__ __forceinline__ void top2_merge(float &d1, int &k1, float &d2, float 
     }
 }
 
-// Exact decision for the uncertain rows of a warp, warp-cooperatively.  The warp takes the
-// uncertain lanes one at a time.  A row's candidates are the codewords of its best chunk `bc`
-// whose scores reach the bound (bits of svmask) and all codewords of the chunks in cmask (16
-// chunks of 16 codewords); each pass scores two chunks, one per half-warp, by FP32 direct
-// differences (relative error below 1e-6 for Ds = 8), and a warp reduction gives the best and
+// Exact decision for the uncertain rows of a warp, warp-cooperatively.  The warp takes
+// the uncertain lanes one at a time; each lane scores one candidate codeword of that row
+// per pass -- the codewords of the saved chunk `bestj` whose scores reach the bound (bits
+// of svmask), then all codewords of the chunks in cmask -- by FP32 direct differences
+// (relative error below 1e-6 for Ds = 8), and a warp reduction gives the best and
 // second-best distances (ties to the lower index).  Unless the FP32 gap settles it, the
 // candidates within the FP32 margin are compared in FP64 (ties to the lower index) -- the
 // decision rule of the CPU reference.  Every lane of the warp must call this.
-__device__ __noinline__ void decide_exact_warp(bool unsure, const float (&x)[DS], const float *cb, unsigned svmask,
-                                               int bc, unsigned cmask, int Ks, int &code)
+__device__ __forceinline__ void decide_exact_warp(bool unsure, float4 v0, float4 v1, const float *cb,
+                                                  unsigned svmask, int bestj, unsigned cmask, int Ks, int &code)
 {
     const int lane = threadIdx.x & 31;
-    const int q = lane & (CW - 1);
     for (unsigned todo = __ballot_sync(0xffffffffu, unsure); todo; todo &= todo - 1) {
         const int u = __ffs(todo) - 1;
-        float xu[DS];
-#pragma unroll
-        for (int d = 0; d < DS; ++d) xu[d] = __shfl_sync(0xffffffffu, x[d], u);
+        const float x[DS] = {__shfl_sync(0xffffffffu, v0.x, u), __shfl_sync(0xffffffffu, v0.y, u),
+                             __shfl_sync(0xffffffffu, v0.z, u), __shfl_sync(0xffffffffu, v0.w, u),
+                             __shfl_sync(0xffffffffu, v1.x, u), __shfl_sync(0xffffffffu, v1.y, u),
+                             __shfl_sync(0xffffffffu, v1.z, u), __shfl_sync(0xffffffffu, v1.w, u)};
         const unsigned sm = __shfl_sync(0xffffffffu, svmask, u);
         const unsigned cm = __shfl_sync(0xffffffffu, cmask, u);
-        const int b = __shfl_sync(0xffffffffu, bc, u);
-        // candidate of this lane in a pass over chunk pair (c0, c1): lanes 0-15 take c0, 16-31 c1
-        auto cand = [&](int c0, int c1) -> int {
-            const int c = lane < CW ? c0 : c1;
-            if (c < 0) return -1;
-            const int k = c * CW + q;
-            if (c == b && !((sm >> q) & 1u)) return -1;
-            return k < Ks ? k : -1;
-        };
+        const int bj = __shfl_sync(0xffffffffu, bestj, u);
         float d1 = FLT_MAX, d2 = FLT_MAX;
         int k1 = INT_MAX;
-        unsigned rem = cm | (1u << b);
-        while (rem) {
-            const int c0 = __ffs(rem) - 1;
-            rem &= rem - 1;
-            int c1 = -1;
-            if (rem) {
-                c1 = __ffs(rem) - 1;
-                rem &= rem - 1;
-            }
-            const int k = cand(c0, c1);
-            if (k >= 0) top2_merge(d1, k1, d2, d2_fp32(xu, cb + k * DS), k, FLT_MAX);
+        if ((sm >> lane) & 1u) {
+            const int k = bj * 32 + lane;
+            top2_merge(d1, k1, d2, d2_fp32(x, cb + k * CB_STRIDE), k, FLT_MAX);
+        }
+        for (unsigned m = cm; m; m &= m - 1) {
+            const int k = (__ffs(m) - 1) * 32 + lane;
+            if (k < Ks) top2_merge(d1, k1, d2, d2_fp32(x, cb + k * CB_STRIDE), k, FLT_MAX);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -340,28 +326,20 @@ __device__ __noinline__ void decide_exact_warp(bool unsure, const float (&x)[DS]
             const float lim = d1 + margin;
             double best = DBL_MAX;
             int bk = INT_MAX;
-            rem = cm | (1u << b);
-            while (rem) {
-                const int c0 = __ffs(rem) - 1;
-                rem &= rem - 1;
-                int c1 = -1;
-                if (rem) {
-                    c1 = __ffs(rem) - 1;
-                    rem &= rem - 1;
-                }
-                const int k = cand(c0, c1);
-                if (k >= 0 && d2_fp32(xu, cb + k * DS) <= lim) {
-                    float cv[DS];
-                    const float4 c0v = __ldg(reinterpret_cast<const float4 *>(cb + k * DS));
-                    const float4 c1v = __ldg(reinterpret_cast<const float4 *>(cb + k * DS + 4));
-                    cv[0] = c0v.x; cv[1] = c0v.y; cv[2] = c0v.z; cv[3] = c0v.w;
-                    cv[4] = c1v.x; cv[5] = c1v.y; cv[6] = c1v.z; cv[7] = c1v.w;
-                    const double e = d2_fp64(xu, cv, DS);
+            auto fp64 = [&](int k) {
+                const float *c = cb + k * CB_STRIDE;
+                if (d2_fp32(x, c) <= lim) {
+                    const double e = d2_fp64(x, c, DS);
                     if (e < best || (e == best && k < bk)) {
                         best = e;
                         bk = k;
                     }
                 }
+            };
+            if ((sm >> lane) & 1u) fp64(bj * 32 + lane);
+            for (unsigned m = cm; m; m &= m - 1) {
+                const int k = (__ffs(m) - 1) * 32 + lane;
+                if (k < Ks) fp64(k);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -374,12 +352,11 @@ __device__ __noinline__ void decide_exact_warp(bool unsure, const float (&x)[DS]
             }
             result = bk;
         }
-        // a row without a finite candidate distance (non-finite input) keeps a valid index
-        if (lane == u) code = (result >= 0 && result < Ks) ? result : 0;
+        if (lane == u) code = result;
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_constant__ CUtensorMap tmap,
+__global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                   const TcArgs a)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -404,18 +381,18 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
     float *xs = reinterpret_cast<float *>(sm + OFF_XS);
     unsigned char *aop = sm + OFF_A;
     unsigned char *bop = sm + OFF_B;
+    float *cbf = reinterpret_cast<float *>(sm + OFF_CBF);
     int *acch = reinterpret_cast<int *>(sm + OFF_ACC);
     int *accl = acch + ACC_BYTES / 4;
+    float *accf = reinterpret_cast<float *>(accl + ACC_BYTES / 4);
     int *cnt = reinterpret_cast<int *>(sm + OFF_CNT);
-    float *winb = reinterpret_cast<float *>(sm + OFF_WIN);
-    int *codes_s = reinterpret_cast<int *>(sm + OFF_CODE);
     uint64_t *mb = reinterpret_cast<uint64_t *>(sm + OFF_MISC);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + OFF_MISC + MISC_TSLOT);
     float *mu = reinterpret_cast<float *>(sm + OFF_MISC + MISC_MU);
     unsigned *bnd = reinterpret_cast<unsigned *>(sm + OFF_MISC + MISC_BND);  // [G][2] float bits: n', ||c'|| maxima
     auto bar = [&](int slot) { return smem_u32(mb + slot); };
 
-    // ---- set-up: codeword mean, B operands, bounds, cleared sums -------------
+    // ---- set-up: codeword mean, B operands, FP32 copies, bounds -------------
     if (tid < G * DS) {
         const int g = tid / DS, j = tid % DS;
         const float *Cm = Cc + (size_t)(m0 + g) * Ks * DS;
@@ -427,21 +404,24 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
     __syncthreads();
     for (int e = tid; e < G * KSMAX; e += kThreads) {
         const int g = e / KSMAX, k = e % KSMAX;
-        float cc[DS];
+        float c[DS], cc[DS];
         float nc = 0.0f;
         if (k < Ks) {
             const float *src = Cc + ((size_t)(m0 + g) * Ks + k) * DS;
 #pragma unroll
             for (int j = 0; j < DS; ++j) {
-                cc[j] = src[j] - mu[g * DS + j];
+                c[j] = src[j];
+                cc[j] = c[j] - mu[g * DS + j];
                 nc = fmaf(cc[j], cc[j], nc);
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < DS; ++j) cc[j] = 0.0f;
+            for (int j = 0; j < DS; ++j) { c[j] = 0.0f; cc[j] = 0.0f; }
         }
         const float norm2c = nc;
         nc *= 0.5f;
+#pragma unroll
+        for (int j = 0; j < DS; ++j) cbf[(g * KSMAX + k) * CB_STRIDE + j] = c[j];
         float ch[DS], cl[DS];
 #pragma unroll
         for (int j = 0; j < DS; ++j) {
@@ -474,14 +454,10 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
             for (int j = 0; j < DS; ++j) {
                 acch[(g * KSMAX + k) * ACC_STRIDE + j] = 0;
                 accl[(g * KSMAX + k) * ACC_STRIDE + j] = 0;
+                accf[(g * KSMAX + k) * ACC_STRIDE + j] = 0.0f;
             }
             cnt[g * KSMAX + k] = 0;
         }
-    }
-    if (fit) {
-        // this CTA's FP32 sums (residual elements beyond the fixed-point format) are added in place
-        float *o = a.part.o + (size_t)blockIdx.x * a.M * Ks * DS + (size_t)m0 * Ks * DS;
-        for (int e = tid; e < G * Ks * DS; e += kThreads) o[e] = 0.0f;
     }
     // constant K lanes 24..31 of every A stage: [1 1 0 0 0 0 0 0]
     for (int e = tid; e < NAS * G * TM; e += kThreads) {
@@ -491,8 +467,7 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
     if (tid == 0) {
         for (int s = 0; s < NXS; ++s) {
             mbar_init(bar(MB_FULL + s), 1);
-            mbar_init(bar(MB_EMPTY + s), 8);  // the four half-1 warps of each subspace
-            mbar_init(bar(MB_WREADY + s), kOpWarps);
+            mbar_init(bar(MB_EMPTY + s), kOpWarps + 8);
         }
         for (int i = 0; i < NAS * G; ++i) {
             mbar_init(bar(MB_AREADY + i), kOpWarps);
@@ -516,8 +491,6 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
     const uint32_t tmem = *tslot;
 
     const int n_my = (tiles_c > lb) ? (tiles_c - 1 - lb) / gxc + 1 : 0;
-    // one fixed-point format for every CTA of the chunk: the row bound is the busiest CTA's rows
-    const int64_t rows_bound = (int64_t)((tiles_c + gxc - 1) / gxc) * TM;
 
     if (warp == 0) {
         // ---- producer: TMA loads of the row tiles -----------------------------
@@ -565,15 +538,8 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
             mbar_wait(bar(MB_DRAIN + g), 0, a.err);
         }
     } else if (warp < kEpi0 / 32) {
-        // ---- operand warps: bf16 A operands of both subspaces and the error window of every
-        // (row, subspace); operand thread t takes rows t + 64 rr
+        // ---- operand warp: bf16 A operands of both subspaces, rows t + 32 rr
         const int t = tid - kOp0;
-        float nbp[G], cbp[G];
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            nbp[g] = __uint_as_float(bnd[g * 2 + 0]) * (1.0f + 1e-5f);
-            cbp[g] = __uint_as_float(bnd[g * 2 + 1]) * (1.0f + 1e-5f);
-        }
         for (int i = 0; i < n_my; ++i) {
             const int s = i % NXS, as = i % NAS;
             if (!__all_sync(0xffffffffu, mbar_wait(bar(MB_FULL + s), (i / NXS) & 1, a.err))) break;
@@ -584,6 +550,8 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
 #pragma unroll
                 for (int c = 0; c < 4; ++c) v[rr][c] = *xs_chunk(stage, t + 32 * kOpWarps * rr, c);
             fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar(MB_EMPTY + s));
             bool ok = true;
 #pragma unroll
             for (int g = 0; g < G; ++g) {
@@ -599,11 +567,9 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
                     const float x[DS] = {v[rr][2 * g].x, v[rr][2 * g].y, v[rr][2 * g].z, v[rr][2 * g].w,
                                          v[rr][2 * g + 1].x, v[rr][2 * g + 1].y, v[rr][2 * g + 1].z, v[rr][2 * g + 1].w};
                     float xh[DS], xl[DS];
-                    float xx = 0.0f;
 #pragma unroll
                     for (int d = 0; d < DS; ++d) {
                         const float xc = x[d] - mu[g * DS + d];
-                        xx = fmaf(xc, xc, xx);
                         xh[d] = __bfloat162float(__float2bfloat16_rn(xc));
                         xl[d] = xc - xh[d];
                     }
@@ -614,225 +580,189 @@ __global__ void __launch_bounds__(kThreads, 1) pq_pass_tc_kernel(const __grid_co
                         make_uint4(pack_bf16(xl[0], xl[1]), pack_bf16(xl[2], xl[3]), pack_bf16(xl[4], xl[5]),
                                    pack_bf16(xl[6], xl[7]));
                     *reinterpret_cast<uint4 *>(a0 + A_K16 + core_off(r, 0)) = wh;
-                    // twice the error bound of the row's scores
-                    const float xn = sqrtf(xx) * (1.0f + 1e-5f);
-                    const float tt = xn + cbp[g];
-                    winb[(s * G + g) * TM + r] = 2.0f * (kC1 * xn * cbp[g] + kC2 * nbp[g] + 1e-13f * tt * tt);
                 }
                 fence_async_smem();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar(MB_AREADY + as * G + g));
             }
             if (!ok) break;
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bar(MB_WREADY + s));
         }
     } else {
-        // ---- epilogue: warpgroup (g, h), thread = row = TMEM lane; every thread takes every
-        // named barrier of its subspace (n_my + 1 of them) whatever happens
-        const int q = (tid - kEpi0) >> 7;
-        const int g = q >> 1, h = q & 1;
+        // ---- epilogue warpgroups: thread = row = TMEM lane, warpgroup g = subspace g
+        const int g = (tid - kEpi0) >> 7;
         const int r = (warp & 3) * 32 + lane;
-        const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((g * 2 + h) * NH);
-        const float *cbg = Cc + (size_t)(m0 + g) * Ks * DS;
-        unsigned char *slot0 = sm + OFF_SLOT0 + (size_t)g * TM * SLOT_BYTES;
-        unsigned char *xch = sm + OFF_XCH;
-        bool alive = true;
-        float sse_s = 0.0f, sse_c = 0.0f;  // Kahan pair (half 1)
-        unsigned rechecks = 0;             // (half 0)
+        const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(g * 2 * NH);
+        const float nb_prime = __uint_as_float(bnd[g * 2 + 0]) * (1.0f + 1e-5f);
+        const float cb_prime = __uint_as_float(bnd[g * 2 + 1]) * (1.0f + 1e-5f);
+        const float *cbg = cbf + g * KSMAX * CB_STRIDE;
+        const int te = tid - kEpi0;
+        float4 *svs = reinterpret_cast<float4 *>(sm + OFF_SV) + te * 8;  // 16-byte pieces swizzled by te & 7
+        float sse_s = 0.0f, sse_c = 0.0f;  // Kahan pair
+        unsigned rechecks = 0;
+        // one format for every CTA of the chunk: the row bound is the busiest CTA's rows
+        const int64_t rows_bound = (int64_t)((tiles_c + gxc - 1) / gxc) * TM;
         const FixFmt fx = fix_format(rows_bound, 2.0f * __uint_as_float(bnd[g * 2 + 1]));
-
-        // the update of tile ip by half 1: residual of its row, squared error, fixed-point sums
-        auto update = [&](int ip) {
-            const int s = ip % NXS;
-            const int64_t row = r0 + (int64_t)(lb + ip * gxc) * TM + r;
-            alive = alive && __all_sync(0xffffffffu, mbar_wait(bar(MB_FULL + s), (ip / NXS) & 1, a.err));
-            if (alive && row < r1) {
-                const int code = min(max(codes_s[((ip & 1) * G + g) * TM + r], 0), Ks - 1);
-                const float *stage = xs + s * (XS_BYTES / 4);
-                const float4 v0 = *xs_chunk(stage, r, 2 * g);
-                const float4 v1 = *xs_chunk(stage, r, 2 * g + 1);
-                const float4 c0 = __ldg(reinterpret_cast<const float4 *>(cbg + code * DS));
-                const float4 c1 = __ldg(reinterpret_cast<const float4 *>(cbg + code * DS + 4));
-                const float res[DS] = {v0.x - c0.x, v0.y - c0.y, v0.z - c0.z, v0.w - c0.w,
-                                       v1.x - c1.x, v1.y - c1.y, v1.z - c1.z, v1.w - c1.w};
-                float e = 0.0f;
-#pragma unroll
-                for (int d = 0; d < DS; ++d) e = fmaf(res[d], res[d], e);
-                const float y = e - sse_c;  // Kahan accumulation of the squared error
-                const float t2 = sse_s + y;
-                sse_c = (t2 - sse_s) - y;
-                sse_s = t2;
-                if (fit) {
-                    const int o = (g * KSMAX + code) * ACC_STRIDE;
-#pragma unroll
-                    for (int d = 0; d < DS; ++d) {
-                        const float t = __fmul_rn(res[d], fx.scale);
-                        if (fabsf(t) < fx.lim) {
-                            const long long qv = __float2ll_rn(t);
-                            atomicAdd(acch + o + d, (int)(qv >> fx.L));
-                            atomicAdd(accl + o + d, (int)(qv & ((1LL << fx.L) - 1)));
-                        } else {
-                            atomicAdd(a.part.o + (((size_t)blockIdx.x * a.M + m0 + g) * Ks + code) * DS + d, res[d]);
-                        }
-                    }
-                    atomicAdd(cnt + g * KSMAX + code, 1);
-                }
-            }
+        for (int i = 0; i < n_my; ++i) {
+            const int s = i % NXS;
+            const int64_t row = r0 + (int64_t)(lb + i * gxc) * TM + r;
+            if (!__all_sync(0xffffffffu, mbar_wait(bar(MB_FULL + s), (i / NXS) & 1, a.err))) break;
+            const float *stage = xs + s * (XS_BYTES / 4);
+            const float4 v0 = *xs_chunk(stage, r, 2 * g);
+            const float4 v1 = *xs_chunk(stage, r, 2 * g + 1);
             // the stage is not read again: order the reads before the TMA that will refill it
             fence_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(bar(MB_EMPTY + s));
-        };
+            const float x[DS] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+            float xx = 0.0f;
+#pragma unroll
+            for (int d = 0; d < DS; ++d) {
+                const float xc = x[d] - mu[g * DS + d];
+                xx = fmaf(xc, xc, xx);
+            }
+            // sqrt as x * rsqrt(x): a few ulp, far inside the 1e-5 inflation
+            const float xn = (xx > 0.0f ? xx * rsqrtf(xx) : 0.0f) * (1.0f + 1e-5f);
+            const float tt = xn + cb_prime;
+            const float win = 2.0f * (kC1 * xn * cb_prime + kC2 * nb_prime + 1e-13f * tt * tt);
 
-        for (int i = 0; i < n_my; ++i) {
-            const int par = i & 1;
-            unsigned char *myslot = h == 0 ? slot0 : sm + OFF_SLOT1 + (size_t)(par * G + g) * TM * SLOT_BYTES;
-            // ---- chunk maxima of this half, its best chunk saved --------------
-            float cmx[NCH];
+            // scores, two halves of 128 codewords, each in its own TMEM buffer
             float best = -FLT_MAX, cm2 = -FLT_MAX;
             int bestj = 0;
-            alive = alive && __all_sync(0xffffffffu, mbar_wait(bar(MB_MMAF + g * 2 + h), i & 1, a.err));
-            if (alive) {
-                tc_after_sync();
-                float vb[2][CW], mx[2];
-                TC_LDMAX16(tl, vb[0], mx[0]);
-                TC_WAITMAX16(vb[0], mx[0]);
+            float cmx[KSMAX / 32];
+            // chunk j+1 is loaded from TMEM while chunk j is reduced (tcgen05.wait::ld waits for
+            // every outstanding load, so each wait sits after the reduction it overlaps)
+            bool ok = __all_sync(0xffffffffu, mbar_wait(bar(MB_MMAF + g * 2 + 0), i & 1, a.err));
+            if (!ok) break;
+            tc_after_sync();
+            float vb[2][32], mb2[2];
+            TC_LDMAX32(tl, vb[0], mb2[0]);
+            TC_WAITMAX32(vb[0], mb2[0]);
 #pragma unroll
-                for (int j = 0; j < NCH; ++j) {
-                    if (j + 1 < NCH) TC_LDMAX16(tl + (uint32_t)((j + 1) * CW), vb[(j + 1) & 1], mx[(j + 1) & 1]);
-                    const float *v = vb[j & 1];
-                    const float cm = mx[j & 1];
-                    cmx[j] = cm;
-                    const bool better = cm > best;
-                    cm2 = better ? best : fmaxf(cm2, cm);
-                    best = better ? cm : best;
-                    bestj = better ? j : bestj;
-                    if (better) {
-#pragma unroll
-                        for (int c = 0; c < 4; ++c)
-                            *slot_piece(myslot, r, c) = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
-                    }
-                    if (j + 1 < NCH) TC_WAITMAX16(vb[(j + 1) & 1], mx[(j + 1) & 1]);
+            for (int j = 0; j < KSMAX / 32; ++j) {
+                if (j + 1 == NH / 32) {
+                    ok = __all_sync(0xffffffffu, mbar_wait(bar(MB_MMAF + g * 2 + 1), i & 1, a.err));
+                    if (!ok) break;
+                    tc_after_sync();
                 }
-            } else {
+                if (j + 1 < KSMAX / 32) TC_LDMAX32(tl + (uint32_t)((j + 1) * 32), vb[(j + 1) & 1], mb2[(j + 1) & 1]);
+                const float *v = vb[j & 1];
+                const float cm = mb2[j & 1];
+                cmx[j] = cm;
+                const bool better = cm > best;
+                cm2 = better ? best : fmaxf(cm2, cm);
+                best = better ? cm : best;
+                bestj = better ? j : bestj;
+                if (better) {
 #pragma unroll
-                for (int j = 0; j < NCH; ++j) cmx[j] = -FLT_MAX;
+                    for (int c = 0; c < 8; ++c)
+                        svs[c ^ (te & 7)] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+                }
+                if (j + 1 == NH / 32) {
+                    // every load of the first buffer has completed: hand it back to the MMA warp
+                    tc_before_sync();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar(MB_TFREE + g * 2 + 0));
+                }
+                if (j + 1 < KSMAX / 32) TC_WAITMAX32(vb[(j + 1) & 1], mb2[(j + 1) & 1]);
             }
-            // every load of this half has completed: hand the buffer back to the MMA warp
+            if (!ok) break;
             tc_before_sync();
             __syncwarp();
-            if (lane == 0) mbar_arrive(bar(MB_TFREE + g * 2 + h));
-            if (h == 1) {
-                unsigned char *xp = xch + ((size_t)(par * G + g) * TM + r) * XCH_BYTES;
-                *reinterpret_cast<float4 *>(xp) = make_float4(best, cm2, __int_as_float(bestj), 0.0f);
-                uint4 mq;
-                mq.x = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_ru(cmx[0])) |
-                       ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_ru(cmx[1])) << 16);
-                mq.y = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_ru(cmx[2])) |
-                       ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_ru(cmx[3])) << 16);
-                mq.z = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_ru(cmx[4])) |
-                       ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_ru(cmx[5])) << 16);
-                mq.w = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_ru(cmx[6])) |
-                       ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_ru(cmx[7])) << 16);
-                *reinterpret_cast<uint4 *>(xp + 16) = mq;
-            }
-            pair_sync(g);
-            if (h == 1) {
-                if (i >= 1) update(i - 1);
-                continue;
-            }
-            // ---- half 0: the decision for tile i --------------------------------
-            const int s = i % NXS;
-            const int64_t row = r0 + (int64_t)(lb + i * gxc) * TM + r;
-            const unsigned char *xp = xch + ((size_t)(par * G + g) * TM + r) * XCH_BYTES;
-            const float4 info = *reinterpret_cast<const float4 *>(xp);
-            const bool w1 = info.x > best;  // ties go to half 0, the lower codewords
-            const float gbest = w1 ? info.x : best;
-            const float gcm2 = fmaxf(w1 ? best : info.x, w1 ? info.y : cm2);
-            const int bc = w1 ? NCH + __float_as_int(info.z) : bestj;  // global chunk 0..15
-            alive = alive && __all_sync(0xffffffffu, mbar_wait(bar(MB_WREADY + s), (i / NXS) & 1, a.err));
-            int code = 0;
-            if (alive) {
-                const float theta = gbest - winb[(s * G + g) * TM + r];
-                const unsigned char *wslot = w1 ? sm + OFF_SLOT1 + (size_t)(par * G + g) * TM * SLOT_BYTES : slot0;
-                float sv[CW];
+            if (lane == 0) mbar_arrive(bar(MB_TFREE + g * 2 + 1));
+            // certain when the best chunk holds exactly one score >= theta and no other chunk reaches it;
+            // the sum below packs that count (low 6 bits) and the score's position (bits 6..)
+            const float theta = best - win;
+            float sv[32];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const float4 t4 = *slot_piece(const_cast<unsigned char *>(wslot), r, c);
-                    sv[4 * c] = t4.x;
-                    sv[4 * c + 1] = t4.y;
-                    sv[4 * c + 2] = t4.z;
-                    sv[4 * c + 3] = t4.w;
+            for (int c = 0; c < 8; ++c) {
+                const float4 t4 = svs[c ^ (te & 7)];
+                sv[4 * c] = t4.x;
+                sv[4 * c + 1] = t4.y;
+                sv[4 * c + 2] = t4.z;
+                sv[4 * c + 3] = t4.w;
+            }
+            float tally = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) tally = fmaf(sv[q] >= theta ? 1.0f : 0.0f, (float)(1 + 64 * q), tally);
+            const int ti = (int)tally;
+            int code = bestj * 32 + (ti >> 6);
+            const bool valid = row < r1;
+            const bool unsure = valid && !((ti & 63) == 1 && cm2 < theta);
+            if (__any_sync(0xffffffffu, unsure)) {
+                unsigned cmask = 0, svmask = 0;
+#pragma unroll
+                for (int c = 0; c < KSMAX / 32; ++c) cmask |= (c != bestj && cmx[c] >= theta) ? (1u << c) : 0u;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) svmask |= (sv[q] >= theta) ? (1u << q) : 0u;
+                decide_exact_warp(unsure, v0, v1, cbg, svmask, bestj, cmask, Ks, code);
+                rechecks += unsure ? 1u : 0u;
+            }
+            if (valid) {
+                const float *c = cbg + code * CB_STRIDE;
+                float res[DS];
+                const float4 c0 = *reinterpret_cast<const float4 *>(c);
+                const float4 c1 = *reinterpret_cast<const float4 *>(c + 4);
+                const float cv[DS] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+                for (int d = 0; d < DS; ++d) res[d] = x[d] - cv[d];
+                if (a.sse) {
+                    float e = 0.0f;
+#pragma unroll
+                    for (int d = 0; d < DS; ++d) e = fmaf(res[d], res[d], e);
+                    const float y = e - sse_c;  // Kahan accumulation of the squared error
+                    const float t2 = sse_s + y;
+                    sse_c = (t2 - sse_s) - y;
+                    sse_s = t2;
                 }
-                // certain when the best chunk holds exactly one score >= theta and no other chunk
-                // reaches it; the sum packs that count (low 6 bits) and the score's position (bits 6..)
-                float tally = 0.0f;
+                if (fit) {
+                    const int o = (g * KSMAX + code) * ACC_STRIDE;
+                    long long q[DS];
+                    bool big = false;
 #pragma unroll
-                for (int c = 0; c < CW; ++c) tally = fmaf(sv[c] >= theta ? 1.0f : 0.0f, (float)(1 + 64 * c), tally);
-                const int ti = (int)tally;
-                code = bc * CW + (ti >> 6);
-                const bool valid = row < r1;
-                const bool unsure = valid && !((ti & 63) == 1 && gcm2 < theta);
-                if (__any_sync(0xffffffffu, unsure)) {
-                    unsigned cmask = 0, svmask = 0;
-#pragma unroll
-                    for (int c = 0; c < NCH; ++c) cmask |= (c != bc && cmx[c] >= theta) ? (1u << c) : 0u;
-                    const uint4 mq = *reinterpret_cast<const uint4 *>(xp + 16);
-                    const uint32_t mw[4] = {mq.x, mq.y, mq.z, mq.w};
-#pragma unroll
-                    for (int c = 0; c < NCH; ++c) {
-                        const float m1 = __bfloat162float(
-                            __ushort_as_bfloat16((unsigned short)(mw[c >> 1] >> (16 * (c & 1)))));
-                        cmask |= (NCH + c != bc && m1 >= theta) ? (1u << (NCH + c)) : 0u;
+                    for (int d = 0; d < DS; ++d) {
+                        const float t = __fmul_rn(res[d], fx.scale);
+                        big |= !(fabsf(t) < fx.lim);
+                        q[d] = __float2ll_rn(t);
                     }
+                    if (!big) {
 #pragma unroll
-                    for (int c = 0; c < CW; ++c) svmask |= (sv[c] >= theta) ? (1u << c) : 0u;
-                    // the row itself, from the stage (landed: the operand warps read it before)
-                    const bool ready = __all_sync(0xffffffffu, mbar_wait(bar(MB_FULL + s), (i / NXS) & 1, a.err));
-                    if (ready) {
-                        const float *stage = xs + s * (XS_BYTES / 4);
-                        const float4 v0 = *xs_chunk(stage, r, 2 * g);
-                        const float4 v1 = *xs_chunk(stage, r, 2 * g + 1);
-                        const float x[DS] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-                        decide_exact_warp(unsure, x, cbg, svmask, bc, cmask, Ks, code);
-                        fence_async_smem();
+                        for (int d = 0; d < DS; ++d) {
+                            atomicAdd(acch + o + d, (int)(q[d] >> fx.L));
+                            atomicAdd(accl + o + d, (int)(q[d] & ((1LL << fx.L) - 1)));
+                        }
+                    } else {
+#pragma unroll
+                        for (int d = 0; d < DS; ++d) atomicAdd(accf + o + d, res[d]);
                     }
-                    alive = alive && ready;
-                    rechecks += unsure ? 1u : 0u;
+                    atomicAdd(cnt + g * KSMAX + code, 1);
                 }
-                if (valid && a.codes) a.codes[row * a.M + m0 + g] = (uint8_t)code;
+                if (a.codes) a.codes[row * a.M + m0 + g] = (uint8_t)code;
             }
-            codes_s[(par * G + g) * TM + r] = code;
         }
-        // the last tile's update: half 0 has published its codes at the barrier below
-        pair_sync(g);
-        if (h == 1 && n_my >= 1) update(n_my - 1);
-
         // ---- results of this CTA -------------------------------------------
-        asm volatile("bar.sync 3, 512;" ::: "memory");
+        asm volatile("bar.sync 1, 256;" ::: "memory");
         if (fit) {
-            for (int e = tid - kEpi0; e < G * KSMAX; e += 512) {
+            const int64_t rows_bound = (int64_t)((tiles_c + gxc - 1) / gxc) * TM;
+            for (int e = tid - kEpi0; e < G * KSMAX; e += 256) {
                 const int gg = e / KSMAX, k = e % KSMAX;
                 if (k >= Ks) continue;
                 const size_t base = ((size_t)blockIdx.x * a.M + m0 + gg) * Ks + k;
                 const FixFmt f = fix_format(rows_bound, 2.0f * __uint_as_float(bnd[gg * 2 + 1]));
                 const int o = (gg * KSMAX + k) * ACC_STRIDE;
 #pragma unroll
-                for (int d = 0; d < DS; ++d)
+                for (int d = 0; d < DS; ++d) {
                     a.part.q[base * DS + d] = (long long)acch[o + d] * (1LL << f.L) + (long long)accl[o + d];
+                    a.part.o[base * DS + d] = accf[o + d];
+                }
                 a.part.cnt[base] = cnt[gg * KSMAX + k];
                 if (lb == 0 && k == 0) a.part.F[chunk * a.M + m0 + gg] = f.F;
             }
         }
-        if (h == 1) {
-            double tot = (double)sse_s - (double)sse_c;
-            tot = warp_sum(tot);
-            if (a.sse && lane == 0) atomicAdd(a.sse, tot);
-        } else {
-            const unsigned rc = warp_sum(rechecks);
-            if (a.rechecks && lane == 0 && rc) atomicAdd(a.rechecks, (unsigned long long)rc);
-        }
+        double tot = (double)sse_s - (double)sse_c;
+        tot = warp_sum(tot);
+        if (a.sse && lane == 0) atomicAdd(a.sse, tot);
+        const unsigned rc = warp_sum(rechecks);
+        if (a.rechecks && lane == 0 && rc) atomicAdd(a.rechecks, (unsigned long long)rc);
     }
     tc_before_sync();
     __syncthreads();
@@ -878,7 +808,6 @@ int launch_pq_pass_tc(PqPass &p, cudaStream_t s)
 {
     if (!tc_pass_supported(p.D, p.M, p.Ks)) return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and M even");
     if (p.N >= (1LL << 31) / TM * TM) return fail(PQ_ENOTSUP, "BF16 tensor-core pass supports N < 2^31");
-    if (reinterpret_cast<uintptr_t>(p.C) & 15) return fail(PQ_EINVAL, "codebooks must be 16-byte aligned");
     PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
     if (!enc) return fail(PQ_ECUDA, "cuTensorMapEncodeTiled unavailable");
     CUtensorMap map;

@@ -24,7 +24,8 @@ EXPORTS = ("pq_fit", "pq_init_kmeanspp", "pq_encode", "pq_decode_rmse", "ivf_bui
            "ivf_copy_coarse", "ivf_copy_lists", "ivf_free", "pq_sync_status", "pq_last_error", "pq_launch_count",
            "pq_profile_enable", "pq_profile_collect", "pq_profile_names", "pq_lloyd_noalloc", "pq_fit_chunked",
            "softpq_forward", "softpq_backward", "pq_tune_chunked", "pq_tune_clear", "pq_fit_encode_host",
-           "pq_test_set_spin_limit", "pq_test_fail_alloc_after")
+           "pq_test_set_spin_limit", "pq_test_fail_alloc_after", "ivf_build_codes", "ivf_copy_centers",
+           "ivf_clone_empty", "ivf_add", "ivf_merge")
 
 
 class PqStats(C.Structure):
@@ -74,6 +75,11 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "pq_fit_encode_host": (i32, [p, i64, i32, i32, i32, i32, u64, i32, p, p, p]),
         "pq_test_set_spin_limit": (i32, [C.c_uint32]),
         "pq_test_fail_alloc_after": (i32, [i32]),
+        "ivf_build_codes": (i32, [p, p, i64, i32, i32, i32, i32, i32, u64, i32, C.POINTER(p), p]),
+        "ivf_copy_centers": (i32, [p, p, p]),
+        "ivf_clone_empty": (i32, [p, C.POINTER(p)]),
+        "ivf_add": (i32, [p, p, p, i64, i32, p]),
+        "ivf_merge": (i32, [p, p, p]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -350,6 +356,61 @@ class IVFIndex:
             _check(_lib.ivf_build(px, pc, N, D, M, nlist, iters, seed & (2**64 - 1), PREC[prec], C.byref(h),
                                   _stream(X)))
         return cls(h.value, X.device)
+
+    @classmethod
+    def build_codes(cls, codes: torch.Tensor, codebooks: torch.Tensor, nlist: int, iters: int = 25, seed: int = 0,
+                    prec: str = "fp32") -> "IVFIndex":
+        """Code-space index (Rii): centre codes by k-means over the PQ codes, lists by symmetric distance."""
+        pc = _need(codes, torch.uint8, 2, "codes")
+        pb = _need(codebooks, torch.float32, 3, "codebooks")
+        N, M = codes.shape
+        _, Ks, ds = codebooks.shape
+        h = C.c_void_p()
+        with torch.cuda.device(codes.device):
+            _check(_lib.ivf_build_codes(pc, pb, N, M * ds, M, Ks, nlist, iters, seed & (2**64 - 1), PREC[prec],
+                                        C.byref(h), _stream(codes)))
+        idx = cls(h.value, codes.device)
+        idx.code_space = True
+        return idx
+
+    code_space = False
+
+    def centers(self) -> torch.Tensor:
+        """Centre codes [nlist][M] of a code-space index."""
+        out = torch.empty((self.nlist, self.M), dtype=torch.uint8, device=self.device)
+        with torch.cuda.device(self.device):
+            _check(_lib.ivf_copy_centers(self._h, C.c_void_p(out.data_ptr()), _stream(out)))
+        return out
+
+    def clone_empty(self) -> "IVFIndex":
+        """A new index with the same coarse quantizer and no rows."""
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(_lib.ivf_clone_empty(self._h, C.byref(h)))
+        idx = IVFIndex(h.value, self.device)
+        idx.code_space = self.code_space
+        return idx
+
+    def add(self, codes: torch.Tensor, X: torch.Tensor | None = None, prec: str = "fp32"):
+        """Appends rows (ids N, N+1, ...) to the lists of their nearest coarse centres."""
+        pc = _need(codes, torch.uint8, 2, "codes")
+        px = _need(X, torch.float32, 2, "X") if X is not None else None
+        with torch.cuda.device(codes.device):
+            _check(_lib.ivf_add(self._h, px, pc, codes.shape[0], PREC[prec], _stream(codes)))
+        self._refresh()
+        return self
+
+    def merge(self, other: "IVFIndex"):
+        """Appends every row of `other` (same coarse quantizer), its ids shifted past this index's rows."""
+        with torch.cuda.device(self.device):
+            _check(_lib.ivf_merge(self._h, other._h, _stream()))
+        self._refresh()
+        return self
+
+    def _refresh(self):
+        N = C.c_int64()
+        _check(_lib.ivf_get_info(self._h, C.byref(N), None, None, None))
+        self.N = N.value
 
     def search(self, codebooks: torch.Tensor, Q: torch.Tensor, nprobe: int, k: int, out_ids=None, out_d=None):
         pc = _need(codebooks, torch.float32, 3, "codebooks")
