@@ -571,7 +571,11 @@ def run_gpu(args):
         Xm = torch.from_numpy(wm.data()).cuda()
         cm = pqgb.fit(Xm, wm.m, wm.ks, iters=wm.iters, seed=wm.init_seed, prec=prec)
         codes_m = pqgb.encode(Xm, cm, prec=prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         idx = pqgb.IVFIndex.build(Xm, codes_m, wm.nlist, iters=wm.ivf_iters, seed=wm.coarse_seed, prec=prec)
+        torch.cuda.synchronize()
+        t_b1 = time.perf_counter() - t0
         Qd = torch.from_numpy(wm.queries()).cuda()
         ms, kern_s, ids, _ = _time_search(torch, pqgb, idx, cm, Qd, wm, args.steps, args.warmup, flush)
         sample = np.random.default_rng(0).choice(wm.nq, 1000, replace=False)
@@ -581,11 +585,28 @@ def run_gpu(args):
                   for r in (1, 10, 100)}
         off, _, _ = idx.lists()
         scanned = _probe_bytes(torch, Qd, idx.coarse(), off, wm.nprobe, wm.m)
-        ivf1 = {"workload": wm.name, "queries_per_s": world * wm.nq / (ms / 1e3), "ms": ms, "nlist": wm.nlist,
+        ivf1 = {"workload": wm.name, "queries_per_s": world * wm.nq / (ms / 1e3), "ms": ms, "build_s": t_b1,
+                "nlist": wm.nlist,
                 "nprobe": wm.nprobe, "topk": wm.topk, "nq": wm.nq, "code_bytes_scanned": scanned,
                 "recall": recall, "recall_sample": "exact FP64 1-NN of 1,000 sampled queries (torch on the device)",
                 "l2_note": "the 16 MB code array is L2-resident"}
         idx.close()
+        # the code-space index (Rii: centre codes by k-means over the PQ codes) over the same codes
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        idxc = pqgb.IVFIndex.build_codes(codes_m, cm, wm.nlist, iters=wm.ivf_iters, seed=wm.coarse_seed, prec=prec)
+        torch.cuda.synchronize()
+        t_bc = time.perf_counter() - t0
+        ms_c, kern_c, ids_c, _ = _time_search(torch, pqgb, idxc, cm, Qd, wm, args.steps, args.warmup, flush)
+        got_c = ids_c.cpu().numpy()[sample]
+        recall_c = {f"recall@{r}": float(np.mean([nn[i] in got_c[i, :r] for i in range(len(sample))]))
+                    for r in (1, 10, 100)}
+        off_c, _, _ = idxc.lists()
+        scanned_c = _probe_bytes(torch, Qd, idxc.coarse(), off_c, wm.nprobe, wm.m)
+        idxc.close()
+        ivf1["code_space"] = {"queries_per_s": world * wm.nq / (ms_c / 1e3), "ms": ms_c, "build_s": t_bc,
+                              "code_bytes_scanned": scanned_c, "recall": recall_c,
+                              "note": "centre codes by k-means over the PQ codes, probed by the query's ADC table"}
         line["ivf_1m"] = ivf1
         line["queries_per_s"] = ivf10["queries_per_s"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -201,6 +201,21 @@ int pq_fit_chunked(const float *X, const int64_t *chunk_offsets, int32_t n_chunk
                    void *stream);
 
 /*
+ * pq_fit_chunked_weighted -- pq_fit_chunked with a weighted centroid dataset
+ * (a variant of Sec. 3's combine step).  Arguments and outputs as pq_fit_chunked.
+ * Pooled codeword k of subspace m of chunk c carries the weight w = its member
+ * count in the chunk's last Lloyd update (the number of the chunk's rows whose
+ * mean it is; 1 when iters = 0), so a weighted mean of pooled codewords is a
+ * mean of the rows behind them.  The global model is seeded by k-means++ on the
+ * pooled codewords as they are, then `iters` rounds of exact nearest-codeword
+ * assignment and weighted update c = sum w x / sum w (float-float sums in pooled
+ * row order, one rounding; a codeword whose members weigh 0 keeps its value).
+ */
+int pq_fit_chunked_weighted(const float *X, const int64_t *chunk_offsets, int32_t n_chunks, int32_t D, int32_t M,
+                            int32_t Ks, int32_t iters, uint64_t seed, int32_t prec, float *codebooks, uint8_t *codes,
+                            double *rmse, void *stream);
+
+/*
  * softpq_forward / softpq_backward -- soft-assignment reconstruction loss for
  * codebook refinement, the differentiable relaxation of the hard assignment of
  * Sec. 2.1:

@@ -459,9 +459,9 @@ int pq_decode_rmse(const uint8_t *codes, const float *codebooks, const float *X,
     return ws.status;
 }
 
-int pq_fit_chunked(const float *X, const int64_t *chunk_offsets, int32_t n_chunks, int32_t D, int32_t M, int32_t Ks,
+static int chunked_entry(const float *X, const int64_t *chunk_offsets, int32_t n_chunks, int32_t D, int32_t M, int32_t Ks,
                    int32_t iters, uint64_t seed, int32_t prec, float *codebooks, uint8_t *codes, double *rmse,
-                   void *stream)
+                   void *stream, bool weighted)
 {
     g_msg[0] = 0;
     if (!X || !chunk_offsets || !codebooks || !codes) return fail(PQ_EINVAL, "null pointer");
@@ -482,7 +482,21 @@ int pq_fit_chunked(const float *X, const int64_t *chunk_offsets, int32_t n_chunk
         return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and M even");
     if ((int64_t)n_chunks * Ks < Ks) return fail(PQ_EINVAL, "empty centroid dataset");
     return run_pq_fit_chunked(X, chunk_offsets, n_chunks, D, M, Ks, iters, seed, prec, codebooks, codes, rmse,
-                              static_cast<cudaStream_t>(stream));
+                              static_cast<cudaStream_t>(stream), weighted);
+}
+
+int pq_fit_chunked(const float *X, const int64_t *chunk_offsets, int32_t n_chunks, int32_t D, int32_t M, int32_t Ks,
+                   int32_t iters, uint64_t seed, int32_t prec, float *codebooks, uint8_t *codes, double *rmse,
+                   void *stream)
+{
+    return chunked_entry(X, chunk_offsets, n_chunks, D, M, Ks, iters, seed, prec, codebooks, codes, rmse, stream, false);
+}
+
+int pq_fit_chunked_weighted(const float *X, const int64_t *chunk_offsets, int32_t n_chunks, int32_t D, int32_t M,
+                            int32_t Ks, int32_t iters, uint64_t seed, int32_t prec, float *codebooks, uint8_t *codes,
+                            double *rmse, void *stream)
+{
+    return chunked_entry(X, chunk_offsets, n_chunks, D, M, Ks, iters, seed, prec, codebooks, codes, rmse, stream, true);
 }
 
 int pq_tune_chunked(const float *X, const int64_t *chunk_offsets, int32_t n_chunks, int32_t D, int32_t M, int32_t Ks,

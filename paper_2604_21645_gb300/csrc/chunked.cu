@@ -62,6 +62,60 @@ __global__ void pool_codewords_kernel(const float *__restrict__ C, int n_chunks,
     }
 }
 
+// W[(c*Ks + k)*M + m] = counts[(c*M + m)*Ks + k]: the weight of pooled row c*Ks + k in subspace m
+__global__ void pool_weights_kernel(const long long *__restrict__ counts, int n_chunks, int M, int Ks,
+                                    long long *__restrict__ W)
+{
+    const int64_t total = (int64_t)n_chunks * M * Ks;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e % Ks);
+        const int64_t cm = e / Ks;
+        const int m = (int)(cm % M);
+        const int64_t c = cm / M;
+        W[(c * Ks + k) * M + m] = counts[e];
+    }
+}
+
+__global__ void fill_ll_kernel(long long *p, int64_t n, long long v)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        p[e] = v;
+}
+
+// Weighted update of the global model, one thread per (subspace, codeword, dimension): over the
+// pooled rows p in order, the members of codeword k in subspace m add W[p][m] * x in float-float
+// (each product exact by TwoProduct), their weights in int64; the codeword becomes the float-float
+// quotient rounded once, or keeps its value when its members weigh nothing.
+__global__ void weighted_update_kernel(const float *__restrict__ P, int64_t n, int D, int M, int Ks, int ds,
+                                       const uint8_t *__restrict__ codes, const long long *__restrict__ W,
+                                       float *__restrict__ C)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)M * Ks * ds) return;
+    const int j = (int)(idx % ds);
+    const int k = (int)((idx / ds) % Ks), m = (int)(idx / ((int64_t)ds * Ks));
+    float sh = 0.0f, sl = 0.0f;
+    long long wsum = 0;
+    for (int64_t p = 0; p < n; ++p) {
+        if (codes[p * M + m] != k) continue;
+        const long long w = W[p * M + m];
+        if (w == 0) continue;
+        float wh, wl;
+        ll_to_ff(w, wh, wl);
+        const float x = P[p * D + (int64_t)m * ds + j];
+        float ph, pe;
+        two_prod(wh, x, ph, pe);
+        pe = __fmaf_rn(wl, x, pe);
+        ff_add(sh, sl, ph, pe, sh, sl);
+        wsum += w;
+    }
+    if (wsum == 0) return;
+    float nh, nl, qh, ql;
+    ll_to_ff(wsum, nh, nl);
+    ff_div(sh, sl, nh, nl, qh, ql);
+    C[idx] = __fadd_rn(qh, ql);
+}
+
 // Grid blocks shared out over the chunks in proportion to their rows: `per` blocks
 // for the whole data set, at least one and at most one row tile's worth per chunk.
 int build_chunk_table(const int64_t *off, int n_chunks, int per, bool tc, ChunkTableParams &tp)
@@ -105,7 +159,8 @@ TuneKey tune_key(const int64_t *off, int n_chunks, int D, int M, int Ks, int pre
 }  // namespace
 
 int run_pq_fit_chunked(const float *X, const int64_t *off, int n_chunks, int D, int M, int Ks, int iters,
-                       uint64_t seed, int prec, float *global_cb, uint8_t *codes, double *rmse, cudaStream_t s)
+                       uint64_t seed, int prec, float *global_cb, uint8_t *codes, double *rmse, cudaStream_t s,
+                       bool weighted)
 {
     const int64_t N = off[n_chunks];
     const int ds = D / M;
@@ -165,12 +220,21 @@ int run_pq_fit_chunked(const float *X, const int64_t *off, int n_chunks, int D, 
     p.chunk_off = d_off;
     p.chunk_blk = d_blk;
     p.n_chunks = n_chunks;
+    // member counts of each chunk's last update (the weights of the weighted combine)
+    long long *counts = weighted ? ws.get<long long>((size_t)n_chunks * M * Ks) : nullptr;
+    if (ws.status) return ws.status;
+    if (weighted && iters == 0) {
+        fill_ll_kernel<<<64, 256, 0, s>>>(counts, (int64_t)n_chunks * M * Ks, 1);
+        count_launch();
+        PQ_TRY_CUDA(cudaGetLastError());
+    }
     for (int t = 0; t < iters; ++t) {
         if (tc)
             PQ_TRY(launch_pq_pass_tc(p, s));
         else
             PQ_TRY(launch_pq_pass_f32(p, s));
-        PQ_TRY(launch_pq_finalize(p.part, gx, M, Ks, ds, Cl, nullptr, s, n_chunks, d_blk));
+        PQ_TRY(launch_pq_finalize(p.part, gx, M, Ks, ds, Cl, nullptr, s, n_chunks, d_blk,
+                                  t + 1 == iters ? counts : nullptr));
     }
 
     // (3) centroid dataset of the pooled codewords, (4) global fit, (5) global encode + error
@@ -186,7 +250,41 @@ int run_pq_fit_chunked(const float *X, const int64_t *off, int n_chunks, int D, 
         count_launch();
         PQ_TRY_CUDA(cudaGetLastError());
     }
-    PQ_TRY(pq_fit(pool, npool, D, M, Ks, iters, seed, prec, nullptr, global_cb, nullptr, s));
+    if (!weighted) {
+        PQ_TRY(pq_fit(pool, npool, D, M, Ks, iters, seed, prec, nullptr, global_cb, nullptr, s));
+    } else {
+        // weighted global fit: k-means++ seeding of the pooled rows, then rounds of exact assignment
+        // (an encode pass) and the weighted update
+        long long *W = ws.get<long long>((size_t)npool * M);
+        uint8_t *pcodes = ws.get<uint8_t>((size_t)npool * M);
+        if (ws.status) return ws.status;
+        {
+            ProfScope ps("pool_weights", s);
+            pool_weights_kernel<<<64, 256, 0, s>>>(counts, n_chunks, M, Ks, W);
+            count_launch();
+            PQ_TRY_CUDA(cudaGetLastError());
+        }
+        PQ_TRY(pq_init_kmeanspp(pool, npool, D, M, Ks, seed, global_cb, s));
+        PqPass gp;
+        gp.X = pool;
+        gp.N = npool;
+        gp.D = D;
+        gp.M = M;
+        gp.Ks = Ks;
+        gp.ds = ds;
+        gp.C = global_cb;
+        gp.codes = pcodes;
+        const int64_t nth = (int64_t)M * Ks * ds;
+        for (int t = 0; t < iters; ++t) {
+            PqPass q = gp;
+            PQ_TRY(tc ? launch_pq_pass_tc(q, s) : launch_pq_pass_f32(q, s));
+            ProfScope ps("weighted_update", s);
+            weighted_update_kernel<<<(unsigned)((nth + 127) / 128), 128, 0, s>>>(pool, npool, D, M, Ks, ds, pcodes, W,
+                                                                              global_cb);
+            count_launch();
+            PQ_TRY_CUDA(cudaGetLastError());
+        }
+    }
     PQ_TRY(pq_encode(X, N, D, M, Ks, global_cb, prec, codes, sse, nullptr, s));
     if (rmse) {
         double h = 0.0;

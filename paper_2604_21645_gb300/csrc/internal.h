@@ -93,8 +93,9 @@ int pq_pass_blocks_per_subspace(const PqPass &p);
 int launch_pq_pass_f32(PqPass &p, cudaStream_t s);
 // Adds the blocks' partials of every (chunk, subspace, codeword) and moves the codeword by
 // its members' mean residual; a codeword without members keeps its value (counted in empties).
+// counts (optional) [n_chunks][M][Ks] receives the member counts.
 int launch_pq_finalize(const Partials &part, int gx, int M, int Ks, int ds, float *C, unsigned long long *empties,
-                       cudaStream_t s, int n_chunks = 1, const int *chunk_blk = nullptr);
+                       cudaStream_t s, int n_chunks = 1, const int *chunk_blk = nullptr, long long *counts = nullptr);
 int launch_decode_rmse(const uint8_t *codes, const float *C, const float *X, int64_t N, int D, int M, int Ks,
                        float *Xhat, double *sse, cudaStream_t s);
 
@@ -150,8 +151,11 @@ int launch_merge_lists(const int64_t *a_off, const int64_t *a_ids, const uint8_t
                        cudaStream_t s);
 
 // ---- chunked divide and conquer (chunked.cu) -------------------------------
+// weighted: each pooled codeword carries its member count in its chunk's last update, and the
+// global model is the weighted fit of the pooled codewords
 int run_pq_fit_chunked(const float *X, const int64_t *off, int n_chunks, int D, int M, int Ks, int iters,
-                       uint64_t seed, int prec, float *global_cb, uint8_t *codes, double *rmse, cudaStream_t s);
+                       uint64_t seed, int prec, float *global_cb, uint8_t *codes, double *rmse, cudaStream_t s,
+                       bool weighted = false);
 
 // ---- query path (ivf_search.cu) --------------------------------------------
 struct SearchArgs {

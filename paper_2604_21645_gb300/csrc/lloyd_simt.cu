@@ -259,7 +259,8 @@ __global__ void __launch_bounds__(kThreads) pq_pass_f32_kernel(const PqPass a, c
 // exactly, the FP32 sums added with TwoSum (block order), the total scaled to a float-float
 // value, divided by the member count in float-float, and added to the codeword.
 __global__ void pq_finalize_kernel(const Partials part, int gx, int M, int Ks, int ds, float *C,
-                                   unsigned long long *empties, int n_chunks, const int *__restrict__ chunk_blk)
+                                   unsigned long long *empties, int n_chunks, const int *__restrict__ chunk_blk,
+                                   long long *__restrict__ counts)
 {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)n_chunks * M * Ks * ds) return;
@@ -278,6 +279,7 @@ __global__ void pq_finalize_kernel(const Partials part, int gx, int M, int Ks, i
         oh = s;
         ol = __fadd_rn(ol, err);
     }
+    if (counts && j == 0) counts[cw] = n;
     if (n == 0) {
         if (empties && j == 0) atomicAdd(empties, 1ull);
         return;
@@ -380,12 +382,12 @@ int launch_pq_pass_f32(PqPass &p, cudaStream_t s)
 }
 
 int launch_pq_finalize(const Partials &part, int gx, int M, int Ks, int ds, float *C, unsigned long long *empties,
-                       cudaStream_t s, int n_chunks, const int *chunk_blk)
+                       cudaStream_t s, int n_chunks, const int *chunk_blk, long long *counts)
 {
     const int64_t n = (int64_t)n_chunks * M * Ks * ds;
     ProfScope ps("pq_finalize", s);
     pq_finalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, gx, M, Ks, ds, C, empties, n_chunks,
-                                                                  chunk_blk);
+                                                                  chunk_blk, counts);
     count_launch();
     PQ_TRY_CUDA(cudaGetLastError());
     return PQ_OK;

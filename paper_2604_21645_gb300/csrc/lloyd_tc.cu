@@ -566,15 +566,18 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
                     const int r = t + 32 * kOpWarps * rr;
                     const float x[DS] = {v[rr][2 * g].x, v[rr][2 * g].y, v[rr][2 * g].z, v[rr][2 * g].w,
                                          v[rr][2 * g + 1].x, v[rr][2 * g + 1].y, v[rr][2 * g + 1].z, v[rr][2 * g + 1].w};
-                    float xh[DS], xl[DS];
+                    // high parts packed straight from the centred pair, low parts from their exact
+                    // bf16 values (bf16 -> float is a 16-bit shift)
+                    float xl[DS];
+                    uint32_t hw[DS / 2];
 #pragma unroll
-                    for (int d = 0; d < DS; ++d) {
-                        const float xc = x[d] - mu[g * DS + d];
-                        xh[d] = __bfloat162float(__float2bfloat16_rn(xc));
-                        xl[d] = xc - xh[d];
+                    for (int d = 0; d < DS; d += 2) {
+                        const float c0 = x[d] - mu[g * DS + d], c1 = x[d + 1] - mu[g * DS + d + 1];
+                        hw[d / 2] = pack_bf16(c0, c1);
+                        xl[d] = c0 - __uint_as_float(hw[d / 2] << 16);
+                        xl[d + 1] = c1 - __uint_as_float(hw[d / 2] & 0xffff0000u);
                     }
-                    const uint4 wh = make_uint4(pack_bf16(xh[0], xh[1]), pack_bf16(xh[2], xh[3]),
-                                                pack_bf16(xh[4], xh[5]), pack_bf16(xh[6], xh[7]));
+                    const uint4 wh = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                     *reinterpret_cast<uint4 *>(a0 + core_off(r, 0)) = wh;
                     *reinterpret_cast<uint4 *>(a0 + core_off(r, 8)) =
                         make_uint4(pack_bf16(xl[0], xl[1]), pack_bf16(xl[2], xl[3]), pack_bf16(xl[4], xl[5]),
@@ -681,10 +684,11 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
                 sv[4 * c + 2] = t4.z;
                 sv[4 * c + 3] = t4.w;
             }
-            float tally = 0.0f;
+            // four independent partial sums (exact small integers, so the order does not matter)
+            float tp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-            for (int q = 0; q < 32; ++q) tally = fmaf(sv[q] >= theta ? 1.0f : 0.0f, (float)(1 + 64 * q), tally);
-            const int ti = (int)tally;
+            for (int q = 0; q < 32; ++q) tp[q & 3] = fmaf(sv[q] >= theta ? 1.0f : 0.0f, (float)(1 + 64 * q), tp[q & 3]);
+            const int ti = (int)((tp[0] + tp[1]) + (tp[2] + tp[3]));
             int code = bestj * 32 + (ti >> 6);
             const bool valid = row < r1;
             const bool unsure = valid && !((ti & 63) == 1 && cm2 < theta);

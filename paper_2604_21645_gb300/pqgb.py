@@ -25,7 +25,7 @@ EXPORTS = ("pq_fit", "pq_init_kmeanspp", "pq_encode", "pq_decode_rmse", "ivf_bui
            "pq_profile_enable", "pq_profile_collect", "pq_profile_names", "pq_lloyd_noalloc", "pq_fit_chunked",
            "softpq_forward", "softpq_backward", "pq_tune_chunked", "pq_tune_clear", "pq_fit_encode_host",
            "pq_test_set_spin_limit", "pq_test_fail_alloc_after", "ivf_build_codes", "ivf_copy_centers",
-           "ivf_clone_empty", "ivf_add", "ivf_merge")
+           "ivf_clone_empty", "ivf_add", "ivf_merge", "pq_fit_chunked_weighted")
 
 
 class PqStats(C.Structure):
@@ -80,6 +80,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "ivf_clone_empty": (i32, [p, C.POINTER(p)]),
         "ivf_add": (i32, [p, p, p, i64, i32, p]),
         "ivf_merge": (i32, [p, p, p]),
+        "pq_fit_chunked_weighted": (i32, [p, C.POINTER(i64), i32, i32, i32, i32, i32, u64, i32, p, p,
+                                          C.POINTER(dbl), p]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -229,10 +231,11 @@ def lloyd_noalloc(X: torch.Tensor, init: torch.Tensor, iters: int, out: torch.Te
 
 
 def fit_chunked(X: torch.Tensor, chunk_offsets, M: int, Ks: int = 256, iters: int = 20, seed: int = 0,
-                prec: str = "fp32", want_rmse: bool = True):
+                prec: str = "fp32", want_rmse: bool = True, weighted: bool = False):
     """Divide-and-conquer PQ (Sec. 3): per-chunk fits, pooled codewords, global refit, global encode.
 
-    ``chunk_offsets`` is a host sequence of n_chunks + 1 row offsets.  Returns
+    ``chunk_offsets`` is a host sequence of n_chunks + 1 row offsets.  ``weighted`` weights each
+    pooled codeword by its member count in its chunk's last update.  Returns
     (global codebooks [M][Ks][D/M], codes [N][M] uint8, RMSE or None).
     """
     px = _need(X, torch.float32, 2, "X")
@@ -245,9 +248,9 @@ def fit_chunked(X: torch.Tensor, chunk_offsets, M: int, Ks: int = 256, iters: in
     codes = torch.empty((N, M), dtype=torch.uint8, device=X.device)
     r = C.c_double(0.0)
     with torch.cuda.device(X.device):
-        _check(_lib.pq_fit_chunked(px, off, n_chunks, D, M, Ks, iters, seed & (2**64 - 1), PREC[prec],
-                                   C.c_void_p(cb.data_ptr()), C.c_void_p(codes.data_ptr()),
-                                   C.byref(r) if want_rmse else None, _stream(X)))
+        fn = _lib.pq_fit_chunked_weighted if weighted else _lib.pq_fit_chunked
+        _check(fn(px, off, n_chunks, D, M, Ks, iters, seed & (2**64 - 1), PREC[prec], C.c_void_p(cb.data_ptr()),
+                  C.c_void_p(codes.data_ptr()), C.byref(r) if want_rmse else None, _stream(X)))
     return cb, codes, (r.value if want_rmse else None)
 
 

@@ -50,6 +50,19 @@ def test_chunked_matches_oracle(pq, case, prec):
     assert np.array_equal(pq.encode(dev(X), dev(gC), prec=prec).cpu().numpy(), codes_ref)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_chunked_weighted_matches_oracle(pq, case, prec):
+    """The weighted centroid dataset (pooled codewords weighted by their member counts)."""
+    X, off, _ = case
+    gC, codes_ref, rmse_ref, local, W = orc.pq_fit_chunked_weighted(X, off, 4, 64, 5, 77)
+    cb, codes, rmse = pq.fit_chunked(dev(X), off.tolist(), 4, 64, iters=5, seed=77, prec=prec, weighted=True)
+    assert_codebooks_close(cb.cpu().numpy(), gC)
+    assert abs(rmse - rmse_ref) <= RMSE_RTOL * rmse_ref
+    assert np.array_equal(pq.encode(dev(X), dev(gC), prec=prec).cpu().numpy(), codes_ref)
+    _, _, rmse_u, _ = orc.pq_fit_chunked(X, off, 4, 64, 5, 77)
+    print(f"RMSE weighted {rmse:.6f}, unweighted {rmse_u:.6f}")
+
+
 def test_chunked_single_chunk_is_plain_fit(pq):
     X = datagen.mixture(9000, 32, 20, "cont", 5151)
     cb, codes, r = pq.fit_chunked(dev(X), [0, 9000], 4, 32, iters=4, seed=3)
