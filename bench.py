@@ -546,10 +546,14 @@ def run_gpu(args):
     if not args.no_search:
         # IVF-ADC search over the same 10M rows: 160 MB of codes, more than L2 holds
         wi = datagen.IVF_10M
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         idx = pqgb.IVFIndex.build(Xd, codes_main, wi.nlist, iters=wi.ivf_iters, seed=wi.coarse_seed, prec=prec)
         torch.cuda.synchronize()
         t_build = time.perf_counter() - t0
+        # the rows are not needed by the search: only the index (codes, ids, lists) stays on the device
+        del Xd
+        torch.cuda.empty_cache()
         Qd = torch.from_numpy(wi.queries()).cuda()
         ms, kern_s, _, _ = _time_search(torch, pqgb, idx, cbs_main, Qd, wi, args.steps, args.warmup, flush)
         off, _, _ = idx.lists()
@@ -565,8 +569,6 @@ def run_gpu(args):
         del Qd
         line["ivf_10m"] = ivf10
         # the medium workload's index (1M x 128, 1,000 components) and its recall
-        del Xd
-        torch.cuda.empty_cache()
         wm = datagen.IVF_MEDIUM
         Xm = torch.from_numpy(wm.data()).cuda()
         cm = pqgb.fit(Xm, wm.m, wm.ks, iters=wm.iters, seed=wm.init_seed, prec=prec)
