@@ -372,6 +372,40 @@ def pq_fit_chunked_weighted(X, chunk_offsets, M: int, Ks: int, iters: int, seed:
     return gC, codes, float(rmse[0]), local, W
 
 
+# -- optimized PQ (Sec. 2.1 "Optimized PQ", Sec. 3.1) -------------------------------------
+
+def opq_rotate(X, R) -> np.ndarray:
+    """Rotated rows X R, computed in FP64 and rounded once to float32."""
+    return (np.asarray(X, dtype=np.float64) @ np.asarray(R, dtype=np.float64)).astype(np.float32)
+
+
+def opq_procrustes(X, Yh) -> np.ndarray:
+    """The orthogonal R minimising ||X R - Yh||_F: R = U V^T for X^T Yh = U S V^T (FP64 SVD)."""
+    A = np.asarray(X, dtype=np.float64).T @ np.asarray(Yh, dtype=np.float64)
+    U, _, Vt = np.linalg.svd(A)
+    return U @ Vt
+
+
+def opq_fit(X, M: int, Ks: int, outer: int, pq_iters: int, seed: int):
+    """Optimized PQ by alternating minimisation (non-parametric OPQ): R = I and a PQ fit of X; then
+    `outer` times: encode the rotated rows, decode, R = Procrustes(X, reconstruction), refit the
+    codebooks on X R from the previous ones (pq_iters Lloyd iterations).  Returns
+    (R [D][D] float32, codebooks, distortion ||X R - Yh||^2 before each rotation update)."""
+    X = _f32(X)
+    D = X.shape[1]
+    R = np.eye(D, dtype=np.float32)
+    Y = opq_rotate(X, R)
+    cb, _ = pq_fit(Y, M, Ks, pq_iters, seed)
+    dist = []
+    for _ in range(outer):
+        Yh = pq_decode(pq_encode(Y, cb), cb)
+        dist.append(float(((Y.astype(np.float64) - Yh) ** 2).sum()))
+        R = opq_procrustes(X, Yh).astype(np.float32)
+        Y = opq_rotate(X, R)
+        cb, _ = pq_fit(Y, M, Ks, pq_iters, 0, init=cb)
+    return R, cb, dist
+
+
 # -- soft-assignment refinement ----------------------------------------------------
 
 def softpq_forward(X, codebooks, tau: float) -> float:

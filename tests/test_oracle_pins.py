@@ -510,3 +510,41 @@ def test_chunked_weighted_decomposes_into_weighted_fits():
     assert np.array_equal(codes, orc.pq_encode(X, want))
     assert r == orc.pq_rmse(X, codes, want)
     print("RMSE weighted", r, "unweighted", ru)
+
+
+# -- optimized PQ ------------------------------------------------------------------------------
+
+def _random_rotation(d, seed):
+    q, r = np.linalg.qr(np.random.default_rng(seed).standard_normal((d, d)))
+    return q * np.sign(np.diag(r))
+
+
+def test_opq_procrustes_recovers_a_known_rotation():
+    X = datagen.mixture(2000, 16, 8, "cont", 70).astype(np.float64)
+    Q = _random_rotation(16, 71)
+    R = orc.opq_procrustes(X, X @ Q)
+    np.testing.assert_allclose(R, Q, atol=1e-10)
+    # and it minimises ||X R - Y|| over rotations: no random rotation does better
+    Y = X @ Q + 0.05 * np.random.default_rng(72).standard_normal(X.shape)
+    R = orc.opq_procrustes(X, Y)
+    best = np.linalg.norm(X @ R - Y)
+    for s in range(20):
+        assert np.linalg.norm(X @ _random_rotation(16, 100 + s) - Y) >= best
+    np.testing.assert_allclose(R @ R.T, np.eye(16), atol=1e-12)
+
+
+def test_opq_fit_distortion_never_rises_and_zero_rounds_is_plain_pq():
+    # rows with correlated dimensions, where a rotation helps PQ
+    base = datagen.mixture(4000, 16, 12, "cont", 73).astype(np.float64)
+    X = (base @ _random_rotation(16, 74) * np.linspace(2.0, 0.2, 16)).astype(np.float32)
+    R0, cb0, _ = orc.opq_fit(X, 4, 16, 0, 5, 75)
+    assert np.array_equal(R0, np.eye(16, dtype=np.float32))
+    ref, _ = orc.pq_fit(X, 4, 16, 5, 75)
+    assert np.array_equal(cb0, ref)
+    R, cb, dist = orc.opq_fit(X, 4, 16, 6, 3, 75)
+    assert np.all(np.diff(dist) <= 1e-6 * dist[0])
+    np.testing.assert_allclose(R.astype(np.float64) @ R.T, np.eye(16), atol=1e-5)
+    Y = orc.opq_rotate(X, R)
+    r_opq = orc.pq_rmse(Y, orc.pq_encode(Y, cb), cb)
+    r_pq = orc.pq_rmse(X, orc.pq_encode(X, ref), ref)
+    assert r_opq < r_pq  # the rotation lowers the reconstruction error on correlated data
