@@ -93,8 +93,9 @@ typedef struct pq_stats {
  * replaces every codeword by the mean of its members; a codeword without
  * members keeps its value.  The member sums are exact integer sums of the
  * residuals x - c in a fixed-point format scaled to the codebook (each element's
- * quantisation error below 2^-(62 - 2b) of twice the largest codeword norm about
- * the codeword mean, b = bit length of the rows one block or CTA handles), plus
+ * quantisation error below 2^-(qb+1) of twice the largest codeword norm about
+ * the codeword mean, qb = min(30, 61 - 2b), b = bit length of the rows one block
+ * or CTA handles), plus
  * FP32 sums of the rare residuals beyond that format; blocks are combined in
  * int64 and the mean is taken in float-float (compensated FP32) arithmetic, so
  * no FP64 arithmetic is involved and the result does not depend on the order of
@@ -214,6 +215,27 @@ int pq_fit_chunked(const float *X, const int64_t *chunk_offsets, int32_t n_chunk
 int pq_fit_chunked_weighted(const float *X, const int64_t *chunk_offsets, int32_t n_chunks, int32_t D, int32_t M,
                             int32_t Ks, int32_t iters, uint64_t seed, int32_t prec, float *codebooks, uint8_t *codes,
                             double *rmse, void *stream);
+
+/*
+ * Optimized PQ (Sec. 2.1 names it; Sec. 3.1: NanoPQ's "PQ and Optimized PQ"): an
+ * orthogonal rotation R of the rows learned jointly with the PQ codebooks of the rotated
+ * rows, by alternating minimisation of ||X R - decode(encode(X R))||^2.
+ * opq_fit -- R = I and codebooks = pq_fit(X, seed, pq_iters); then `outer` times: encode and
+ *   decode X R, set R to the Procrustes solution of (X, reconstruction), refit the codebooks
+ *   on X R from the previous ones (pq_iters Lloyd iterations).  Outputs R [D][D] (row-major;
+ *   a row x maps to x R) and codebooks [M][Ks][Ds] of X R.  Synchronizes.  Scratch: about
+ *   2*N*D*4 + N*M bytes.  Codes, indexes and queries then use rotated rows (opq_rotate).
+ * opq_rotate -- Y [N][D] = X R in FP32 (every output summed in the same k order); Y must not
+ *   alias X.
+ * opq_procrustes -- R = U V^T for X^T Y = U S V^T, the orthogonal R minimising ||X R - Y||_F:
+ *   X^T Y on the device (FP32 products over 1,024-row ranges, added in float-float), its SVD
+ *   on the host in FP64 (one-sided Jacobi).  Synchronizes.
+ * D <= 1024 for all three.
+ */
+int opq_fit(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, int32_t outer, int32_t pq_iters,
+            uint64_t seed, int32_t prec, float *R, float *codebooks, void *stream);
+int opq_rotate(const float *X, int64_t N, int32_t D, const float *R, float *Y, void *stream);
+int opq_procrustes(const float *X, const float *Y, int64_t N, int32_t D, float *R, void *stream);
 
 /*
  * softpq_forward / softpq_backward -- soft-assignment reconstruction loss for

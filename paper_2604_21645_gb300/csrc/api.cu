@@ -881,6 +881,61 @@ int ivf_merge(ivf_index *dst, const ivf_index *src, void *stream)
     return merge_into(dst, src->offsets, src->ids, src->codes, src->N, static_cast<cudaStream_t>(stream));
 }
 
+int opq_rotate(const float *X, int64_t N, int32_t D, const float *R, float *Y, void *stream)
+{
+    g_msg[0] = 0;
+    if (!X || !R || !Y) return fail(PQ_EINVAL, "null pointer");
+    if (N < 0 || D < 1 || D > 1024) return fail(PQ_EINVAL, "need N >= 0 and 1 <= D <= 1024");
+    if (X == Y) return fail(PQ_EINVAL, "Y must not alias X");
+    return launch_rotate(X, N, D, R, Y, static_cast<cudaStream_t>(stream));
+}
+
+int opq_procrustes(const float *X, const float *Y, int64_t N, int32_t D, float *R, void *stream)
+{
+    g_msg[0] = 0;
+    if (!X || !Y || !R) return fail(PQ_EINVAL, "null pointer");
+    if (N < 1 || D < 1 || D > 1024) return fail(PQ_EINVAL, "need N >= 1 and 1 <= D <= 1024");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Scratch ws(s);
+    PQ_TRY(run_procrustes(X, Y, N, D, R, ws, s));
+    return ws.status;
+}
+
+int opq_fit(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks, int32_t outer, int32_t pq_iters,
+            uint64_t seed, int32_t prec, float *R, float *codebooks, void *stream)
+{
+    g_msg[0] = 0;
+    PQ_TRY(check_pq_shape(N, D, M, Ks, true));
+    PQ_TRY(check_prec(prec));
+    if (!X || !R || !codebooks) return fail(PQ_EINVAL, "null pointer");
+    if (!aligned16(X) || !aligned16(codebooks)) return fail(PQ_EINVAL, "X and codebooks must be 16-byte aligned");
+    if (outer < 0 || pq_iters < 0 || pq_iters > PQ_STATS_MAX_ITERS) return fail(PQ_EINVAL, "bad iteration counts");
+    if (D > 1024) return fail(PQ_ENOTSUP, "opq_fit supports D <= 1024");
+    if (prec == PQ_PREC_BF16 && !tc_pass_supported(D, M, Ks))
+        return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and M even");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Scratch ws(s);
+    float *Y = ws.get<float>((size_t)N * D);
+    float *Yh = ws.get<float>((size_t)N * D);
+    uint8_t *codes = ws.get<uint8_t>((size_t)N * M);
+    if (ws.status) return ws.status;
+    // R = I, codebooks: the PQ fit of X itself
+    std::vector<float> eye((size_t)D * D, 0.0f);
+    for (int i = 0; i < D; ++i) eye[(size_t)i * D + i] = 1.0f;
+    PQ_TRY_CUDA(cudaMemcpyAsync(R, eye.data(), eye.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    PQ_TRY_CUDA(cudaMemcpyAsync(Y, X, (size_t)N * D * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    PQ_TRY(pq_fit(Y, N, D, M, Ks, pq_iters, seed, prec, nullptr, codebooks, nullptr, stream));
+    for (int t = 0; t < outer; ++t) {
+        PQ_TRY(pq_encode(Y, N, D, M, Ks, codebooks, prec, codes, nullptr, nullptr, stream));
+        PQ_TRY(launch_decode_codes(codes, codebooks, N, D, M, Ks, Yh, s));
+        PQ_TRY(run_procrustes(X, Yh, N, D, R, ws, s));
+        PQ_TRY(launch_rotate(X, N, D, R, Y, s));
+        PQ_TRY(pq_fit(Y, N, D, M, Ks, pq_iters, 0, prec, codebooks, codebooks, nullptr, stream));
+    }
+    PQ_TRY_CUDA(cudaStreamSynchronize(s));  // the host identity matrix above is read asynchronously
+    return ws.status;
+}
+
 int ivf_copy_centers(const ivf_index *index, uint8_t *centers, void *stream)
 {
     if (!index || !centers) return fail(PQ_EINVAL, "null pointer");

@@ -160,15 +160,15 @@ __device__ __forceinline__ void ll_to_ff(long long v, float &hi, float &lo)
 // Each member adds its residual r = x - c_code.  An element becomes the integer
 // q = rint(r * 2^F) and is added into a block's shared sums as two int32 parts,
 // q >> L and q & (2^L - 1); with at most 2^b rows per block (b = bit length of
-// the row bound), L = 31 - b keeps the low sum below 2^31 and |q| < 2^(61 - 2b)
-// keeps the high sum below 2^31.  F puts the residual scale r0 at that limit:
-// elements whose magnitude reaches 2^(61 - 2b - F) (beyond r0) go to an FP32 sum
+// the row bound), L = 31 - b keeps the low sum below 2^31 and |q| < 2^qb,
+// qb = min(30, 61 - 2b), keeps the high sum below 2^31 and q an int32.  F puts the
+// residual scale r0 at that limit: elements beyond r0 go to an FP32 sum
 // instead.  The integer sums do not depend on the order of the additions; each
 // block writes hi * 2^L + lo as one int64 per (subspace, codeword, dimension),
 // and the finalise kernel adds the blocks in int64 (exact), converts the total to
 // a float-float value, adds the FP32 sums with TwoSum and moves the codeword by
 // the float-float mean residual.  An element's quantisation error is at most
-// 2^-(F+1), i.e. 2^-(62 - 2b) of r0 (rows per block of 2^16: 2^-30 of r0).
+// 2^-(F+1), i.e. 2^-(qb+1) of r0 (rows per block of 2^16: 2^-30 of r0).
 // ---------------------------------------------------------------------------
 struct FixFmt {
     int L, F;
@@ -180,7 +180,7 @@ __host__ __device__ __forceinline__ FixFmt fix_format(int64_t rows, float r0)
     while (b < 62 && ((int64_t)1 << b) <= rows) ++b;  // bit length of the row bound
     FixFmt f;
     f.L = 31 - b;
-    const int qb = 61 - 2 * b;  // |q| < 2^qb
+    const int qb = (61 - 2 * b) < 30 ? (61 - 2 * b) : 30;  // |q| < 2^qb, and q fits an int32
     int e = 0;
     (void)frexpf(r0 > 0.0f ? r0 : 1.0f, &e);  // r0 < 2^e
     f.F = qb - e;

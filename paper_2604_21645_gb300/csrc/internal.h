@@ -150,6 +150,12 @@ int launch_merge_lists(const int64_t *a_off, const int64_t *a_ids, const uint8_t
                        int64_t b_shift, int nlist, int M, int64_t *out_off, int64_t *out_ids, uint8_t *out_codes,
                        cudaStream_t s);
 
+// ---- optimized PQ (opq.cu) -------------------------------------------------
+// Y [N][D] = X [N][D] R [D][D] (FP32, every output summed in k order)
+int launch_rotate(const float *X, int64_t N, int D, const float *R, float *Y, cudaStream_t s);
+// R_out [D][D] (device) = the orthogonal R minimising ||X R - Y||_F; synchronizes the stream
+int run_procrustes(const float *X, const float *Y, int64_t N, int D, float *R_out, Scratch &ws, cudaStream_t s);
+
 // ---- chunked divide and conquer (chunked.cu) -------------------------------
 // weighted: each pooled codeword carries its member count in its chunk's last update, and the
 // global model is the weighted fit of the pooled codewords

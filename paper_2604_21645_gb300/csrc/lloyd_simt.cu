@@ -216,9 +216,9 @@ __global__ void __launch_bounds__(kThreads) pq_pass_f32_kernel(const PqPass a, c
                 if (!big) {
 #pragma unroll
                     for (int j = 0; j < DS; ++j) {
-                        const long long q = __float2ll_rn(__fmul_rn(x[j] - cb[code * DS + j], fx.scale));
-                        atomicAdd(acch + o + j, (int)(q >> fx.L));
-                        atomicAdd(accl + o + j, (int)(q & ((1LL << fx.L) - 1)));
+                        const int q = __float2int_rn(__fmul_rn(x[j] - cb[code * DS + j], fx.scale));
+                        atomicAdd(acch + o + j, q >> fx.L);
+                        atomicAdd(accl + o + j, q & ((1 << fx.L) - 1));
                     }
                 } else {
 #pragma unroll

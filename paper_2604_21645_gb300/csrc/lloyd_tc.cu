@@ -720,19 +720,19 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
                 }
                 if (fit) {
                     const int o = (g * KSMAX + code) * ACC_STRIDE;
-                    long long q[DS];
+                    int q[DS];
                     bool big = false;
 #pragma unroll
                     for (int d = 0; d < DS; ++d) {
                         const float t = __fmul_rn(res[d], fx.scale);
                         big |= !(fabsf(t) < fx.lim);
-                        q[d] = __float2ll_rn(t);
+                        q[d] = __float2int_rn(t);
                     }
                     if (!big) {
 #pragma unroll
                         for (int d = 0; d < DS; ++d) {
-                            atomicAdd(acch + o + d, (int)(q[d] >> fx.L));
-                            atomicAdd(accl + o + d, (int)(q[d] & ((1LL << fx.L) - 1)));
+                            atomicAdd(acch + o + d, q[d] >> fx.L);
+                            atomicAdd(accl + o + d, q[d] & ((1 << fx.L) - 1));
                         }
                     } else {
 #pragma unroll

@@ -25,7 +25,8 @@ EXPORTS = ("pq_fit", "pq_init_kmeanspp", "pq_encode", "pq_decode_rmse", "ivf_bui
            "pq_profile_enable", "pq_profile_collect", "pq_profile_names", "pq_lloyd_noalloc", "pq_fit_chunked",
            "softpq_forward", "softpq_backward", "pq_tune_chunked", "pq_tune_clear", "pq_fit_encode_host",
            "pq_test_set_spin_limit", "pq_test_fail_alloc_after", "ivf_build_codes", "ivf_copy_centers",
-           "ivf_clone_empty", "ivf_add", "ivf_merge", "pq_fit_chunked_weighted")
+           "ivf_clone_empty", "ivf_add", "ivf_merge", "pq_fit_chunked_weighted", "opq_fit", "opq_rotate",
+           "opq_procrustes")
 
 
 class PqStats(C.Structure):
@@ -82,6 +83,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "ivf_merge": (i32, [p, p, p]),
         "pq_fit_chunked_weighted": (i32, [p, C.POINTER(i64), i32, i32, i32, i32, i32, u64, i32, p, p,
                                           C.POINTER(dbl), p]),
+        "opq_fit": (i32, [p, i64, i32, i32, i32, i32, i32, u64, i32, p, p, p]),
+        "opq_rotate": (i32, [p, i64, i32, p, p, p]),
+        "opq_procrustes": (i32, [p, p, i64, i32, p, p]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -252,6 +256,42 @@ def fit_chunked(X: torch.Tensor, chunk_offsets, M: int, Ks: int = 256, iters: in
         _check(fn(px, off, n_chunks, D, M, Ks, iters, seed & (2**64 - 1), PREC[prec], C.c_void_p(cb.data_ptr()),
                   C.c_void_p(codes.data_ptr()), C.byref(r) if want_rmse else None, _stream(X)))
     return cb, codes, (r.value if want_rmse else None)
+
+
+def opq_fit(X: torch.Tensor, M: int, Ks: int = 256, outer: int = 5, pq_iters: int = 5, seed: int = 0,
+            prec: str = "fp32"):
+    """Optimized PQ: (R [D][D], codebooks [M][Ks][D/M]) with the codebooks those of X R."""
+    px = _need(X, torch.float32, 2, "X")
+    N, D = X.shape
+    R = torch.empty((D, D), dtype=torch.float32, device=X.device)
+    cb = torch.empty((M, Ks, D // M), dtype=torch.float32, device=X.device)
+    with torch.cuda.device(X.device):
+        _check(_lib.opq_fit(px, N, D, M, Ks, outer, pq_iters, seed & (2**64 - 1), PREC[prec],
+                            C.c_void_p(R.data_ptr()), C.c_void_p(cb.data_ptr()), _stream(X)))
+    return R, cb
+
+
+def opq_rotate(X: torch.Tensor, R: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    """X R (rows rotated into the space the OPQ codebooks quantize)."""
+    px = _need(X, torch.float32, 2, "X")
+    pr = _need(R, torch.float32, 2, "R")
+    if out is None:
+        out = torch.empty_like(X)
+    po = _need(out, torch.float32, 2, "out")
+    with torch.cuda.device(X.device):
+        _check(_lib.opq_rotate(px, X.shape[0], X.shape[1], pr, po, _stream(X)))
+    return out
+
+
+def opq_procrustes(X: torch.Tensor, Y: torch.Tensor) -> torch.Tensor:
+    """The orthogonal R minimising ||X R - Y||_F."""
+    px = _need(X, torch.float32, 2, "X")
+    py = _need(Y, torch.float32, 2, "Y")
+    D = X.shape[1]
+    R = torch.empty((D, D), dtype=torch.float32, device=X.device)
+    with torch.cuda.device(X.device):
+        _check(_lib.opq_procrustes(px, py, X.shape[0], D, C.c_void_p(R.data_ptr()), _stream(X)))
+    return R
 
 
 def softpq_forward(X: torch.Tensor, codebooks: torch.Tensor, tau: float, out: torch.Tensor | None = None):

@@ -14,7 +14,7 @@ LIB = os.path.join(ROOT, "paper_2604_21645_gb300", "libpqgb.so")
 def declared():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b((?:pq|ivf|softpq)_[a-z_0-9]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b((?:pq|ivf|softpq|opq)_[a-z_0-9]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
