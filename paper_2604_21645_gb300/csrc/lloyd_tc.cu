@@ -19,8 +19,9 @@
 //
 // Decision.  The epilogue reads each row's 256 scores from TMEM in chunks of
 // 32 (each load also returns the chunk's maximum, tcgen05.ld.red), keeps the
-// eight chunk maxima and the values of the best chunk, and accepts the argmax
-// when no other score lies within twice the error bound of it.  For the other rows (about 0.2% on clustered data) every codeword that
+// eight chunk maxima and, in registers, the values of the best chunk, and
+// accepts the argmax when no other score lies within twice the error bound of
+// it.  For the other rows (about 0.2% on clustered data) every codeword that
 // may be the nearest -- the saved chunk's scores within the bound, and all
 // codewords of any other chunk whose maximum reaches it -- is re-ranked exactly
 // from the FP32 codebook copy in shared memory: FP32 direct differences, then
@@ -65,7 +66,7 @@ constexpr int DS = 8;       // subspace width
 constexpr int NXS = 5;      // X stages
 constexpr int NAS = 2;      // A stages
 // Warps per block must keep ceil(warps / 4) * 32 * registers within one SM sub-partition's
-// 16K registers: 12 warps leave room for the epilogue's double-buffered TMEM loads.
+// 16K registers: 12 warps leave room for the epilogue's loaded chunk and its saved best chunk.
 constexpr int kOpWarps = 1;                         // operand warps
 constexpr int kOpRows = TM / (32 * kOpWarps);       // rows per operand thread
 constexpr int kThreads = 96 + 32 * kOpWarps + 256;  // TMA warp, two MMA warps, operand warps, two epilogue warpgroups
@@ -86,8 +87,7 @@ constexpr int OFF_CBF = OFF_B + G * B_SUB;
 constexpr int ACC_BYTES = G * KSMAX * ACC_STRIDE * 4;
 constexpr int OFF_ACC = OFF_CBF + G * KSMAX * CB_STRIDE * 4;  // int32 [3][G][KSMAX][ACC_STRIDE]: high, low, float
 constexpr int OFF_CNT = OFF_ACC + 3 * ACC_BYTES;
-constexpr int OFF_SV = OFF_CNT + G * KSMAX * 4;        // [256 epilogue threads][32] best-chunk scores
-constexpr int OFF_MISC = OFF_SV + 256 * 32 * 4;
+constexpr int OFF_MISC = OFF_CNT + G * KSMAX * 4;
 constexpr int MISC_BYTES = 512;
 constexpr int SMEM_BYTES = OFF_MISC + MISC_BYTES + 1024;  // + alignment slack
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory of the tensor-core pass exceeds one CTA's limit");
@@ -204,29 +204,10 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
 
-#define TC_LD32(base, v)                                                                                            \
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16," \
-                 "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                             \
-                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]),   \
-                   "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]),         \
-                   "=f"(v[15]), "=f"(v[16]), "=f"(v[17]), "=f"(v[18]), "=f"(v[19]), "=f"(v[20]), "=f"(v[21]),       \
-                   "=f"(v[22]), "=f"(v[23]), "=f"(v[24]), "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]),       \
-                   "=f"(v[29]), "=f"(v[30]), "=f"(v[31])                                                            \
-                 : "r"(base))
+// 32 consecutive columns of this thread's TMEM lane (one row's scores) and, by the load's max
+// reduction, their largest value m, so a chunk's maximum needs no instructions of its own.
 // tcgen05.ld writes its registers asynchronously: the wait names them as in/out operands so that
 // the compiler cannot move a use of the loaded values above it.
-#define TC_WAIT32(v)                                                                                              \
-    asm volatile("tcgen05.wait::ld.sync.aligned;"                                                                 \
-                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]),  \
-                   "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]),         \
-                   "+f"(v[15]), "+f"(v[16]), "+f"(v[17]), "+f"(v[18]), "+f"(v[19]), "+f"(v[20]), "+f"(v[21]),       \
-                   "+f"(v[22]), "+f"(v[23]), "+f"(v[24]), "+f"(v[25]), "+f"(v[26]), "+f"(v[27]), "+f"(v[28]),       \
-                   "+f"(v[29]), "+f"(v[30]), "+f"(v[31])                                                            \
-                 :                                                                                                \
-                 : "memory")
-
-// The same load with a max reduction: m receives the largest of the 32 values this thread loads
-// (one row's 32 consecutive columns), so a chunk's maximum needs no instructions of its own.
 #define TC_LDMAX32(base, v, m)                                                                                      \
     asm volatile("tcgen05.ld.red.sync.aligned.32x32b.x32.max.f32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"  \
                  "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, %32, [%33];"             \
@@ -598,8 +579,6 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
         const float nb_prime = __uint_as_float(bnd[g * 2 + 0]) * (1.0f + 1e-5f);
         const float cb_prime = __uint_as_float(bnd[g * 2 + 1]) * (1.0f + 1e-5f);
         const float *cbg = cbf + g * KSMAX * CB_STRIDE;
-        const int te = tid - kEpi0;
-        float4 *svs = reinterpret_cast<float4 *>(sm + OFF_SV) + te * 8;  // 16-byte pieces swizzled by te & 7
         float sse_s = 0.0f, sse_c = 0.0f;  // Kahan pair
         unsigned rechecks = 0;
         // one format for every CTA of the chunk: the row bound is the busiest CTA's rows
@@ -628,45 +607,37 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
             const float tt = xn + cb_prime;
             const float win = 2.0f * (kC1 * xn * cb_prime + kC2 * nb_prime + 1e-13f * tt * tt);
 
-            // scores, two halves of 128 codewords, each in its own TMEM buffer
+            // scores, two halves of 128 codewords, each in its own TMEM buffer.  A load returns after
+            // ~30 cycles, so chunks are loaded one at a time; the best chunk so far is copied in
+            // registers (a shared-memory copy would put ~2k wavefronts per tile on the shared pipe).
             float best = -FLT_MAX, cm2 = -FLT_MAX;
             int bestj = 0;
             float cmx[KSMAX / 32];
-            // chunk j+1 is loaded from TMEM while chunk j is reduced (tcgen05.wait::ld waits for
-            // every outstanding load, so each wait sits after the reduction it overlaps)
+            float sv[32];
             bool ok = __all_sync(0xffffffffu, mbar_wait(bar(MB_MMAF + g * 2 + 0), i & 1, a.err));
             if (!ok) break;
             tc_after_sync();
-            float vb[2][32], mb2[2];
-            TC_LDMAX32(tl, vb[0], mb2[0]);
-            TC_WAITMAX32(vb[0], mb2[0]);
 #pragma unroll
             for (int j = 0; j < KSMAX / 32; ++j) {
-                if (j + 1 == NH / 32) {
+                if (j == NH / 32) {
+                    // every load of the first buffer has completed: hand it back to the MMA warp
+                    tc_before_sync();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar(MB_TFREE + g * 2 + 0));
                     ok = __all_sync(0xffffffffu, mbar_wait(bar(MB_MMAF + g * 2 + 1), i & 1, a.err));
                     if (!ok) break;
                     tc_after_sync();
                 }
-                if (j + 1 < KSMAX / 32) TC_LDMAX32(tl + (uint32_t)((j + 1) * 32), vb[(j + 1) & 1], mb2[(j + 1) & 1]);
-                const float *v = vb[j & 1];
-                const float cm = mb2[j & 1];
+                float v[32], cm;
+                TC_LDMAX32(tl + (uint32_t)(j * 32), v, cm);
+                TC_WAITMAX32(v, cm);
                 cmx[j] = cm;
                 const bool better = cm > best;
                 cm2 = better ? best : fmaxf(cm2, cm);
                 best = better ? cm : best;
                 bestj = better ? j : bestj;
-                if (better) {
 #pragma unroll
-                    for (int c = 0; c < 8; ++c)
-                        svs[c ^ (te & 7)] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
-                }
-                if (j + 1 == NH / 32) {
-                    // every load of the first buffer has completed: hand it back to the MMA warp
-                    tc_before_sync();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(bar(MB_TFREE + g * 2 + 0));
-                }
-                if (j + 1 < KSMAX / 32) TC_WAITMAX32(vb[(j + 1) & 1], mb2[(j + 1) & 1]);
+                for (int c = 0; c < 32; ++c) sv[c] = (j == 0 || better) ? v[c] : sv[c];
             }
             if (!ok) break;
             tc_before_sync();
@@ -675,15 +646,6 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
             // certain when the best chunk holds exactly one score >= theta and no other chunk reaches it;
             // the sum below packs that count (low 6 bits) and the score's position (bits 6..)
             const float theta = best - win;
-            float sv[32];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const float4 t4 = svs[c ^ (te & 7)];
-                sv[4 * c] = t4.x;
-                sv[4 * c + 1] = t4.y;
-                sv[4 * c + 2] = t4.z;
-                sv[4 * c + 3] = t4.w;
-            }
             // four independent partial sums (exact small integers, so the order does not matter)
             float tp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
