@@ -244,7 +244,10 @@ __global__ void __launch_bounds__(kThreads, 1) coarse_tc_kernel(const __grid_con
                                                                  const CoarseTcArgs a)
 {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // aligned by an offset from the shared array itself, so that the compiler keeps every access
+    // below in the shared address space
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem_raw);
+    unsigned char *sm = smem_raw + (((sbase + 1023u) & ~1023u) - sbase);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int D = a.D, KD = D / 16, T = 2 * KD + 1, NB = a.nlist_pad / NBLK, NBOX = D / 32;
     uint64_t *mb = reinterpret_cast<uint64_t *>(sm + OFF_MISC);

@@ -41,7 +41,8 @@
 // warpgroups; thread = row = TMEM lane) own subspace 0 and 1 and two 128-column
 // TMEM buffers each, one per codeword half: the MMA of a half is issued as soon
 // as the epilogue has read the same half of the previous tile, so the tensor
-// core works while the epilogue runs.  All hand-offs are mbarriers; every wait
+// core works while the epilogue runs.  Warpgroup 0 hands part of its registers
+// to the epilogue warpgroups (setmaxnreg).  All hand-offs are mbarriers; every wait
 // is bounded, and a timed-out wait records PQ_ETIMEOUT and lets the CTA unwind
 // (its copies and MMAs waited for, its tensor memory freed).
 #include <cuda.h>
@@ -65,13 +66,21 @@ constexpr int NH = 128;     // codewords per MMA (one TMEM buffer)
 constexpr int DS = 8;       // subspace width
 constexpr int NXS = 5;      // X stages
 constexpr int NAS = 2;      // A stages
-// Warps per block must keep ceil(warps / 4) * 32 * registers within one SM sub-partition's
-// 16K registers: 12 warps leave room for the epilogue's loaded chunk and its saved best chunk.
 constexpr int kOpWarps = 1;                         // operand warps
 constexpr int kOpRows = TM / (32 * kOpWarps);       // rows per operand thread
 constexpr int kThreads = 96 + 32 * kOpWarps + 256;  // TMA warp, two MMA warps, operand warps, two epilogue warpgroups
 constexpr int kOp0 = 96;                            // first operand thread
 constexpr int kEpi0 = kOp0 + 32 * kOpWarps;         // first epilogue thread
+// Registers: the block is launched with kRegLaunch per thread (12 warps fill the register file);
+// warpgroup 0 (TMA, MMA and operand warps) then hands registers over to the two epilogue
+// warpgroups (setmaxnreg), which hold a loaded 32-score chunk and the best chunk so far.
+constexpr int kRegLaunch = 168;
+constexpr int kRegLo = 112;
+constexpr int kRegHi = 192;
+static_assert(kEpi0 == 128, "warpgroup 0 must be exactly the TMA, MMA and operand warps");
+static_assert(128 * kRegLo + 256 * kRegHi <= kThreads * kRegLaunch,
+              "register hand-over exceeds the registers the block is launched with");
+static_assert(kThreads * kRegLaunch <= 65536, "launch registers exceed the SM's register file");
 
 constexpr int XS_BYTES = TM * G * DS * 4;  // 8 KB per stage (rows of 64 B)
 constexpr int A_K16 = TM * 16 * 2;         // 4 KB: 128 rows x K=16 bf16
@@ -337,11 +346,14 @@ __device__ __forceinline__ void decide_exact_warp(bool unsure, float4 v0, float4
     }
 }
 
-__global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUtensorMap tmap,
+__global__ void __maxnreg__(kRegLaunch) pq_pass_tc_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                   const TcArgs a)
 {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // aligned by an offset from the shared array itself, so that the compiler keeps every access
+    // below in the shared address space (shared loads, stores and atomics, not generic ones)
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem_raw);
+    unsigned char *sm = smem_raw + (((sbase + 1023u) & ~1023u) - sbase);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int grp = blockIdx.y, m0 = grp * G;
     const int Ks = a.Ks;
@@ -473,6 +485,8 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
 
     const int n_my = (tiles_c > lb) ? (tiles_c - 1 - lb) / gxc + 1 : 0;
 
+    if (warp < kEpi0 / 32) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegLo));
     if (warp == 0) {
         // ---- producer: TMA loads of the row tiles -----------------------------
         if (lane == 0) {
@@ -518,7 +532,7 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
             mma_commit(bar(MB_DRAIN + g));
             mbar_wait(bar(MB_DRAIN + g), 0, a.err);
         }
-    } else if (warp < kEpi0 / 32) {
+    } else {
         // ---- operand warp: bf16 A operands of both subspaces, rows t + 32 rr
         const int t = tid - kOp0;
         for (int i = 0; i < n_my; ++i) {
@@ -571,7 +585,9 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
             }
             if (!ok) break;
         }
+    }
     } else {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegHi));
         // ---- epilogue warpgroups: thread = row = TMEM lane, warpgroup g = subspace g
         const int g = (tid - kEpi0) >> 7;
         const int r = (warp & 3) * 32 + lane;
@@ -589,18 +605,16 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
             const int64_t row = r0 + (int64_t)(lb + i * gxc) * TM + r;
             if (!__all_sync(0xffffffffu, mbar_wait(bar(MB_FULL + s), (i / NXS) & 1, a.err))) break;
             const float *stage = xs + s * (XS_BYTES / 4);
-            const float4 v0 = *xs_chunk(stage, r, 2 * g);
-            const float4 v1 = *xs_chunk(stage, r, 2 * g + 1);
-            // the stage is not read again: order the reads before the TMA that will refill it
-            fence_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bar(MB_EMPTY + s));
-            const float x[DS] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
             float xx = 0.0f;
+            {
+                const float4 v0 = *xs_chunk(stage, r, 2 * g);
+                const float4 v1 = *xs_chunk(stage, r, 2 * g + 1);
+                const float x[DS] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
-            for (int d = 0; d < DS; ++d) {
-                const float xc = x[d] - mu[g * DS + d];
-                xx = fmaf(xc, xc, xx);
+                for (int d = 0; d < DS; ++d) {
+                    const float xc = x[d] - mu[g * DS + d];
+                    xx = fmaf(xc, xc, xx);
+                }
             }
             // sqrt as x * rsqrt(x): a few ulp, far inside the 1e-5 inflation
             const float xn = (xx > 0.0f ? xx * rsqrtf(xx) : 0.0f) * (1.0f + 1e-5f);
@@ -643,6 +657,14 @@ __global__ void __maxnreg__(168) pq_pass_tc_kernel(const __grid_constant__ CUten
             tc_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive(bar(MB_TFREE + g * 2 + 1));
+            // the row again (not kept in registers across the chunks); the stage is not read again:
+            // order the reads before the TMA that will refill it
+            const float4 v0 = *xs_chunk(stage, r, 2 * g);
+            const float4 v1 = *xs_chunk(stage, r, 2 * g + 1);
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar(MB_EMPTY + s));
+            const float x[DS] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
             // certain when the best chunk holds exactly one score >= theta and no other chunk reaches it;
             // the sum below packs that count (low 6 bits) and the score's position (bits 6..)
             const float theta = best - win;
@@ -806,6 +828,16 @@ int launch_pq_pass_tc(PqPass &p, cudaStream_t s)
     a.chunk_off = p.chunk_off;
     a.chunk_blk = p.chunk_blk;
     PQ_TRY_CUDA(cudaFuncSetAttribute(pq_pass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    // the register hand-over inside the kernel waits for registers the launch must have given it
+    static int launch_regs = -1;
+    if (launch_regs < 0) {
+        cudaFuncAttributes fa;
+        PQ_TRY_CUDA(cudaFuncGetAttributes(&fa, pq_pass_tc_kernel));
+        launch_regs = fa.numRegs;
+    }
+    if (launch_regs * kThreads < 128 * kRegLo + 256 * kRegHi)
+        return fail(PQ_ECUDA, "tensor-core pass built with %d registers per thread, fewer than its register hand-over needs",
+                    launch_regs);
     dim3 grid(p.gx, p.M / G);
     ProfScope ps("pq_pass_tc", s);
     pq_pass_tc_kernel<<<grid, kThreads, SMEM_BYTES, s>>>(map, a);
