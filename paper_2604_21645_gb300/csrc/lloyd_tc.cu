@@ -36,7 +36,7 @@
 // Pipeline (one CTA per SM, a group of 2 subspaces, persistent over row tiles
 // of 128).  Warp 0 issues TMA loads of 128 x 16 float tiles (64B swizzle) into
 // five stages.  Warp 3 (the operand warp) turns each tile into the bf16 A
-// operands of both subspaces (two A stages, so the loads run three tiles ahead).  Warps 1 and 2 issue the MMAs of
+// operands of both subspaces (four A stages).  Warps 1 and 2 issue the MMAs of
 // subspace 0 and 1.  Warps 4-7 and 8-11 (the epilogue
 // warpgroups; thread = row = TMEM lane) own subspace 0 and 1 and two 128-column
 // TMEM buffers each, one per codeword half: the MMA of a half is issued as soon
@@ -65,7 +65,7 @@ constexpr int KSMAX = 256;  // codewords
 constexpr int NH = 128;     // codewords per MMA (one TMEM buffer)
 constexpr int DS = 8;       // subspace width
 constexpr int NXS = 5;      // X stages
-constexpr int NAS = 2;      // A stages
+constexpr int NAS = 4;      // A stages: the operand warp runs up to three tiles ahead of the MMAs
 constexpr int kOpWarps = 1;                         // operand warps
 constexpr int kOpRows = TM / (32 * kOpWarps);       // rows per operand thread
 constexpr int kThreads = 96 + 32 * kOpWarps + 256;  // TMA warp, two MMA warps, operand warps, two epilogue warpgroups
