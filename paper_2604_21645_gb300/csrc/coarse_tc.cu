@@ -1,8 +1,8 @@
 // coarse_tc.cu -- nearest coarse centroid of every row on the tcgen05 tensor
 // cores (the coarse quantizer of the inverted index, Sec. 2.2 / Sec. 3.1).
 //
-// Scores S_l = x'.c'_l - ||c'_l||^2/2 with x' = x - mu, c' = c - mu (mu = mean
-// of the centroids) are accumulated in TMEM over K = 3D + 16 bf16 lanes, the
+// Scores S_l = x'.c'_l - ||c'_l||^2/2 with x' = x - mu, c' = c - mu (mu = the mean
+// of the centroids rounded to integers) are accumulated in TMEM over K = 3D + 16 bf16 lanes, the
 // three-term split of the contraction
 //     x'.c' ~ xh.ch + xl.ch + xh.cl        (x' = xh + xl, c' = ch + cl)
 // plus the folded half norm (-nh - nl against a constant 1).  The error of S
@@ -15,15 +15,15 @@
 // within twice the bound; every other row goes to the FP64 re-check queue
 // (coarse.cu), so the list of every row is exact.
 //
-// Pipeline, one CTA (224 threads) per SM, persistent over 128-row tiles:
-// lane 0 of warp 0 loads the X tile by TMA (128B-swizzled 32-column boxes),
-// lane 0 of warp 2 streams the pre-tiled B operand (8 KB tiles, bulk copies)
-// through an 8-slot ring (each producer in a warp of its own, so one's wait
-// never stalls the other), lane 0 of warp 1 issues M=128 N=256 K=16 MMAs into
-// two TMEM accumulators (256 centroids each), warps 3-6 build the A operand and
-// run the epilogue.  Every wait is bounded.
+// Pipeline, one CTA (384 threads) per SM, persistent over 128-row tiles: lane 0
+// of warp 0 streams the pre-tiled B operand (8 KB tiles, bulk copies) through an
+// 8-slot ring; lane 0 of warp 1 issues M=128 N=256 K=16 MMAs into two TMEM
+// accumulators (256 centroids each); warps 4-7 build the A operand of the next
+// tile (two stages) from rows read straight from global memory; warps 8-11 drain
+// the accumulators and decide.  When no row of a tile has a bf16 low part (integer
+// rows within 256 of the centring), the MMAs of the xl.ch term are skipped: they
+// would add exact zeros.  Every wait is bounded.
 #include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -39,23 +39,30 @@ constexpr int TM = 128;
 constexpr int NBLK = 256;            // centroids per MMA / TMEM accumulator
 constexpr int DMAX = 128;
 constexpr int KDMAX = DMAX / 16;     // K steps of one term
-constexpr int kThreads = 96 + 128;  // X-load warp, MMA warp, B-load warp, epilogue warpgroup
-constexpr int kEpi0 = 96;
+// warp 0: B loads; warp 1: MMA issue; warps 2-3: spare; warps 4-7: A builder; warps 8-11: drain
+constexpr int kThreads = 384;
+constexpr int kBuild0 = 128, kDrain0 = 256;
 constexpr int A_TILE = TM * 16 * 2;  // 4 KB
+constexpr int A_STAGE = (2 * KDMAX + 1) * A_TILE;  // 68 KB: xh tiles, xl tiles, the constant tile
+constexpr int NA = 2;                // A stages
+constexpr int NXN = 4;               // row-norm slots (the builder runs at most 3 tiles ahead of the drain)
 constexpr int B_TILE = NBLK * 16 * 2;  // 8 KB
 constexpr int RING = 8;
-constexpr int XBOX = TM * 32 * 4;    // 16 KB, one 32-column box
-constexpr int OFF_X = 0;                                  // 4 boxes
-constexpr int OFF_A = OFF_X + (DMAX / 32) * XBOX;        // (2*KD + 1) tiles
-constexpr int OFF_RING = OFF_A + (2 * KDMAX + 1) * A_TILE;
-constexpr int OFF_MISC = OFF_RING + RING * B_TILE;
-constexpr int OFF_CMX = OFF_MISC + 1024;                  // [32 chunks][128 rows] chunk maxima
+constexpr int OFF_A = 0;
+constexpr int OFF_RING = OFF_A + NA * A_STAGE;
+constexpr int OFF_MISC = OFF_RING + RING * B_TILE;        // mbarriers, TMEM slot, mu, low-part flags
+constexpr int OFF_XN = OFF_MISC + 1024;                   // [NXN][TM] float: ||x'|| per row
+constexpr int OFF_CMX = OFF_XN + NXN * TM * 4;            // [32 chunks][128 rows] chunk maxima
 constexpr int SMEM_BYTES = OFF_CMX + 32 * TM * 4 + 1024;
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory of one CTA");
 
 // mbarrier slots
-constexpr int MB_XFULL = 0, MB_XEMPTY = 1, MB_AREADY = 2, MB_AFREE = 3, MB_MMA = 4 /*2*/, MB_TFREE = 6 /*2*/,
-              MB_RFULL = 8 /*RING*/, MB_REMPTY = 8 + RING /*RING*/, MB_COUNT = 8 + 2 * RING;
+constexpr int MB_AREADY = 0 /*NA*/, MB_AFREE = 2 /*NA*/, MB_MMA = 4 /*2*/, MB_TFREE = 6 /*2*/,
+              MB_RFULL = 8 /*RING*/, MB_REMPTY = 8 + RING /*RING*/, MB_XNREADY = 8 + 2 * RING /*NXN*/,
+              MB_COUNT = 8 + 2 * RING + NXN;
+constexpr int MISC_TSLOT = 8 * MB_COUNT, MISC_MU = 256, MISC_XLNZ = 768;  // xlnz: [NA][4] int
+static_assert(MISC_TSLOT + 4 <= MISC_MU && MISC_MU + 4 * DMAX <= MISC_XLNZ && MISC_XLNZ + 4 * NA * 4 <= 1024,
+              "misc area overlap");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint32_t a, uint32_t c)
@@ -91,14 +98,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int *err)
         if ((it & 255) == 255 && *(volatile int *)err != 0) return false;
     }
 }
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            dst),
-        "l"(map), "r"(x), "r"(y), "r"(mbar)
-        : "memory");
-}
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar)
 {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -132,24 +131,25 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
-#define TC_LD32(base, v)                                                                                            \
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16," \
-                 "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                             \
+// 32 consecutive columns of this thread's TMEM lane (one row's scores) and, by the load's max
+// reduction, their largest value m.  tcgen05.ld writes its registers asynchronously: the wait
+// names them as in/out operands so that the compiler cannot move a use of the loaded values above it.
+#define TC_LDMAX32(base, v, m)                                                                                      \
+    asm volatile("tcgen05.ld.red.sync.aligned.32x32b.x32.max.f32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"  \
+                 "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, %32, [%33];"             \
                  : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]),   \
                    "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]),         \
                    "=f"(v[15]), "=f"(v[16]), "=f"(v[17]), "=f"(v[18]), "=f"(v[19]), "=f"(v[20]), "=f"(v[21]),       \
                    "=f"(v[22]), "=f"(v[23]), "=f"(v[24]), "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]),       \
-                   "=f"(v[29]), "=f"(v[30]), "=f"(v[31])                                                            \
+                   "=f"(v[29]), "=f"(v[30]), "=f"(v[31]), "=f"(m)                                                   \
                  : "r"(base))
-// tcgen05.ld writes its registers asynchronously: the wait names them as in/out operands so that
-// the compiler cannot move a use of the loaded values above it.
-#define TC_WAIT32(v)                                                                                              \
+#define TC_WAITMAX32(v, m)                                                                                        \
     asm volatile("tcgen05.wait::ld.sync.aligned;"                                                                 \
                  : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]),  \
                    "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]),         \
                    "+f"(v[15]), "+f"(v[16]), "+f"(v[17]), "+f"(v[18]), "+f"(v[19]), "+f"(v[20]), "+f"(v[21]),       \
                    "+f"(v[22]), "+f"(v[23]), "+f"(v[24]), "+f"(v[25]), "+f"(v[26]), "+f"(v[27]), "+f"(v[28]),       \
-                   "+f"(v[29]), "+f"(v[30]), "+f"(v[31])                                                            \
+                   "+f"(v[29]), "+f"(v[30]), "+f"(v[31]), "+f"(m)                                                   \
                  :                                                                                                \
                  : "memory")
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
@@ -162,8 +162,10 @@ __device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(_
 // ---- preparation: centring mean, bounds, tiled B operand -------------------
 // Bp layout: [blk][tile][256 rows][16 bf16] core-matrix tiles; tile 2k = ch of K step k,
 // 2k+1 = cl of K step k, 2*KD = the half-norm tile.
-// mu = mean of the centroids (the centring of the scores; any fixed value keeps the decisions
-// exact).  Block of 1024 threads: 8 groups of lists per dimension, added in a fixed order.
+// mu = mean of the centroids rounded to an integer (the centring of the scores; any fixed value
+// keeps the decisions exact, and an integer one keeps integer-valued rows of magnitude <= 256
+// exact in bf16 after centring, so that their low parts vanish).  Block of 1024 threads: 8 groups
+// of lists per dimension, added in a fixed order.
 constexpr int kMuGroups = 8;
 __global__ void __launch_bounds__(1024) coarse_mu_kernel(const float *C, int nlist, int D, float *mu)
 {
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(1024) coarse_mu_kernel(const float *C, int nli
     if (g == 0 && j < D) {
         float t = 0.0f;
         for (int q = 0; q < kMuGroups; ++q) t += part[q][j];
-        mu[j] = t / (float)nlist;
+        mu[j] = rintf(t / (float)nlist);
     }
 }
 
@@ -227,6 +229,7 @@ __global__ void coarse_prep_kernel(const float *C, int nlist, int nlist_pad, int
 struct CoarseTcArgs {
     int64_t N;
     int D, nlist, nlist_pad, tiles;
+    const float *X;
     const unsigned char *Bp;
     const float *mu;
     const unsigned *maxbits;
@@ -240,8 +243,7 @@ struct CoarseTcArgs {
 // NBT > 0: at most NBT centroid blocks (NBT * 8 chunks of 32 <= 32); the chunk maxima are kept
 // and an uncertain row is queued with the mask of chunks that can hold its nearest centroid.
 template <int NBT>
-__global__ void __launch_bounds__(kThreads, 1) coarse_tc_kernel(const __grid_constant__ CUtensorMap tmap,
-                                                                 const CoarseTcArgs a)
+__global__ void __launch_bounds__(kThreads, 1) coarse_tc_kernel(const CoarseTcArgs a)
 {
     extern __shared__ unsigned char smem_raw[];
     // aligned by an offset from the shared array itself, so that the compiler keeps every access
@@ -249,11 +251,14 @@ __global__ void __launch_bounds__(kThreads, 1) coarse_tc_kernel(const __grid_con
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem_raw);
     unsigned char *sm = smem_raw + (((sbase + 1023u) & ~1023u) - sbase);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int D = a.D, KD = D / 16, T = 2 * KD + 1, NB = a.nlist_pad / NBLK, NBOX = D / 32;
+    const int D = a.D, KD = D / 16, T = 2 * KD + 1, NB = a.nlist_pad / NBLK;
     uint64_t *mb = reinterpret_cast<uint64_t *>(sm + OFF_MISC);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + OFF_MISC + 8 * MB_COUNT);
-    float *smu = reinterpret_cast<float *>(sm + OFF_MISC + 256);
-    unsigned char *xs = sm + OFF_X;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + OFF_MISC + MISC_TSLOT);
+    float *smu = reinterpret_cast<float *>(sm + OFF_MISC + MISC_MU);
+    // per builder warp and A stage: does the tile's A operand have a nonzero low part?  When none
+    // does, the MMAs of xl.ch (exact zeros) are skipped, which leaves every score unchanged
+    volatile int *xlnz = reinterpret_cast<volatile int *>(sm + OFF_MISC + MISC_XLNZ);
+    float *xn_s = reinterpret_cast<float *>(sm + OFF_XN);
     unsigned char *aop = sm + OFF_A;
     unsigned char *ring = sm + OFF_RING;
 
@@ -261,7 +266,9 @@ __global__ void __launch_bounds__(kThreads, 1) coarse_tc_kernel(const __grid_con
     if (tid == 0) {
         for (int i = 0; i < MB_COUNT; ++i) {
             uint32_t c = 1;
-            if (i == MB_XEMPTY || i == MB_AREADY || i == MB_TFREE || i == MB_TFREE + 1) c = 4;
+            if ((i >= MB_AREADY && i < MB_AREADY + NA) || i == MB_TFREE || i == MB_TFREE + 1 ||
+                (i >= MB_XNREADY && i < MB_XNREADY + NXN))
+                c = 4;
             mbar_init(smem_u32(mb + i), c);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -278,21 +285,7 @@ __global__ void __launch_bounds__(kThreads, 1) coarse_tc_kernel(const __grid_con
 
     if (warp == 0) {
         if (lane == 0) {
-            // X tiles: NBOX TMA boxes of 128 rows x 32 floats
-            int issued = 0;
-            for (int i = 0; i < n_my; ++i) {
-                if (i >= 1 && !mbar_wait(smem_u32(mb + MB_XEMPTY), (i - 1) & 1, a.err)) break;
-                mbar_expect_tx(smem_u32(mb + MB_XFULL), NBOX * XBOX);
-                const int y = ((int)blockIdx.x + i * (int)gridDim.x) * TM;
-                for (int bx = 0; bx < NBOX; ++bx)
-                    tma_load_2d(smem_u32(xs + bx * XBOX), &tmap, bx * 32, y, smem_u32(mb + MB_XFULL));
-                ++issued;
-            }
-            if (issued) mbar_wait(smem_u32(mb + MB_XFULL), (issued - 1) & 1, a.err);
-        }
-    } else if (warp == 2) {
-        if (lane == 0) {
-            // B tiles in MMA order through the ring (a warp of its own: its waits never hold up the X loads)
+            // B tiles in MMA order through the ring (a warp of its own)
             int z = 0;
             bool ok = true;
             for (int i = 0; i < n_my && ok; ++i)
@@ -311,63 +304,85 @@ __global__ void __launch_bounds__(kThreads, 1) coarse_tc_kernel(const __grid_con
                 mbar_wait(smem_u32(mb + MB_RFULL + q % RING), (q / RING) & 1, a.err);
         }
     } else if (warp == 1) {
+        // ---- MMA issue.  One thread issues every MMA, so its own instructions between two MMAs
+        // bound the tensor pipe: descriptors are base values plus offsets, the ring position is a
+        // running counter, and the wait for a B tile is a plain poll.
         if (lane == 0) {
-            int z = 0;
+            const uint64_t dA0 = smem_desc(smem_u32(aop)), dB0 = smem_desc(smem_u32(ring));
+            const uint32_t rfull0 = smem_u32(mb + MB_RFULL), rempty0 = smem_u32(mb + MB_REMPTY);
+            int slot = 0;
+            uint32_t ph = 0;
             bool ok = true;
+            // the next B tile has landed (bounded poll)
+            auto ring_wait = [&]() -> bool {
+                for (unsigned it = 0; !mbar_try(rfull0 + 8 * slot, ph); ++it) {
+                    if (it > kSpinLimit) {
+                        atomicCAS(a.err, 0, PQ_ETIMEOUT);
+                        return false;
+                    }
+                    if ((it & 255) == 255 && *(volatile int *)a.err != 0) return false;
+                }
+                return true;
+            };
+            auto ring_next = [&]() {
+                mma_commit(rempty0 + 8 * slot);
+                if (++slot == RING) {
+                    slot = 0;
+                    ph ^= 1u;
+                }
+            };
             for (int i = 0; i < n_my && ok; ++i) {
-                if (!mbar_wait(smem_u32(mb + MB_AREADY), i & 1, a.err)) break;
+                const int as = i % NA;
+                if (!mbar_wait(smem_u32(mb + MB_AREADY + as), (i / NA) & 1, a.err)) break;
                 tc_after_sync();
+                const bool xl = (xlnz[as * 4 + 0] | xlnz[as * 4 + 1] | xlnz[as * 4 + 2] | xlnz[as * 4 + 3]) != 0;
+                const uint64_t dA = dA0 + (uint64_t)((as * A_STAGE) >> 4);
                 for (int b = 0; b < NB && ok; ++b) {
                     const int v = i * NB + b, buf = v & 1, u = v >> 1;
                     if (u >= 1 && !mbar_wait(smem_u32(mb + MB_TFREE + buf), (u - 1) & 1, a.err)) { ok = false; break; }
                     tc_after_sync();
                     const uint32_t d = tmem + (uint32_t)(buf * NBLK);
-                    for (int t = 0; t < T; ++t, ++z) {
-                        const int slot = z % RING, use = z / RING;
-                        if (!mbar_wait(smem_u32(mb + MB_RFULL + slot), use & 1, a.err)) { ok = false; break; }
-                        tc_after_sync();
-                        const uint64_t db = smem_desc(smem_u32(ring + slot * B_TILE));
-                        if (t == 2 * KD) {
-                            mma_bf16(d, smem_desc(smem_u32(aop + 2 * KD * A_TILE)), db, 1u);  // half norm
-                        } else if ((t & 1) == 0) {
-                            const int k = t >> 1;  // ch: against xh and xl
-                            mma_bf16(d, smem_desc(smem_u32(aop + k * A_TILE)), db, t == 0 ? 0u : 1u);
-                            mma_bf16(d, smem_desc(smem_u32(aop + (KD + k) * A_TILE)), db, 1u);
-                        } else {
-                            const int k = t >> 1;  // cl: against xh
-                            mma_bf16(d, smem_desc(smem_u32(aop + k * A_TILE)), db, 1u);
-                        }
-                        mma_commit(smem_u32(mb + MB_REMPTY + slot));
+                    // B tiles in order ch_0, cl_0, ch_1, cl_1, ..., the half-norm tile
+                    for (int k = 0; k < KD; ++k) {
+                        if (!ring_wait()) { ok = false; break; }
+                        const uint64_t dbh = dB0 + (uint64_t)((slot * B_TILE) >> 4);
+                        mma_bf16(d, dA + (uint64_t)((k * A_TILE) >> 4), dbh, k == 0 ? 0u : 1u);  // xh.ch
+                        if (xl) mma_bf16(d, dA + (uint64_t)(((KD + k) * A_TILE) >> 4), dbh, 1u);  // xl.ch
+                        ring_next();
+                        if (!ring_wait()) { ok = false; break; }
+                        mma_bf16(d, dA + (uint64_t)((k * A_TILE) >> 4), dB0 + (uint64_t)((slot * B_TILE) >> 4), 1u);  // xh.cl
+                        ring_next();
                     }
-                    if (!ok) break;
+                    if (!ok || !ring_wait()) { ok = false; break; }
+                    mma_bf16(d, dA + (uint64_t)((2 * KD * A_TILE) >> 4), dB0 + (uint64_t)((slot * B_TILE) >> 4), 1u);  // -n'
+                    ring_next();
                     mma_commit(smem_u32(mb + MB_MMA + buf));
                 }
                 if (!ok) break;
-                mma_commit(smem_u32(mb + MB_AFREE));
+                mma_commit(smem_u32(mb + MB_AFREE + as));
             }
         }
-    } else if (warp >= kEpi0 / 32) {
-        const int q = warp & 3;  // TMEM lane quadrant of this warp
-        const int r = q * 32 + lane;
-        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
-        const float nmax = __uint_as_float(a.maxbits[0]) * (1.0f + 1e-5f);
-        const float cmax = __uint_as_float(a.maxbits[1]) * (1.0f + 1e-5f);
-        const float u2 = 1.52587890625e-05f;  // 2^-16
-        const float acc_b = (float)(3 * D + 2) * 5.9604645e-8f;
-        const float C1 = 1.5f * (3.1f * u2 + acc_b), C2 = 1.5f * (u2 + acc_b);
+    } else if (warp >= kBuild0 / 32 && warp < kDrain0 / 32) {
+        // ---- A builder: thread = row; the row read straight from global memory, centred, split into
+        // bf16 high and low parts; rows past N read as zeros (their lists are never written)
+        const int q = warp & 3, r = q * 32 + lane;
         for (int i = 0; i < n_my; ++i) {
+            const int as = i % NA;
+            if (i >= NA &&
+                !__all_sync(0xffffffffu, mbar_wait(smem_u32(mb + MB_AFREE + as), ((i / NA) - 1) & 1, a.err)))
+                break;
             const int64_t row = (int64_t)((int)blockIdx.x + i * (int)gridDim.x) * TM + r;
-            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(mb + MB_XFULL), i & 1, a.err))) break;
-            if (i >= 1 && !__all_sync(0xffffffffu, mbar_wait(smem_u32(mb + MB_AFREE), (i - 1) & 1, a.err))) break;
-            // A operand: xh tiles [0, KD), xl tiles [KD, 2KD), constant tile 2KD
+            const bool in = row < a.N;
+            const float *xr = a.X + (in ? row : 0) * (int64_t)D;
+            unsigned char *ab = aop + as * A_STAGE;
             float xx = 0.0f;
+            bool nz = false;
             for (int k = 0; k < KD; ++k) {
-                const float *box = reinterpret_cast<const float *>(xs + (k >> 1) * XBOX);
                 float hi[16], lo[16];
 #pragma unroll
                 for (int c4 = 0; c4 < 4; ++c4) {
-                    const int chunk = ((k & 1) << 2) + c4;
-                    const float4 v = *reinterpret_cast<const float4 *>(box + r * 32 + ((chunk ^ (r & 7)) << 2));
+                    const float4 v = in ? __ldg(reinterpret_cast<const float4 *>(xr + 16 * k + 4 * c4))
+                                        : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                     const float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                     for (int w = 0; w < 4; ++w) {
@@ -375,9 +390,10 @@ __global__ void __launch_bounds__(kThreads, 1) coarse_tc_kernel(const __grid_con
                         xx = fmaf(xc, xc, xx);
                         hi[4 * c4 + w] = bf16_round(xc);
                         lo[4 * c4 + w] = xc - hi[4 * c4 + w];
+                        nz |= lo[4 * c4 + w] != 0.0f;
                     }
                 }
-                unsigned char *th = aop + k * A_TILE, *tlo = aop + (KD + k) * A_TILE;
+                unsigned char *th = ab + k * A_TILE, *tlo = ab + (KD + k) * A_TILE;
                 *reinterpret_cast<uint4 *>(th + core_off(r, 0)) = make_uint4(pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]),
                                                                              pack_bf16(hi[4], hi[5]), pack_bf16(hi[6], hi[7]));
                 *reinterpret_cast<uint4 *>(th + core_off(r, 8)) = make_uint4(pack_bf16(hi[8], hi[9]), pack_bf16(hi[10], hi[11]),
@@ -388,58 +404,58 @@ __global__ void __launch_bounds__(kThreads, 1) coarse_tc_kernel(const __grid_con
                                                                               pack_bf16(lo[12], lo[13]), pack_bf16(lo[14], lo[15]));
             }
             {
-                unsigned char *tn = aop + 2 * KD * A_TILE;
+                unsigned char *tn = ab + 2 * KD * A_TILE;
                 *reinterpret_cast<uint4 *>(tn + core_off(r, 0)) = make_uint4(pack_bf16(1.0f, 1.0f), 0u, 0u, 0u);
                 *reinterpret_cast<uint4 *>(tn + core_off(r, 8)) = make_uint4(0u, 0u, 0u, 0u);
             }
+            xn_s[(i % NXN) * TM + r] = sqrtf(xx) * (1.0f + 1e-5f);
             fence_async_smem();
-            __syncwarp();
+            const bool wnz = __any_sync(0xffffffffu, nz);
             if (lane == 0) {
-                mbar_arrive(smem_u32(mb + MB_AREADY));
-                mbar_arrive(smem_u32(mb + MB_XEMPTY));
+                xlnz[as * 4 + q] = wnz ? 1 : 0;
+                mbar_arrive(smem_u32(mb + MB_AREADY + as));
+                mbar_arrive(smem_u32(mb + MB_XNREADY + i % NXN));
             }
-            const float xn = sqrtf(xx) * (1.0f + 1e-5f);
+        }
+    } else if (warp >= kDrain0 / 32) {
+        // ---- drain: thread = row = TMEM lane; the scores of every centroid block, the chunk maxima
+        // from the loads' max reduction, the best chunk kept in registers
+        const int q = warp & 3, r = q * 32 + lane;
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+        const float nmax = __uint_as_float(a.maxbits[0]) * (1.0f + 1e-5f);
+        const float cmax = __uint_as_float(a.maxbits[1]) * (1.0f + 1e-5f);
+        const float u2 = 1.52587890625e-05f;  // 2^-16
+        const float acc_b = (float)(3 * D + 2) * 5.9604645e-8f;
+        const float C1 = 1.5f * (3.1f * u2 + acc_b), C2 = 1.5f * (u2 + acc_b);
+        float *cmx = reinterpret_cast<float *>(sm + OFF_CMX);
+        for (int i = 0; i < n_my; ++i) {
+            const int64_t row = (int64_t)((int)blockIdx.x + i * (int)gridDim.x) * TM + r;
+            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(mb + MB_XNREADY + i % NXN), (i / NXN) & 1, a.err))) break;
+            const float xn = xn_s[(i % NXN) * TM + r];
             const float tt = xn + cmax;
             const float win = 2.0f * (C1 * xn * cmax + C2 * nmax + 1e-13f * tt * tt);
-
             float best = -FLT_MAX, cm2 = -FLT_MAX;
             int bestj = 0;
             float sv[32];
-            float *cmx = reinterpret_cast<float *>(sm + OFF_CMX);
-#pragma unroll
-            for (int q2 = 0; q2 < 32; ++q2) sv[q2] = -FLT_MAX;
             bool ok = true;
             for (int b = 0; b < NB; ++b) {
                 const int v = i * NB + b, buf = v & 1, u = v >> 1;
                 if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(mb + MB_MMA + buf), u & 1, a.err))) { ok = false; break; }
                 tc_after_sync();
                 const uint32_t tb = tl + (uint32_t)(buf * NBLK);
-#pragma unroll 1
-                for (int cp = 0; cp < NBLK / 64; ++cp) {
-                    float v2[2][32];
-                    TC_LD32(tb + (uint32_t)(cp * 64), v2[0]);
-                    TC_LD32(tb + (uint32_t)(cp * 64 + 32), v2[1]);
-                    TC_WAIT32(v2[0]);
-                    TC_WAIT32(v2[1]);
 #pragma unroll
-                    for (int hh = 0; hh < 2; ++hh) {
-                        const float *vv = v2[hh];
-                        float m16[16];
+                for (int cc = 0; cc < NBLK / 32; ++cc) {
+                    float vv[32], cm;
+                    TC_LDMAX32(tb + (uint32_t)(cc * 32), vv, cm);
+                    TC_WAITMAX32(vv, cm);
+                    const int j = b * (NBLK / 32) + cc;
+                    if (NBT > 0) cmx[j * TM + r] = cm;
+                    const bool better = cm > best;
+                    cm2 = better ? best : fmaxf(cm2, cm);
+                    best = better ? cm : best;
+                    bestj = better ? j : bestj;
 #pragma unroll
-                        for (int q2 = 0; q2 < 16; ++q2) m16[q2] = fmaxf(vv[2 * q2], vv[2 * q2 + 1]);
-#pragma unroll
-                        for (int q2 = 0; q2 < 8; ++q2) m16[q2] = fmaxf(m16[2 * q2], m16[2 * q2 + 1]);
-#pragma unroll
-                        for (int q2 = 0; q2 < 4; ++q2) m16[q2] = fmaxf(m16[2 * q2], m16[2 * q2 + 1]);
-                        const float cm = fmaxf(fmaxf(m16[0], m16[1]), fmaxf(m16[2], m16[3]));
-                        if (NBT > 0) cmx[((b * NBLK + cp * 64 + hh * 32) / 32) * TM + r] = cm;
-                        const bool better = cm > best;
-                        cm2 = better ? best : fmaxf(cm2, cm);
-                        best = better ? cm : best;
-                        bestj = better ? (b * NBLK + cp * 64 + hh * 32) / 32 : bestj;
-#pragma unroll
-                        for (int q2 = 0; q2 < 32; ++q2) sv[q2] = better ? vv[q2] : sv[q2];
-                    }
+                    for (int q2 = 0; q2 < 32; ++q2) sv[q2] = (j == 0 || better) ? vv[q2] : sv[q2];
                 }
                 tc_before_sync();
                 __syncwarp();
@@ -496,20 +512,6 @@ __global__ void __launch_bounds__(kThreads, 1) coarse_tc_kernel(const __grid_con
     }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 get_encode()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
-    return fn;
-}
-
 }  // namespace
 
 bool coarse_tc_supported(int D, int nlist) { return D % 32 == 0 && D >= 32 && D <= DMAX && nlist >= 1; }
@@ -521,8 +523,7 @@ int launch_coarse_tc(const float *X, int64_t N, int D, const float *C, int nlist
 {
     if (!coarse_tc_supported(D, nlist)) return fail(PQ_ENOTSUP, "tensor-core coarse assignment needs D % 32 == 0, D <= 128");
     if (N >= (1LL << 31) - TM) return fail(PQ_ENOTSUP, "tensor-core coarse assignment supports N < 2^31");
-    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
-    if (!enc) return fail(PQ_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    if (reinterpret_cast<uintptr_t>(X) & 15) return fail(PQ_EINVAL, "X must be 16-byte aligned");
     const int nlist_pad = (nlist + NBLK - 1) / NBLK * NBLK;
     const int KD = D / 16, T = 2 * KD + 1;
     float *mu = ws.get<float>((size_t)D);
@@ -541,21 +542,13 @@ int launch_coarse_tc(const float *X, int64_t N, int D, const float *C, int nlist
         count_launch(2);
         PQ_TRY_CUDA(cudaGetLastError());
     }
-    CUtensorMap map;
-    const cuuint64_t gdim[2] = {(cuuint64_t)D, (cuuint64_t)N};
-    const cuuint64_t gstride[1] = {(cuuint64_t)D * sizeof(float)};
-    const cuuint32_t box[2] = {32u, (cuuint32_t)TM};
-    const cuuint32_t estride[2] = {1, 1};
-    const CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(X), gdim, gstride, box,
-                            estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) return fail(PQ_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
     CoarseTcArgs a;
     a.N = N;
     a.D = D;
     a.nlist = nlist;
     a.nlist_pad = nlist_pad;
     a.tiles = (int)((N + TM - 1) / TM);
+    a.X = X;
     a.Bp = Bp;
     a.mu = mu;
     a.maxbits = maxbits;
@@ -568,10 +561,10 @@ int launch_coarse_tc(const float *X, int64_t N, int D, const float *C, int nlist
     ProfScope ps("coarse_assign_tc", s);
     if (nlist_pad <= 4 * NBLK) {
         PQ_TRY_CUDA(cudaFuncSetAttribute(coarse_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-        coarse_tc_kernel<4><<<grid, kThreads, SMEM_BYTES, s>>>(map, a);
+        coarse_tc_kernel<4><<<grid, kThreads, SMEM_BYTES, s>>>(a);
     } else {
         PQ_TRY_CUDA(cudaFuncSetAttribute(coarse_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-        coarse_tc_kernel<0><<<grid, kThreads, SMEM_BYTES, s>>>(map, a);
+        coarse_tc_kernel<0><<<grid, kThreads, SMEM_BYTES, s>>>(a);
     }
     count_launch();
     PQ_TRY_CUDA(cudaGetLastError());
