@@ -15,14 +15,17 @@
 // within twice the bound; every other row goes to the FP64 re-check queue
 // (coarse.cu), so the list of every row is exact.
 //
-// Pipeline, one CTA (384 threads) per SM, persistent over 128-row tiles: lane 0
-// of warp 0 streams the pre-tiled B operand (8 KB tiles, bulk copies) through an
-// 8-slot ring; lane 0 of warp 1 issues M=128 N=256 K=16 MMAs into two TMEM
-// accumulators (256 centroids each); warps 4-7 build the A operand of the next
-// tile (two stages) from rows read straight from global memory; warps 8-11 drain
-// the accumulators and decide.  When no row of a tile has a bf16 low part (integer
-// rows within 256 of the centring), the MMAs of the xl.ch term are skipped: they
-// would add exact zeros.  Every wait is bounded.
+// Pipeline, one CTA (384 threads) per SM, persistent over 128-row tiles: the
+// centroid blocks of a tile alternate between two TMEM accumulators (256 centroids
+// each), and each accumulator has a pipe of its own: a loading thread (warp 0 or
+// 3) streams its blocks' pre-tiled B operand (8 KB tiles, bulk copies) through a
+// 4-slot ring, and an issuing thread (warp 1 or 2) issues its M=128 N=256 K=16
+// MMAs -- one issuing thread's own instruction chain cannot keep the tensor pipe
+// busy.  Warps 4-7 build the A operand of the next tile (two stages) from rows
+// read straight from global memory; warps 8-11 drain the accumulators and decide.
+// When no row of a tile has a bf16 low part (integer rows within 256 of the
+// integer centring), the MMAs of the xl.ch term are skipped: they would add exact
+// zeros.  Every wait is bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -47,10 +50,10 @@ constexpr int A_STAGE = (2 * KDMAX + 1) * A_TILE;  // 68 KB: xh tiles, xl tiles,
 constexpr int NA = 2;                // A stages
 constexpr int NXN = 4;               // row-norm slots (the builder runs at most 3 tiles ahead of the drain)
 constexpr int B_TILE = NBLK * 16 * 2;  // 8 KB
-constexpr int RING = 8;
+constexpr int RING = 4;              // B slots per pipe (two pipes, one per TMEM buffer)
 constexpr int OFF_A = 0;
 constexpr int OFF_RING = OFF_A + NA * A_STAGE;
-constexpr int OFF_MISC = OFF_RING + RING * B_TILE;        // mbarriers, TMEM slot, mu, low-part flags
+constexpr int OFF_MISC = OFF_RING + 2 * RING * B_TILE;        // mbarriers, TMEM slot, mu, low-part flags
 constexpr int OFF_XN = OFF_MISC + 1024;                   // [NXN][TM] float: ||x'|| per row
 constexpr int OFF_CMX = OFF_XN + NXN * TM * 4;            // [32 chunks][128 rows] chunk maxima
 constexpr int SMEM_BYTES = OFF_CMX + 32 * TM * 4 + 1024;
@@ -58,8 +61,8 @@ static_assert(SMEM_BYTES <= 227 * 1024, "shared memory of one CTA");
 
 // mbarrier slots
 constexpr int MB_AREADY = 0 /*NA*/, MB_AFREE = 2 /*NA*/, MB_MMA = 4 /*2*/, MB_TFREE = 6 /*2*/,
-              MB_RFULL = 8 /*RING*/, MB_REMPTY = 8 + RING /*RING*/, MB_XNREADY = 8 + 2 * RING /*NXN*/,
-              MB_COUNT = 8 + 2 * RING + NXN;
+              MB_RFULL = 8 /*2 x RING*/, MB_REMPTY = 8 + 2 * RING /*2 x RING*/, MB_XNREADY = 8 + 4 * RING /*NXN*/,
+              MB_COUNT = 8 + 4 * RING + NXN;
 constexpr int MISC_TSLOT = 8 * MB_COUNT, MISC_MU = 256, MISC_XLNZ = 768;  // xlnz: [NA][4] int
 static_assert(MISC_TSLOT + 4 <= MISC_MU && MISC_MU + 4 * DMAX <= MISC_XLNZ && MISC_XLNZ + 4 * NA * 4 <= 1024,
               "misc area overlap");
@@ -269,6 +272,7 @@ __global__ void __launch_bounds__(kThreads, 1) coarse_tc_kernel(const CoarseTcAr
             if ((i >= MB_AREADY && i < MB_AREADY + NA) || i == MB_TFREE || i == MB_TFREE + 1 ||
                 (i >= MB_XNREADY && i < MB_XNREADY + NXN))
                 c = 4;
+            if (i >= MB_AFREE && i < MB_AFREE + NA) c = 2;  // both MMA warps
             mbar_init(smem_u32(mb + i), c);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -283,33 +287,40 @@ __global__ void __launch_bounds__(kThreads, 1) coarse_tc_kernel(const CoarseTcAr
     const uint32_t tmem = *tslot;
     const int n_my = (a.tiles > (int)blockIdx.x) ? (a.tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
-    if (warp == 0) {
+    if (warp == 0 || warp == 3) {
+        // ---- B loads: pipe e (warp 0: e = 0, warp 3: e = 1) streams the tiles of the centroid
+        // blocks whose sequence number v = i * NB + b has v % 2 == e, in MMA order, through its ring
         if (lane == 0) {
-            // B tiles in MMA order through the ring (a warp of its own)
+            const int e = warp == 0 ? 0 : 1;
+            const uint32_t rfull0 = smem_u32(mb + MB_RFULL + e * RING), rempty0 = smem_u32(mb + MB_REMPTY + e * RING);
+            unsigned char *rg = ring + e * RING * B_TILE;
             int z = 0;
             bool ok = true;
             for (int i = 0; i < n_my && ok; ++i)
-                for (int b = 0; b < NB && ok; ++b)
+                for (int b = 0; b < NB && ok; ++b) {
+                    if (((i * NB + b) & 1) != e) continue;
                     for (int t = 0; t < T; ++t, ++z) {
                         const int slot = z % RING, use = z / RING;
-                        if (use >= 1 && !mbar_wait(smem_u32(mb + MB_REMPTY + slot), (use - 1) & 1, a.err)) {
+                        if (use >= 1 && !mbar_wait(rempty0 + 8 * slot, (use - 1) & 1, a.err)) {
                             ok = false;
                             break;
                         }
-                        mbar_expect_tx(smem_u32(mb + MB_RFULL + slot), B_TILE);
-                        bulk_load(smem_u32(ring + slot * B_TILE), a.Bp + ((size_t)b * T + t) * B_TILE, B_TILE,
-                                  smem_u32(mb + MB_RFULL + slot));
+                        mbar_expect_tx(rfull0 + 8 * slot, B_TILE);
+                        bulk_load(smem_u32(rg + slot * B_TILE), a.Bp + ((size_t)b * T + t) * B_TILE, B_TILE,
+                                  rfull0 + 8 * slot);
                     }
-            for (int q = (z > RING ? z - RING : 0); q < z; ++q)
-                mbar_wait(smem_u32(mb + MB_RFULL + q % RING), (q / RING) & 1, a.err);
+                }
+            for (int q = (z > RING ? z - RING : 0); q < z; ++q) mbar_wait(rfull0 + 8 * (q % RING), (q / RING) & 1, a.err);
         }
-    } else if (warp == 1) {
-        // ---- MMA issue.  One thread issues every MMA, so its own instructions between two MMAs
-        // bound the tensor pipe: descriptors are base values plus offsets, the ring position is a
-        // running counter, and the wait for a B tile is a plain poll.
+    } else if (warp == 1 || warp == 2) {
+        // ---- MMA issue, two warps: warp 1 + e issues the blocks of pipe e into TMEM buffer e.  A
+        // single issuing thread's own instructions between two MMAs bound the tensor pipe, so two
+        // issue in turn; descriptors are base values plus offsets, the ring position is a running
+        // counter, and the wait for a B tile is a plain poll.
         if (lane == 0) {
-            const uint64_t dA0 = smem_desc(smem_u32(aop)), dB0 = smem_desc(smem_u32(ring));
-            const uint32_t rfull0 = smem_u32(mb + MB_RFULL), rempty0 = smem_u32(mb + MB_REMPTY);
+            const int e = warp - 1;
+            const uint64_t dA0 = smem_desc(smem_u32(aop)), dB0 = smem_desc(smem_u32(ring + e * RING * B_TILE));
+            const uint32_t rfull0 = smem_u32(mb + MB_RFULL + e * RING), rempty0 = smem_u32(mb + MB_REMPTY + e * RING);
             int slot = 0;
             uint32_t ph = 0;
             bool ok = true;
@@ -339,6 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1) coarse_tc_kernel(const CoarseTcAr
                 const uint64_t dA = dA0 + (uint64_t)((as * A_STAGE) >> 4);
                 for (int b = 0; b < NB && ok; ++b) {
                     const int v = i * NB + b, buf = v & 1, u = v >> 1;
+                    if (buf != e) continue;
                     if (u >= 1 && !mbar_wait(smem_u32(mb + MB_TFREE + buf), (u - 1) & 1, a.err)) { ok = false; break; }
                     tc_after_sync();
                     const uint32_t d = tmem + (uint32_t)(buf * NBLK);
