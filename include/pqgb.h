@@ -193,9 +193,14 @@ int pq_lloyd_noalloc(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks
  * `seed`, then `iters` Lloyd iterations); the codewords of all chunks form the
  * centroid dataset (row c*Ks + k = concatenation over m of codeword k of
  * subspace m of chunk c), on which the global PQ is fitted with `seed`.  All
- * chunks are fitted together: one launch seeds every (chunk, subspace) pair and
- * each Lloyd iteration is one launch over all chunks.  With rmse == NULL the
- * call never synchronizes and can be captured in a CUDA graph.
+ * chunks are fitted together: one launch seeds every (chunk, subspace) pair, and
+ * the Lloyd iterations of every (chunk, subspace group) run in one persistent
+ * cooperative launch (BF16 form; its units of rows are shared out over the
+ * resident CTAs, and after each pass the last unit of a (chunk, group) to finish
+ * moves that chunk's codebooks and lets the group's next pass start; the FP32
+ * form runs one launch per iteration).  The unit size is the one pq_tune_chunked
+ * chose for this shape, else a default.  With rmse == NULL the call never
+ * synchronizes and can be captured in a CUDA graph.
  */
 int pq_fit_chunked(const float *X, const int64_t *chunk_offsets, int32_t n_chunks, int32_t D, int32_t M, int32_t Ks,
                    int32_t iters, uint64_t seed, int32_t prec, float *codebooks, uint8_t *codes, double *rmse,
@@ -261,16 +266,19 @@ int softpq_backward(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks,
                     const float *grad_loss, float *dcodebooks, float *dX, void *stream);
 
 /*
- * pq_tune_chunked -- autotuner of the batched Lloyd pass of pq_fit_chunked.
+ * pq_tune_chunked -- autotuner of the batched Lloyd passes of pq_fit_chunked.
  *   Same X, chunk_offsets (HOST array), n_chunks, D, M, Ks and prec rules as
- *   pq_fit_chunked.  Seeds every chunk, then times one batched pass (mean of
- *   three after a warm-up, CUDA events on `stream`) for each candidate number of
- *   CTAs per subspace group (0.5x to 4x the default, shared out over the chunks
- *   in proportion to their rows) and keeps the fastest in a process-wide cache
- *   keyed by the shape (n_chunks, N, D, M, Ks, prec, SM count, chunk offsets);
- *   later pq_fit_chunked calls of that shape use it.  Synchronizes `stream`.
- *   ctas     receives the chosen CTAs per subspace group (nullable).
- *   pass_ms  receives its measured pass time in milliseconds (nullable).
+ *   pq_fit_chunked.  Seeds every chunk, then, for each candidate number of work
+ *   units per subspace group (0.5x to 4x the default, shared out over the chunks
+ *   in proportion to their rows, so that a unit is a run of ceil(tiles / units)
+ *   128-row tiles of one chunk), times the batched passes: BF16, the persistent
+ *   launch of three passes after a one-pass warm-up; FP32, the mean of three
+ *   passes after a warm-up (CUDA events on `stream`).  The fastest is kept in a
+ *   process-wide cache keyed by the shape (n_chunks, N, D, M, Ks, prec, SM
+ *   count, chunk offsets); later pq_fit_chunked calls of that shape use it.
+ *   Synchronizes `stream`.
+ *   ctas     receives the chosen units per subspace group (nullable).
+ *   pass_ms  receives its measured time per pass in milliseconds (nullable).
  * pq_tune_clear forgets every tuned shape.
  */
 int pq_tune_chunked(const float *X, const int64_t *chunk_offsets, int32_t n_chunks, int32_t D, int32_t M, int32_t Ks,

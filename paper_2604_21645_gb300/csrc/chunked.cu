@@ -228,13 +228,18 @@ int run_pq_fit_chunked(const float *X, const int64_t *off, int n_chunks, int D, 
         count_launch();
         PQ_TRY_CUDA(cudaGetLastError());
     }
-    for (int t = 0; t < iters; ++t) {
-        if (tc)
-            PQ_TRY(launch_pq_pass_tc(p, s));
-        else
+    if (tc) {
+        // all the passes of every (chunk, subspace group) in one persistent launch
+        int *arrive = ws.get<int>((size_t)n_chunks * (M / tc_pass_group()), true);
+        int *ready = ws.get<int>((size_t)n_chunks * (M / tc_pass_group()), true);
+        if (ws.status) return ws.status;
+        PQ_TRY(launch_pq_fit_persistent_tc(p, iters, arrive, ready, counts, s));
+    } else {
+        for (int t = 0; t < iters; ++t) {
             PQ_TRY(launch_pq_pass_f32(p, s));
-        PQ_TRY(launch_pq_finalize(p.part, gx, M, Ks, ds, Cl, nullptr, s, n_chunks, d_blk,
-                                  t + 1 == iters ? counts : nullptr));
+            PQ_TRY(launch_pq_finalize(p.part, gx, M, Ks, ds, Cl, nullptr, s, n_chunks, d_blk,
+                                      t + 1 == iters ? counts : nullptr));
+        }
     }
 
     // (3) centroid dataset of the pooled codewords, (4) global fit, (5) global encode + error
@@ -333,6 +338,9 @@ int run_pq_tune_chunked(const float *X, const int64_t *off, int n_chunks, int D,
     int *d_blk = ws.get<int>((size_t)n_chunks + 1);
     int *d_bc = ws.get<int>((size_t)gmax);
     void *pb = ws.raw(Partials::bytes(gmax, M, Ks, ds, n_chunks), false);
+    const size_t ncg = (size_t)n_chunks * (M / tc_pass_group());
+    int *arrive = tc ? ws.get<int>(ncg) : nullptr;
+    int *ready = tc ? ws.get<int>(ncg) : nullptr;
     if (ws.status) return ws.status;
     cudaEvent_t e0, e1;
     PQ_TRY_CUDA(cudaEventCreate(&e0));
@@ -358,10 +366,22 @@ int run_pq_tune_chunked(const float *X, const int64_t *off, int n_chunks, int D,
         p.chunk_off = d_off;
         p.chunk_blk = d_blk;
         p.n_chunks = n_chunks;
-        // one pass to warm up, then the mean of three (the codebooks are not updated)
-        for (int r = 0; r < 4 && st == PQ_OK; ++r) {
-            if (r == 1) cudaEventRecord(e0, s);
-            st = tc ? launch_pq_pass_tc(p, s) : launch_pq_pass_f32(p, s);
+        if (tc) {
+            // the persistent form: one launch of one pass to warm up, then one launch of three passes
+            // (the codebooks of the tuning run are updated; they are scratch)
+            for (int r = 0; r < 2 && st == PQ_OK; ++r) {
+                if (r == 1) cudaEventRecord(e0, s);
+                cudaError_t ce = cudaMemsetAsync(arrive, 0, ncg * sizeof(int), s);
+                if (ce == cudaSuccess) ce = cudaMemsetAsync(ready, 0, ncg * sizeof(int), s);
+                st = ce == cudaSuccess ? launch_pq_fit_persistent_tc(p, r == 0 ? 1 : 3, arrive, ready, nullptr, s)
+                                       : cuda_check(ce, "pq_tune_chunked");
+            }
+        } else {
+            // one pass to warm up, then the mean of three (the codebooks are not updated)
+            for (int r = 0; r < 4 && st == PQ_OK; ++r) {
+                if (r == 1) cudaEventRecord(e0, s);
+                st = launch_pq_pass_f32(p, s);
+            }
         }
         if (st != PQ_OK) break;
         cudaEventRecord(e1, s);

@@ -70,6 +70,44 @@ struct Partials {
     __host__ __device__ bool active() const { return q != nullptr; }
 };
 
+#ifdef __CUDACC__
+// The update of one codeword element (chunk c, subspace m, codeword k, dimension j) from the
+// partial sums of blocks [b0, b1): the int64 sums added exactly, the FP32 sums added with TwoSum
+// in block order, the total turned into a float-float value, divided by the member count in
+// float-float and added to the codeword with one rounding.  An empty codeword keeps its value.
+// Returns the member count.
+__device__ __forceinline__ long long finalize_element(const Partials &part, int M, int Ks, int ds, float *C, int c,
+                                                      int m, int k, int j, int b0, int b1)
+{
+    long long n = 0, q = 0;
+    float oh = 0.0f, ol = 0.0f;
+    for (int b = b0; b < b1; ++b) {
+        const size_t e = ((size_t)b * M + m) * Ks + k;
+        n += __ldcg(part.cnt + e);
+        q += __ldcg(part.q + e * ds + j);
+        float s, err;
+        two_sum(oh, __ldcg(part.o + e * ds + j), s, err);
+        oh = s;
+        ol = __fadd_rn(ol, err);
+    }
+    if (n == 0) return 0;
+    const int F = __ldcg(part.F + c * M + m);
+    float sh, sl;
+    ll_to_ff(q, sh, sl);
+    sh = ldexpf(sh, -F);
+    sl = ldexpf(sl, -F);
+    ff_add(sh, sl, oh, ol, sh, sl);
+    float nh, nl, mh, ml;
+    ll_to_ff(n, nh, nl);
+    ff_div(sh, sl, nh, nl, mh, ml);
+    float *cp = C + (size_t)c * M * Ks * ds + ((size_t)m * Ks + k) * ds + j;
+    float t, e;
+    two_sum(__ldcg(cp), mh, t, e);
+    *cp = __fadd_rn(t, __fadd_rn(e, ml));
+    return n;
+}
+#endif
+
 // ---- PQ Lloyd pass, FP32 SIMT form (lloyd_simt.cu) ------------------------
 struct PqPass {
     const float *X = nullptr;
@@ -105,6 +143,12 @@ int tc_pass_group();  // subspaces per CTA of the tensor-core pass
 int pq_pass_tc_blocks(const PqPass &p);
 // writes per-CTA residual sums (x - c_code) into p.part; finalise with launch_pq_finalize
 int launch_pq_pass_tc(PqPass &p, cudaStream_t s);
+// All `iters` Lloyd passes of the batched form (p: chunk table and partial sums set, p.gx its
+// blocks) in one persistent cooperative launch: the (block, subspace group) units are shared out
+// over the resident CTAs, and after each pass the last unit of a (chunk, group) to finish moves that
+// chunk's codebooks (p.C, in place).  arrive/ready: n_chunks * (M / 2) zeroed ints; counts: the
+// member counts of the last update, or null.
+int launch_pq_fit_persistent_tc(PqPass &p, int iters, int *arrive, int *ready, long long *counts, cudaStream_t s);
 
 // ---- coarse quantizer and inverted lists (coarse.cu) ----------------------
 struct CoarseBound {

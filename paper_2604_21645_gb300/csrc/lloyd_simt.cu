@@ -268,35 +268,9 @@ __global__ void pq_finalize_kernel(const Partials part, int gx, int M, int Ks, i
     const int64_t cw = idx / ds;
     const int c = (int)(cw / ((int64_t)M * Ks)), m = (int)((cw / Ks) % M), k = (int)(cw % Ks);
     const int b0 = chunk_blk ? chunk_blk[c] : 0, b1 = chunk_blk ? chunk_blk[c + 1] : gx;
-    long long n = 0, q = 0;
-    float oh = 0.0f, ol = 0.0f;
-    for (int b = b0; b < b1; ++b) {
-        const size_t e = ((size_t)b * M + m) * Ks + k;
-        n += part.cnt[e];
-        q += part.q[e * ds + j];
-        float s, err;
-        two_sum(oh, part.o[e * ds + j], s, err);
-        oh = s;
-        ol = __fadd_rn(ol, err);
-    }
+    const long long n = finalize_element(part, M, Ks, ds, C, c, m, k, j, b0, b1);
     if (counts && j == 0) counts[cw] = n;
-    if (n == 0) {
-        if (empties && j == 0) atomicAdd(empties, 1ull);
-        return;
-    }
-    const int F = part.F[c * M + m];
-    float sh, sl;
-    ll_to_ff(q, sh, sl);
-    sh = ldexpf(sh, -F);
-    sl = ldexpf(sl, -F);
-    ff_add(sh, sl, oh, ol, sh, sl);
-    float nh, nl, mh, ml;
-    ll_to_ff(n, nh, nl);
-    ff_div(sh, sl, nh, nl, mh, ml);
-    float *cp = C + (size_t)c * M * Ks * ds + ((size_t)m * Ks + k) * ds + j;
-    float t, e;
-    two_sum(*cp, mh, t, e);
-    *cp = __fadd_rn(t, __fadd_rn(e, ml));
+    if (n == 0 && empties && j == 0) atomicAdd(empties, 1ull);
 }
 
 // One thread per (row, subspace): reconstruction and/or squared error.

@@ -131,6 +131,14 @@ struct TcArgs {
     const int *blk_chunk;      // optional chunk table (batched form)
     const int64_t *chunk_off;
     const int *chunk_blk;
+    // persistent form (the batched Lloyd iterations in one launch): `iters` passes over `units`
+    // (x, group) units of the chunk table (x < gxu), shared out over the CTAs; after each pass over
+    // a (chunk, group) the last of its units to finish moves its codebooks (Cw) and publishes the
+    // pass in ready[chunk * groups + group], counting arrivals in arrive[]
+    int iters, units, gxu;
+    float *Cw;
+    int *arrive, *ready;
+    long long *counts;         // member counts of the last update, or null
 };
 
 // ---- PTX wrappers ----------------------------------------------------------
@@ -346,6 +354,9 @@ __device__ __forceinline__ void decide_exact_warp(bool unsure, float4 v0, float4
     }
 }
 
+// PERSIST: the persistent form (see TcArgs): the CTA runs its units pass after pass, waiting before
+// a unit for the previous pass of its (chunk, group) to be published; no register hand-over.
+template <bool PERSIST>
 __global__ void __maxnreg__(kRegLaunch) pq_pass_tc_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                   const TcArgs a)
 {
@@ -355,21 +366,8 @@ __global__ void __maxnreg__(kRegLaunch) pq_pass_tc_kernel(const __grid_constant_
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem_raw);
     unsigned char *sm = smem_raw + (((sbase + 1023u) & ~1023u) - sbase);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int grp = blockIdx.y, m0 = grp * G;
     const int Ks = a.Ks;
     const bool fit = a.part.active();
-    // chunk of this CTA (batched form): its rows, its share of the CTAs, its codebooks
-    int chunk = 0, lb = blockIdx.x, gxc = gridDim.x;
-    int64_t r0 = 0, r1 = a.N;
-    if (a.blk_chunk) {
-        chunk = a.blk_chunk[blockIdx.x];
-        lb = blockIdx.x - a.chunk_blk[chunk];
-        gxc = a.chunk_blk[chunk + 1] - a.chunk_blk[chunk];
-        r0 = a.chunk_off[chunk];
-        r1 = a.chunk_off[chunk + 1];
-    }
-    const int tiles_c = (int)((r1 - r0 + TM - 1) / TM);
-    const float *Cc = a.C + (size_t)chunk * a.M * Ks * DS;
 
     float *xs = reinterpret_cast<float *>(sm + OFF_XS);
     unsigned char *aop = sm + OFF_A;
@@ -384,13 +382,70 @@ __global__ void __maxnreg__(kRegLaunch) pq_pass_tc_kernel(const __grid_constant_
     float *mu = reinterpret_cast<float *>(sm + OFF_MISC + MISC_MU);
     unsigned *bnd = reinterpret_cast<unsigned *>(sm + OFF_MISC + MISC_BND);  // [G][2] float bits: n', ||c'|| maxima
     auto bar = [&](int slot) { return smem_u32(mb + slot); };
+    __shared__ int s_flag;
+
+    // tensor memory, held for the whole launch
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tslot)) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = *tslot;
+
+    const int n_iter = PERSIST ? a.iters : 1;
+    const int n_units = PERSIST ? a.units : 1;
+    bool live = true;  // CTA-uniform: false once a wait for another CTA ran out
+    for (int it = 0; it < n_iter && live; ++it)
+    for (int uu = PERSIST ? (int)blockIdx.x : 0; uu < n_units && live; uu += PERSIST ? (int)gridDim.x : 1) {
+    const int ux = PERSIST ? uu % a.gxu : (int)blockIdx.x;
+    const int grp = PERSIST ? uu / a.gxu : (int)blockIdx.y, m0 = grp * G;
+    // chunk of this unit (batched form): its rows, its share of the units, its codebooks
+    int chunk = 0, lb = ux, gxc = PERSIST ? a.gxu : (int)gridDim.x;
+    int64_t r0 = 0, r1 = a.N;
+    if (a.blk_chunk) {
+        chunk = a.blk_chunk[ux];
+        lb = ux - a.chunk_blk[chunk];
+        gxc = a.chunk_blk[chunk + 1] - a.chunk_blk[chunk];
+        r0 = a.chunk_off[chunk];
+        r1 = a.chunk_off[chunk + 1];
+    }
+    const int tiles_c = (int)((r1 - r0 + TM - 1) / TM);
+    const float *Cc = a.C + (size_t)chunk * a.M * Ks * DS;
+    const int cg = chunk * (a.M / G) + grp;
+    if (PERSIST && it > 0) {
+        // the previous pass over this (chunk, group) has been published (bounded wait)
+        if (tid == 0) {
+            int ok = 1;
+            for (unsigned spin = 0; *(volatile int *)(a.ready + cg) < it; ++spin) {
+                if (spin > kSpinLimit) {
+                    atomicCAS(a.err, 0, PQ_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                if ((spin & 255) == 255 && *(volatile int *)a.err != 0) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(128);
+            }
+            __threadfence();
+            s_flag = ok;
+        }
+        __syncthreads();
+        if (!s_flag) {
+            live = false;
+            break;
+        }
+    }
 
     // ---- set-up: codeword mean, B operands, FP32 copies, bounds -------------
     if (tid < G * DS) {
         const int g = tid / DS, j = tid % DS;
         const float *Cm = Cc + (size_t)(m0 + g) * Ks * DS;
         float s = 0.0f;
-        for (int k = 0; k < Ks; ++k) s += Cm[k * DS + j];
+        for (int k = 0; k < Ks; ++k) s += __ldcg(Cm + k * DS + j);
         mu[tid] = s / (float)Ks;
     }
     if (tid < G * 4) bnd[tid] = 0u;
@@ -403,7 +458,7 @@ __global__ void __maxnreg__(kRegLaunch) pq_pass_tc_kernel(const __grid_constant_
             const float *src = Cc + ((size_t)(m0 + g) * Ks + k) * DS;
 #pragma unroll
             for (int j = 0; j < DS; ++j) {
-                c[j] = src[j];
+                c[j] = __ldcg(src + j);
                 cc[j] = c[j] - mu[g * DS + j];
                 nc = fmaf(cc[j], cc[j], nc);
             }
@@ -473,20 +528,15 @@ __global__ void __maxnreg__(kRegLaunch) pq_pass_tc_kernel(const __grid_constant_
         for (int g = 0; g < G; ++g) mbar_init(bar(MB_DRAIN + g), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tslot)) : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
     fence_async_smem();
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
-    const uint32_t tmem = *tslot;
 
     const int n_my = (tiles_c > lb) ? (tiles_c - 1 - lb) / gxc + 1 : 0;
 
     if (warp < kEpi0 / 32) {
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegLo));
+        if constexpr (!PERSIST) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegLo));
     if (warp == 0) {
         // ---- producer: TMA loads of the row tiles -----------------------------
         if (lane == 0) {
@@ -587,7 +637,7 @@ __global__ void __maxnreg__(kRegLaunch) pq_pass_tc_kernel(const __grid_constant_
         }
     }
     } else {
-        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegHi));
+        if constexpr (!PERSIST) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegHi));
         // ---- epilogue warpgroups: thread = row = TMEM lane, warpgroup g = subspace g
         const int g = (tid - kEpi0) >> 7;
         const int r = (warp & 3) * 32 + lane;
@@ -734,7 +784,7 @@ __global__ void __maxnreg__(kRegLaunch) pq_pass_tc_kernel(const __grid_constant_
             for (int e = tid - kEpi0; e < G * KSMAX; e += 256) {
                 const int gg = e / KSMAX, k = e % KSMAX;
                 if (k >= Ks) continue;
-                const size_t base = ((size_t)blockIdx.x * a.M + m0 + gg) * Ks + k;
+                const size_t base = ((size_t)ux * a.M + m0 + gg) * Ks + k;
                 const FixFmt f = fix_format(rows_bound, 2.0f * __uint_as_float(bnd[gg * 2 + 1]));
                 const int o = (gg * KSMAX + k) * ACC_STRIDE;
 #pragma unroll
@@ -755,6 +805,29 @@ __global__ void __maxnreg__(kRegLaunch) pq_pass_tc_kernel(const __grid_constant_
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
+    if constexpr (PERSIST) {
+        // the last unit of this (chunk, group) to finish the pass moves its codebooks and
+        // publishes the pass
+        if (tid == 0) {
+            __threadfence();
+            s_flag = atomicAdd(a.arrive + cg, 1) == (it + 1) * gxc - 1;
+            __threadfence();
+        }
+        __syncthreads();
+        if (s_flag) {
+            const int b0 = a.chunk_blk[chunk], b1 = a.chunk_blk[chunk + 1];
+            for (int e = tid; e < G * Ks * DS; e += kThreads) {
+                const int gg = e / (Ks * DS), k = (e / DS) % Ks, j = e % DS;
+                const long long n = finalize_element(a.part, a.M, Ks, DS, a.Cw, chunk, m0 + gg, k, j, b0, b1);
+                if (a.counts && it + 1 == n_iter && j == 0) a.counts[((size_t)chunk * a.M + m0 + gg) * Ks + k] = n;
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) atomicExch(a.ready + cg, it + 1);
+        }
+        __syncthreads();
+    }
+    }  // units and passes
     if (warp == 1) {
         __syncwarp();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
@@ -792,13 +865,15 @@ int pq_pass_tc_blocks(const PqPass &p)
     return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, std::max(1, sms / groups)));
 }
 
-int launch_pq_pass_tc(PqPass &p, cudaStream_t s)
+namespace {
+
+// the row tiles' tensor map and the kernel arguments of pass p
+int prepare_tc(const PqPass &p, CUtensorMap &map, TcArgs &a)
 {
     if (!tc_pass_supported(p.D, p.M, p.Ks)) return fail(PQ_ENOTSUP, "BF16 tensor-core pass needs D/M == 8 and M even");
     if (p.N >= (1LL << 31) / TM * TM) return fail(PQ_ENOTSUP, "BF16 tensor-core pass supports N < 2^31");
     PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
     if (!enc) return fail(PQ_ECUDA, "cuTensorMapEncodeTiled unavailable");
-    CUtensorMap map;
     const cuuint64_t gdim[2] = {(cuuint64_t)p.D, (cuuint64_t)p.N};
     const cuuint64_t gstride[1] = {(cuuint64_t)p.D * sizeof(float)};
     const cuuint32_t box[2] = {(cuuint32_t)(G * DS), (cuuint32_t)TM};
@@ -811,8 +886,7 @@ int launch_pq_pass_tc(PqPass &p, cudaStream_t s)
     PQ_TRY_CUDA(cudaGetDevice(&dev));
     int *err = device_error_word(dev);
     if (!err) return fail(PQ_ENOMEM, "device error word");
-    if (p.gx <= 0) p.gx = pq_pass_tc_blocks(p);
-    TcArgs a;
+    a = TcArgs{};
     a.N = p.N;
     a.D = p.D;
     a.M = p.M;
@@ -827,12 +901,24 @@ int launch_pq_pass_tc(PqPass &p, cudaStream_t s)
     a.blk_chunk = p.blk_chunk;
     a.chunk_off = p.chunk_off;
     a.chunk_blk = p.chunk_blk;
-    PQ_TRY_CUDA(cudaFuncSetAttribute(pq_pass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    a.iters = 1;
+    return PQ_OK;
+}
+
+}  // namespace
+
+int launch_pq_pass_tc(PqPass &p, cudaStream_t s)
+{
+    CUtensorMap map;
+    TcArgs a;
+    PQ_TRY(prepare_tc(p, map, a));
+    if (p.gx <= 0) p.gx = pq_pass_tc_blocks(p);
+    PQ_TRY_CUDA(cudaFuncSetAttribute(pq_pass_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     // the register hand-over inside the kernel waits for registers the launch must have given it
     static int launch_regs = -1;
     if (launch_regs < 0) {
         cudaFuncAttributes fa;
-        PQ_TRY_CUDA(cudaFuncGetAttributes(&fa, pq_pass_tc_kernel));
+        PQ_TRY_CUDA(cudaFuncGetAttributes(&fa, pq_pass_tc_kernel<false>));
         launch_regs = fa.numRegs;
     }
     if (launch_regs * kThreads < 128 * kRegLo + 256 * kRegHi)
@@ -840,7 +926,40 @@ int launch_pq_pass_tc(PqPass &p, cudaStream_t s)
                     launch_regs);
     dim3 grid(p.gx, p.M / G);
     ProfScope ps("pq_pass_tc", s);
-    pq_pass_tc_kernel<<<grid, kThreads, SMEM_BYTES, s>>>(map, a);
+    pq_pass_tc_kernel<false><<<grid, kThreads, SMEM_BYTES, s>>>(map, a);
+    count_launch();
+    PQ_TRY_CUDA(cudaGetLastError());
+    return PQ_OK;
+}
+
+int launch_pq_fit_persistent_tc(PqPass &p, int iters, int *arrive, int *ready, long long *counts, cudaStream_t s)
+{
+    if (!p.part.active() || !p.chunk_blk || p.gx <= 0)
+        return fail(PQ_EINTERNAL, "persistent tensor-core fit needs a chunk table and partial sums");
+    if (iters <= 0) return PQ_OK;
+    CUtensorMap map;
+    TcArgs a;
+    PQ_TRY(prepare_tc(p, map, a));
+    a.iters = iters;
+    a.gxu = p.gx;
+    a.units = p.gx * (p.M / G);
+    a.Cw = const_cast<float *>(p.C);
+    a.arrive = arrive;
+    a.ready = ready;
+    a.counts = counts;
+    PQ_TRY_CUDA(cudaFuncSetAttribute(pq_pass_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    // every CTA must be resident at once (a unit may wait for units of other CTAs): a cooperative
+    // launch of at most the co-resident CTAs
+    int dev = 0, sms = 0, per_sm = 0;
+    PQ_TRY_CUDA(cudaGetDevice(&dev));
+    PQ_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PQ_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pq_pass_tc_kernel<true>, kThreads, SMEM_BYTES));
+    if (per_sm < 1) return fail(PQ_ECUDA, "persistent tensor-core fit: no CTA fits an SM");
+    const int grid = std::max(1, std::min(a.units, per_sm * sms));
+    void *args[] = {&map, &a};
+    ProfScope ps("pq_fit_persistent_tc", s);
+    PQ_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)pq_pass_tc_kernel<true>, dim3(grid), dim3(kThreads), args,
+                                            SMEM_BYTES, s));
     count_launch();
     PQ_TRY_CUDA(cudaGetLastError());
     return PQ_OK;
