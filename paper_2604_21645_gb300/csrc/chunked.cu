@@ -230,10 +230,9 @@ int run_pq_fit_chunked(const float *X, const int64_t *off, int n_chunks, int D, 
     }
     if (tc) {
         // all the passes of every (chunk, subspace group) in one persistent launch
-        int *arrive = ws.get<int>((size_t)n_chunks * (M / tc_pass_group()), true);
-        int *ready = ws.get<int>((size_t)n_chunks * (M / tc_pass_group()), true);
+        int *sync = ws.get<int>(persistent_sync_ints(n_chunks, M), true);
         if (ws.status) return ws.status;
-        PQ_TRY(launch_pq_fit_persistent_tc(p, iters, arrive, ready, counts, s));
+        PQ_TRY(launch_pq_fit_persistent_tc(p, iters, sync, counts, s));
     } else {
         for (int t = 0; t < iters; ++t) {
             PQ_TRY(launch_pq_pass_f32(p, s));
@@ -338,9 +337,8 @@ int run_pq_tune_chunked(const float *X, const int64_t *off, int n_chunks, int D,
     int *d_blk = ws.get<int>((size_t)n_chunks + 1);
     int *d_bc = ws.get<int>((size_t)gmax);
     void *pb = ws.raw(Partials::bytes(gmax, M, Ks, ds, n_chunks), false);
-    const size_t ncg = (size_t)n_chunks * (M / tc_pass_group());
-    int *arrive = tc ? ws.get<int>(ncg) : nullptr;
-    int *ready = tc ? ws.get<int>(ncg) : nullptr;
+    const size_t nsync = persistent_sync_ints(n_chunks, M);
+    int *sync = tc ? ws.get<int>(nsync) : nullptr;
     if (ws.status) return ws.status;
     cudaEvent_t e0, e1;
     PQ_TRY_CUDA(cudaEventCreate(&e0));
@@ -371,9 +369,8 @@ int run_pq_tune_chunked(const float *X, const int64_t *off, int n_chunks, int D,
             // (the codebooks of the tuning run are updated; they are scratch)
             for (int r = 0; r < 2 && st == PQ_OK; ++r) {
                 if (r == 1) cudaEventRecord(e0, s);
-                cudaError_t ce = cudaMemsetAsync(arrive, 0, ncg * sizeof(int), s);
-                if (ce == cudaSuccess) ce = cudaMemsetAsync(ready, 0, ncg * sizeof(int), s);
-                st = ce == cudaSuccess ? launch_pq_fit_persistent_tc(p, r == 0 ? 1 : 3, arrive, ready, nullptr, s)
+                const cudaError_t ce = cudaMemsetAsync(sync, 0, nsync * sizeof(int), s);
+                st = ce == cudaSuccess ? launch_pq_fit_persistent_tc(p, r == 0 ? 1 : 3, sync, nullptr, s)
                                        : cuda_check(ce, "pq_tune_chunked");
             }
         } else {

@@ -146,9 +146,10 @@ int launch_pq_pass_tc(PqPass &p, cudaStream_t s);
 // All `iters` Lloyd passes of the batched form (p: chunk table and partial sums set, p.gx its
 // blocks) in one persistent cooperative launch: the (block, subspace group) units are shared out
 // over the resident CTAs, and after each pass the last unit of a (chunk, group) to finish moves that
-// chunk's codebooks (p.C, in place).  arrive/ready: n_chunks * (M / 2) zeroed ints; counts: the
-// member counts of the last update, or null.
-int launch_pq_fit_persistent_tc(PqPass &p, int iters, int *arrive, int *ready, long long *counts, cudaStream_t s);
+// chunk's codebooks (p.C, in place).  sync: persistent_sync_ints(p) zeroed ints (arrival counters,
+// ready flags, the unit counter); counts: the member counts of the last update, or null.
+int launch_pq_fit_persistent_tc(PqPass &p, int iters, int *sync, long long *counts, cudaStream_t s);
+inline size_t persistent_sync_ints(int n_chunks, int M) { return (size_t)n_chunks * (M / 2) * 2 + 1; }
 
 // ---- coarse quantizer and inverted lists (coarse.cu) ----------------------
 struct CoarseBound {

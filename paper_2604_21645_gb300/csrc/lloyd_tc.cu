@@ -132,12 +132,13 @@ struct TcArgs {
     const int64_t *chunk_off;
     const int *chunk_blk;
     // persistent form (the batched Lloyd iterations in one launch): `iters` passes over `units`
-    // (x, group) units of the chunk table (x < gxu), shared out over the CTAs; after each pass over
-    // a (chunk, group) the last of its units to finish moves its codebooks (Cw) and publishes the
-    // pass in ready[chunk * groups + group], counting arrivals in arrive[]
+    // (x, group) units of the chunk table (x < gxu); the CTAs take the units of every pass in order
+    // from the counter *next; after each pass over a (chunk, group) the last of its units to finish
+    // moves its codebooks (Cw) and publishes the pass in ready[chunk * groups + group], counting
+    // arrivals in arrive[]
     int iters, units, gxu;
     float *Cw;
-    int *arrive, *ready;
+    int *arrive, *ready, *next;
     long long *counts;         // member counts of the last update, or null
 };
 
@@ -395,10 +396,22 @@ __global__ void __maxnreg__(kRegLaunch) pq_pass_tc_kernel(const __grid_constant_
     const uint32_t tmem = *tslot;
 
     const int n_iter = PERSIST ? a.iters : 1;
-    const int n_units = PERSIST ? a.units : 1;
-    bool live = true;  // CTA-uniform: false once a wait for another CTA ran out
-    for (int it = 0; it < n_iter && live; ++it)
-    for (int uu = PERSIST ? (int)blockIdx.x : 0; uu < n_units && live; uu += PERSIST ? (int)gridDim.x : 1) {
+    __shared__ int s_q;
+    // the units, pass after pass: a CTA takes the next one in order (pass t's units all come before
+    // pass t + 1's, so a unit only waits for units already taken, by CTAs that are all resident)
+    for (int q_local = 0;; ++q_local) {
+    int q;
+    if constexpr (PERSIST) {
+        if (tid == 0) s_q = atomicAdd(a.next, 1);
+        __syncthreads();
+        q = s_q;
+        if (q >= a.iters * a.units) break;
+    } else {
+        if (q_local > 0) break;
+        q = 0;
+    }
+    const int it = PERSIST ? q / a.units : 0;
+    const int uu = PERSIST ? q % a.units : 0;
     const int ux = PERSIST ? uu % a.gxu : (int)blockIdx.x;
     const int grp = PERSIST ? uu / a.gxu : (int)blockIdx.y, m0 = grp * G;
     // chunk of this unit (batched form): its rows, its share of the units, its codebooks
@@ -434,10 +447,7 @@ __global__ void __maxnreg__(kRegLaunch) pq_pass_tc_kernel(const __grid_constant_
             s_flag = ok;
         }
         __syncthreads();
-        if (!s_flag) {
-            live = false;
-            break;
-        }
+        if (!s_flag) break;
     }
 
     // ---- set-up: codeword mean, B operands, FP32 copies, bounds -------------
@@ -932,7 +942,7 @@ int launch_pq_pass_tc(PqPass &p, cudaStream_t s)
     return PQ_OK;
 }
 
-int launch_pq_fit_persistent_tc(PqPass &p, int iters, int *arrive, int *ready, long long *counts, cudaStream_t s)
+int launch_pq_fit_persistent_tc(PqPass &p, int iters, int *sync, long long *counts, cudaStream_t s)
 {
     if (!p.part.active() || !p.chunk_blk || p.gx <= 0)
         return fail(PQ_EINTERNAL, "persistent tensor-core fit needs a chunk table and partial sums");
@@ -944,8 +954,10 @@ int launch_pq_fit_persistent_tc(PqPass &p, int iters, int *arrive, int *ready, l
     a.gxu = p.gx;
     a.units = p.gx * (p.M / G);
     a.Cw = const_cast<float *>(p.C);
-    a.arrive = arrive;
-    a.ready = ready;
+    const int ncg = p.n_chunks * (p.M / G);
+    a.arrive = sync;
+    a.ready = sync + ncg;
+    a.next = sync + 2 * ncg;
     a.counts = counts;
     PQ_TRY_CUDA(cudaFuncSetAttribute(pq_pass_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     // every CTA must be resident at once (a unit may wait for units of other CTAs): a cooperative
