@@ -269,7 +269,7 @@ int softpq_backward(const float *X, int64_t N, int32_t D, int32_t M, int32_t Ks,
  * pq_tune_chunked -- autotuner of the batched Lloyd passes of pq_fit_chunked.
  *   Same X, chunk_offsets (HOST array), n_chunks, D, M, Ks and prec rules as
  *   pq_fit_chunked.  Seeds every chunk, then, for each candidate number of work
- *   units per subspace group (0.5x to 4x the default, shared out over the chunks
+ *   units per subspace group (0.5x to 8x the default, shared out over the chunks
  *   in proportion to their rows, so that a unit is a run of ceil(tiles / units)
  *   128-row tiles of one chunk), times the batched passes: BF16, the persistent
  *   launch of three passes after a one-pass warm-up; FP32, the mean of three

@@ -324,7 +324,7 @@ int run_pq_tune_chunked(const float *X, const int64_t *off, int n_chunks, int D,
     PQ_TRY(launch_kmeanspp_chunks(X, D, ch.data(), n_chunks, ds, M, Ks, Cl, ws, err, s, "kmeanspp_chunks"));
     // candidate block counts around the default; the part buffers are sized for the largest
     const int base = default_per(sms, N, M, tc);
-    const double scales[] = {0.5, 0.75, 1.0, 1.25, 1.5, 2.0, 3.0, 4.0};
+    const double scales[] = {0.5, 0.75, 1.0, 1.5, 2.0, 3.0, 4.0, 6.0, 8.0};
     std::vector<int> cand;
     for (double f : scales) {
         const int v = std::max(1, (int)std::llround(base * f));
