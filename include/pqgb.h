@@ -372,12 +372,15 @@ int64_t pq_launch_count(void);
  * Failure injection for tests of the failure handling (no counterpart in the
  * paper).  Process-wide settings; they exercise error paths without faulting
  * or hanging the GPU.
- * pq_test_set_spin_limit -- poll budget of the k-means++ seeding's waits on
- *   other blocks (its group barrier and its per-round sum polls), normally
- *   2^22 polls.  A small budget makes a wait run out: the block records
- *   PQ_ETIMEOUT in the device error word and the kernel's blocks return (the
- *   seeding has no bulk copies in flight to wait for); pq_sync_status then
- *   returns PQ_ETIMEOUT and clears the word.  0 restores the default.
+ * pq_test_set_spin_limit -- poll budget of the waits on other blocks: the
+ *   k-means++ seeding's (its group barrier and its per-round sum polls) and the
+ *   persistent batched fit's (a unit's wait for the previous pass of its chunk
+ *   and subspace group), normally 2^22 polls.  A small budget makes a wait run
+ *   out: the block records PQ_ETIMEOUT in the device error word and returns (no
+ *   bulk copies or MMAs of its own are in flight at these waits), the other
+ *   blocks' waits give up on seeing the error word, and the call's later kernels
+ *   finish or give up the same way; pq_sync_status then returns PQ_ETIMEOUT and
+ *   clears the word.  0 restores the default.
  * pq_test_fail_alloc_after -- the (n+1)-th scratch allocation from now fails
  *   as if the device were out of memory: the call returns PQ_ENOMEM at that
  *   point, releasing the scratch it already took.  n < 0 turns this off.

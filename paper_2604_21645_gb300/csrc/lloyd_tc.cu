@@ -139,6 +139,7 @@ struct TcArgs {
     int iters, units, gxu;
     float *Cw;
     int *arrive, *ready, *next;
+    unsigned spin;             // poll budget of a unit's wait for the previous pass
     long long *counts;         // member counts of the last update, or null
 };
 
@@ -432,7 +433,7 @@ __global__ void __maxnreg__(kRegLaunch) pq_pass_tc_kernel(const __grid_constant_
         if (tid == 0) {
             int ok = 1;
             for (unsigned spin = 0; *(volatile int *)(a.ready + cg) < it; ++spin) {
-                if (spin > kSpinLimit) {
+                if (spin > a.spin) {
                     atomicCAS(a.err, 0, PQ_ETIMEOUT);
                     ok = 0;
                     break;
@@ -959,6 +960,7 @@ int launch_pq_fit_persistent_tc(PqPass &p, int iters, int *sync, long long *coun
     a.ready = sync + ncg;
     a.next = sync + 2 * ncg;
     a.counts = counts;
+    a.spin = seeding_spin_limit();
     PQ_TRY_CUDA(cudaFuncSetAttribute(pq_pass_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     // every CTA must be resident at once (a unit may wait for units of other CTAs): a cooperative
     // launch of at most the co-resident CTAs

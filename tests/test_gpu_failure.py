@@ -69,3 +69,32 @@ def test_injected_allocation_failure_returns_enomem(pq, after):
     got = pq.fit(Xd, 4, 32, iters=2, seed=3)
     ref, _ = orc.pq_fit(X, 4, 32, 2, 3)
     np.testing.assert_allclose(got.cpu().numpy(), ref, rtol=0, atol=1e-5 * np.abs(ref).max())
+
+
+def test_persistent_batched_fit_wait_that_runs_out_reports_timeout(pq):
+    """The persistent batched fit: a unit of pass t + 1 waits for the previous pass of its (chunk,
+    subspace group).  Here a pass has fewer units than there are resident CTAs, so CTAs take
+    pass-1 units while pass 0 still runs; with a one-poll budget those waits run out, the CTAs
+    leave, the call finishes, and pq_sync_status reports PQ_ETIMEOUT once.  The next call, with
+    the default budget, gives the same model as a call before the failure."""
+    X = datagen.mixture(200_000, 32, 20, "cont", 33)
+    Xd = torch.from_numpy(X).cuda()
+    off = [0, 90_000, 200_000]
+    M, Ks = 4, 64
+    pq.tune_clear()
+    pq.sync_status()
+    ref_cb, ref_codes, _ = pq.fit_chunked(Xd, off, M, Ks, iters=6, seed=5, prec="bf16", want_rmse=False)
+    pq.sync_status()
+    ref_cb, ref_codes = ref_cb.clone(), ref_codes.clone()
+    try:
+        pq.lib().pq_test_set_spin_limit(1)
+        pq.fit_chunked(Xd, off, M, Ks, iters=6, seed=5, prec="bf16", want_rmse=False)
+        with pytest.raises(pq.PqError) as e:
+            pq.sync_status()
+        assert e.value.status == pq.PQ_ETIMEOUT
+    finally:
+        pq.lib().pq_test_set_spin_limit(0)
+    pq.sync_status()  # the error word was cleared
+    cb, codes, _ = pq.fit_chunked(Xd, off, M, Ks, iters=6, seed=5, prec="bf16", want_rmse=False)
+    pq.sync_status()
+    assert torch.equal(cb, ref_cb) and torch.equal(codes, ref_codes)
