@@ -149,8 +149,11 @@ __device__ __forceinline__ void load_codes(const uint8_t *p, uint8_t (&c)[M])
 }
 
 constexpr int kScanThreads = 256;
-constexpr int kSelCap = 2048;   // candidate buffer entries per query
-constexpr int kSamples = 512;   // codes scored first to set the candidate threshold
+constexpr int kSelCap = 2048;      // candidate buffer entries per query
+constexpr int kSamples = 512;      // codes scored first to set the candidate threshold ...
+constexpr int kSamplesBig = 2048;  // ... and for a query with more than kBigScan probed codes
+constexpr int kBigScan = 131072;
+static_assert(kSamplesBig <= kSelCap, "the sample is sorted in the candidate buffer");
 
 // In-place ascending bitonic sort of n (power of two) entries by every thread of the block.
 __device__ void bitonic_sort_n(Cand *v, int n)
@@ -181,11 +184,35 @@ __device__ __forceinline__ float adc_score(const float *lut, const uint8_t *code
     return d;
 }
 
+// The same sum, left as soon as a partial sum exceeds tau.  Every LUT entry is a
+// squared distance (>= 0) and a rounded FP32 sum of non-negative terms never
+// decreases, so the full score of a code left early is above tau as well: the codes
+// kept, and their scores (same terms in the same order), are those of adc_score.
+template <int M, int KS>
+__device__ __forceinline__ float adc_score_below(const float *lut, const uint8_t *code, float tau)
+{
+    uint8_t c[M];
+    load_codes<M>(code, c);
+    float d = 0.0f;
+#pragma unroll
+    for (int m = 0; m < M / 2; ++m) d += lut[m * KS + c[m]];
+    if (d > tau) return d;
+#pragma unroll
+    for (int m = M / 2; m < (3 * M) / 4; ++m) d += lut[m * KS + c[m]];
+    if (d > tau) return d;
+#pragma unroll
+    for (int m = (3 * M) / 4; m < M; ++m) d += lut[m * KS + c[m]];
+    return d;
+}
+
 // Scan of one query (one block), in two phases.  (1) A threshold: the scores of
-// kSamples codes spread evenly over the probed lists are sorted and the one at about
-// twice the expected rank of k is taken.  (2) Every probed code is scored and the
-// ones at or below the threshold (all ties included) go to the candidate buffer,
-// which is sorted by (score, id) at the end.  If the threshold turns out too tight
+// S codes spread evenly over the probed lists are sorted (S = 512, or 2048 above
+// kBigScan codes) and the one at about twice the expected rank of k is taken, but no
+// higher than the rank expected to hold half the candidate buffer (with n probed
+// codes, sample rank r stands for about (r + 1) n / (S + 1) codes).  (2) Every probed
+// code is scored, left early once a partial sum passes the threshold, and the ones at
+// or below the threshold (all ties included) go to the candidate buffer, which is
+// sorted by (score, id) at the end.  If the threshold turns out too tight
 // (fewer than k candidates) or too loose (buffer full), the scan is repeated with the
 // threshold at +inf and the buffer compacted by sorting whenever it fills.
 template <int M, int KS>
@@ -240,16 +267,19 @@ __global__ void __launch_bounds__(kScanThreads) adc_scan_kernel(const float *__r
     };
     // ---- (1) threshold from a sorted sample --------------------------------
     float tau = FLT_MAX;
-    if (n > kSamples) {
-        for (int j = threadIdx.x; j < kSamples; j += kScanThreads) {
+    const int S = n > kBigScan ? kSamplesBig : kSamples;
+    if (n > S) {
+        for (int j = threadIdx.x; j < S; j += kScanThreads) {
             int p;
-            const int pos = (int)(((int64_t)j * n) / kSamples);
+            const int pos = (int)(((int64_t)j * n) / S);
             buf[j].d = adc_score<M, KS>(lut, code_at(pos, p));
             buf[j].id = j;
         }
-        bitonic_sort_n(buf, kSamples);
-        const int r = (int)(((int64_t)2 * k * kSamples + n - 1) / n) + 2;
-        tau = r < kSamples ? buf[r].d : FLT_MAX;
+        bitonic_sort_n(buf, S);
+        const int64_t r_lo = ((int64_t)2 * k * S + n - 1) / n + 2;         // about twice the rank of k
+        const int64_t r_hi = (int64_t)(kSelCap / 2) * (S + 1) / n - 1;     // about half the buffer
+        const int64_t r = min(r_lo, r_hi);
+        tau = r < S ? buf[max(r, (int64_t)0)].d : FLT_MAX;
         __syncthreads();
     }
     // ---- (2) filtered scan, repeated without a threshold if it missed -------
@@ -266,7 +296,7 @@ __global__ void __launch_bounds__(kScanThreads) adc_scan_kernel(const float *__r
             for (int e0 = 0; e0 < len; e0 += kScanThreads) {
                 const int e = e0 + threadIdx.x;
                 if (e < len) {
-                    const float d = adc_score<M, KS>(lut, lc + (size_t)e * M);
+                    const float d = adc_score_below<M, KS>(lut, lc + (size_t)e * M, tau);
                     if (d <= tau) {
                         const int slot = atomicAdd(&s_count, 1);
                         if (slot < kSelCap) {

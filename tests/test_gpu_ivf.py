@@ -108,6 +108,28 @@ def test_search_matches_oracle(pq, setup, nprobe, k):
     assert ties <= 0.01 * ref_ids.size
 
 
+@pytest.mark.parametrize("D,M", [(32, 8), (64, 16)])
+def test_search_long_scans_match_oracle(pq, D, M):
+    """Queries that probe more than 131,072 codes (about 200k here: 4 lists, nprobe 2) take the larger
+    threshold sample, and codes whose partial score passes the threshold are left early: the top-k
+    still equals the oracle's (ids exact except counted near-ties, distances within 1e-5 relative)."""
+    N, Ks, nlist = 400_009, 64, 4
+    X = datagen.mixture(N, D, 60, "int255", 9100 + D)
+    cb, _ = orc.pq_fit(X[:20_000], M, Ks, 3, 11)
+    codes = orc.pq_encode(X, cb)
+    ref = orc.ivf_build(X, codes, nlist, 2, 13)
+    idx = pq.IVFIndex.build(dev(X), dev(codes), nlist, iters=2, seed=13)
+    off = idx.lists()[0].cpu().numpy()
+    Q = datagen.queries(64, D, 60, "int255", 9100 + D)
+    ref_ids, ref_d, _ = orc.ivf_search(ref, cb, Q, 2, 100)
+    ids, d = idx.search(dev(cb), dev(Q), 2, 100)
+    idx.close()
+    # most queries scan more than 131,072 codes
+    assert np.sort(np.diff(off))[-2:].sum() > 131_072
+    ties = check_topk(ids.cpu().numpy(), d.cpu().numpy(), ref_ids, ref_d)
+    assert ties <= 0.01 * ref_ids.size
+
+
 def test_search_pads_missing_results(pq):
     N, D, M, Ks, nlist = 2_000, 16, 4, 16, 40
     X = datagen.mixture(N, D, 8, "cont", 5)
