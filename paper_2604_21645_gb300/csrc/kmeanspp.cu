@@ -428,6 +428,22 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
         part = warp_sum(part);
         if ((tid & 31) == 0) s_warp[tid >> 5] = part;
         __syncthreads();
+        const uint64_t r = rng_draw(seed, (uint64_t)m, (uint64_t)t) >> 11;
+        if (solo) {
+            // a block alone in its group owns the whole threshold: no publication and no poll
+            if (tid == 0) {
+                uint64_t W = 0;
+                for (int w = 0; w < kWarps; ++w) W += s_warp[w];
+                s_fail = 0;
+                if (W == 0) {
+                    s_pick = scale_index(r, (uint64_t)n);
+                } else {
+                    s_pick = -1;
+                    s_owner = b;
+                    s_thr = (__umul64hi(r, W) << 11) | ((r * W) >> 53);
+                }
+            }
+        } else {
         if (tid == 0) {
             uint64_t tot = 0;
             for (int w = 0; w < kWarps; ++w) tot += s_warp[w];
@@ -439,7 +455,6 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
 
         // every block: wait for all round-t sums of its group, then find the owner block and
         // threshold.  Lane l polls and holds the sums of blocks [l*kPer, (l+1)*kPer).
-        const uint64_t r = rng_draw(seed, (uint64_t)m, (uint64_t)t) >> 11;
         if (tid < 32) {
             const unsigned *tg = tags + (size_t)cur * bplane * kTagStride;
             bool ok = true;
@@ -497,6 +512,7 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
             }
             if (tid == 0) s_pick = p;
         }
+        }
         __syncthreads();
         if (s_fail) return;
         if (s_pick < 0) {
@@ -533,14 +549,39 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
                     s_pick = hit;
                 }
             } else {
-                for (int i = s0; i < s1; ++i) w += weight(src ? src[i] : __ldcg(D2c + o0 + i), sh, any);
+                // eight values in flight at a time (the weights are integers: the order of the sum is free)
+                auto d2at = [&](int i) { return src ? src[i] : __ldcg(D2c + o0 + i); };
+                int i = s0;
+                for (; i + 8 <= s1; i += 8) {
+                    float dv[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) dv[q] = d2at(i + q);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) w += weight(dv[q], sh, any);
+                }
+                for (; i < s1; ++i) w += weight(d2at(i), sh, any);
                 const uint64_t incl = block_scan_u64(w, s_warp);
                 const uint64_t excl = incl - w;
                 if (excl <= thr_local && thr_local < incl) {
+                    // the block of eight that crosses the threshold, then its values one at a time
                     uint64_t acc = excl;
-                    for (int i = s0; i < s1; ++i) {
-                        acc += weight(src ? src[i] : __ldcg(D2c + o0 + i), sh, any);
-                        if (acc > thr_local) { s_pick = o0 + i; break; }
+                    int j = s0;
+                    for (; j + 8 <= s1; j += 8) {
+                        float dv[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) dv[q] = d2at(j + q);
+                        uint64_t bs = 0;
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) bs += weight(dv[q], sh, any);
+                        if (acc + bs > thr_local) break;
+                        acc += bs;
+                    }
+                    for (; j < s1; ++j) {
+                        acc += weight(d2at(j), sh, any);
+                        if (acc > thr_local) {
+                            s_pick = o0 + j;
+                            break;
+                        }
                     }
                 }
             }
