@@ -232,3 +232,41 @@ def test_full_size_search_matches_oracle(pq):
     ties = check_topk(got_ids.cpu().numpy()[sample], got_d.cpu().numpy()[sample], o_ids, o_d)
     print("near-tie id differences", ties, "of", o_ids.size)
     assert ties <= 0.01 * o_ids.size
+
+
+@pytest.mark.slow
+def test_full_size_10m_search_matches_oracle(pq):
+    """The benchmarked 10M search (10M x 128, nlist=1024, nprobe=16, top-100; about 445k probed codes per
+    query, more than the scan's large-sample threshold) against the oracle's search over the same index on
+    64 sampled queries.  The index is pinned by samples: 4,000 sampled rows lie in the list of their exact
+    FP64 nearest coarse centroid (the oracle's assignment) and carry the oracle's codes under the GPU's
+    codebooks.  Ids exact except counted near-ties, distances within 1e-5 relative."""
+    w = datagen.IVF_10M
+    X = w.data()
+    Xd = dev(X)
+    cbs = pq.fit(Xd, w.m, w.ks, iters=w.iters, seed=w.init_seed, prec="bf16")
+    cb = cbs.cpu().numpy()
+    codes = pq.encode(Xd, cbs, prec="bf16")
+    idx = pq.IVFIndex.build(Xd, codes, w.nlist, iters=w.ivf_iters, seed=w.coarse_seed, prec="bf16")
+    del Xd
+    torch.cuda.empty_cache()
+    coarse = idx.coarse().cpu().numpy()
+    off, ids, lcodes = (t.cpu().numpy() for t in idx.lists())
+    assert off[0] == 0 and off[-1] == w.n and np.all(np.diff(off) >= 0)
+    list_of = np.empty(w.n, dtype=np.int64)
+    list_of[ids] = np.repeat(np.arange(w.nlist), np.diff(off))
+    rows = np.sort(np.random.default_rng(5).choice(w.n, 4000, replace=False))
+    ref_lists, _, _ = orc.assign(X[rows], coarse[None])
+    assert np.array_equal(list_of[rows], ref_lists[:, 0])
+    pos = np.empty(w.n, dtype=np.int64)
+    pos[ids] = np.arange(w.n)
+    assert np.array_equal(lcodes[pos[rows]], orc.pq_encode(X[rows], cb))
+    Q = w.queries()
+    got_ids, got_d = idx.search(cbs, dev(Q), w.nprobe, w.topk)
+    idx.close()
+    sample = np.sort(np.random.default_rng(8).choice(w.nq, 64, replace=False))
+    ref = {"coarse": coarse, "offsets": off, "ids": ids, "list_codes": lcodes}
+    o_ids, o_d, _ = orc.ivf_search(ref, cb, Q[sample], w.nprobe, w.topk)
+    ties = check_topk(got_ids.cpu().numpy()[sample], got_d.cpu().numpy()[sample], o_ids, o_d)
+    print("near-tie id differences", ties, "of", o_ids.size)
+    assert ties <= 0.01 * o_ids.size
