@@ -444,74 +444,74 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
                 }
             }
         } else {
-        if (tid == 0) {
-            uint64_t tot = 0;
-            for (int w = 0; w < kWarps; ++w) tot += s_warp[w];
-            unsigned *line = tags + ((size_t)cur * bplane + b) * kTagStride;
-            *reinterpret_cast<unsigned long long *>(line + 2) = tot;
-            // publishes the sum and (ordered before it by the __syncthreads above) the block's D2 copy
-            st_release_u32(line, (unsigned)t);
-        }
+            if (tid == 0) {
+                uint64_t tot = 0;
+                for (int w = 0; w < kWarps; ++w) tot += s_warp[w];
+                unsigned *line = tags + ((size_t)cur * bplane + b) * kTagStride;
+                *reinterpret_cast<unsigned long long *>(line + 2) = tot;
+                // publishes the sum and (ordered before it by the __syncthreads above) the block's D2 copy
+                st_release_u32(line, (unsigned)t);
+            }
 
-        // every block: wait for all round-t sums of its group, then find the owner block and
-        // threshold.  Lane l polls and holds the sums of blocks [l*kPer, (l+1)*kPer).
-        if (tid < 32) {
-            const unsigned *tg = tags + (size_t)cur * bplane * kTagStride;
-            bool ok = true;
-            for (unsigned it = 0;; ++it) {
-                bool mine = true;
+            // every block: wait for all round-t sums of its group, then find the owner block and
+            // threshold.  Lane l polls and holds the sums of blocks [l*kPer, (l+1)*kPer).
+            if (tid < 32) {
+                const unsigned *tg = tags + (size_t)cur * bplane * kTagStride;
+                bool ok = true;
+                for (unsigned it = 0;; ++it) {
+                    bool mine = true;
+#pragma unroll
+                    for (int q = 0; q < kPer; ++q) {
+                        const int bi = tid * kPer + q;
+                        if (bi < a.bps) mine &= ld_acquire_u32(tg + (size_t)bi * kTagStride) == (unsigned)t;
+                    }
+                    if (__all_sync(0xffffffffu, mine)) break;
+                    // warp-uniform decision to give up (bounded wait)
+                    const bool give_up = it >= a.spin || ((it & 255) == 255 && *(volatile int *)a.err != 0);
+                    if (__any_sync(0xffffffffu, give_up)) {
+                        if (tid == 0) atomicCAS(a.err, 0, PQ_ETIMEOUT);
+                        ok = false;
+                        break;
+                    }
+                }
+                if (tid == 0) s_fail = !ok;
+                // each block's sum sits in its tag's line, read after the acquire that saw the tag
+                uint64_t v[kPer];
+                uint64_t tot = 0;
 #pragma unroll
                 for (int q = 0; q < kPer; ++q) {
                     const int bi = tid * kPer + q;
-                    if (bi < a.bps) mine &= ld_acquire_u32(tg + (size_t)bi * kTagStride) == (unsigned)t;
+                    v[q] = bi < a.bps ? *reinterpret_cast<const volatile unsigned long long *>(tg + (size_t)bi * kTagStride + 2)
+                                      : 0ull;
+                    tot += v[q];
                 }
-                if (__all_sync(0xffffffffu, mine)) break;
-                // warp-uniform decision to give up (bounded wait)
-                const bool give_up = it >= a.spin || ((it & 255) == 255 && *(volatile int *)a.err != 0);
-                if (__any_sync(0xffffffffu, give_up)) {
-                    if (tid == 0) atomicCAS(a.err, 0, PQ_ETIMEOUT);
-                    ok = false;
-                    break;
-                }
-            }
-            if (tid == 0) s_fail = !ok;
-            // each block's sum sits in its tag's line, read after the acquire that saw the tag
-            uint64_t v[kPer];
-            uint64_t tot = 0;
+                const uint64_t incl = warp_incl_scan(tot);
+                const uint64_t W = __shfl_sync(0xffffffffu, incl, 31);
+                long long p = -1;
+                if (W == 0) {
+                    p = scale_index(r, (uint64_t)n);
+                } else {
+                    const uint64_t thr = (__umul64hi(r, W) << 11) | ((r * W) >> 53);
+                    const unsigned hit = __ballot_sync(0xffffffffu, incl > thr);
+                    const int l = __ffs(hit) - 1;
+                    if (tid == l) {
+                        uint64_t acc = incl - tot;
+                        int owner = -1;
+                        uint64_t thr_local = 0;
 #pragma unroll
-            for (int q = 0; q < kPer; ++q) {
-                const int bi = tid * kPer + q;
-                v[q] = bi < a.bps ? *reinterpret_cast<const volatile unsigned long long *>(tg + (size_t)bi * kTagStride + 2)
-                                  : 0ull;
-                tot += v[q];
-            }
-            const uint64_t incl = warp_incl_scan(tot);
-            const uint64_t W = __shfl_sync(0xffffffffu, incl, 31);
-            long long p = -1;
-            if (W == 0) {
-                p = scale_index(r, (uint64_t)n);
-            } else {
-                const uint64_t thr = (__umul64hi(r, W) << 11) | ((r * W) >> 53);
-                const unsigned hit = __ballot_sync(0xffffffffu, incl > thr);
-                const int l = __ffs(hit) - 1;
-                if (tid == l) {
-                    uint64_t acc = incl - tot;
-                    int owner = -1;
-                    uint64_t thr_local = 0;
-#pragma unroll
-                    for (int q = 0; q < kPer; ++q) {
-                        if (owner < 0 && acc + v[q] > thr) {
-                            owner = tid * kPer + q;
-                            thr_local = thr - acc;
+                        for (int q = 0; q < kPer; ++q) {
+                            if (owner < 0 && acc + v[q] > thr) {
+                                owner = tid * kPer + q;
+                                thr_local = thr - acc;
+                            }
+                            acc += v[q];
                         }
-                        acc += v[q];
+                        s_owner = owner;
+                        s_thr = thr_local;
                     }
-                    s_owner = owner;
-                    s_thr = thr_local;
                 }
+                if (tid == 0) s_pick = p;
             }
-            if (tid == 0) s_pick = p;
-        }
         }
         __syncthreads();
         if (s_fail) return;
