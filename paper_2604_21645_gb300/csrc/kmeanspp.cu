@@ -264,8 +264,36 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
     // so that consecutive threads read consecutive addresses.  The copy is written by this kernel
     // (round 0), so it is read through L2 (ld.global.cg), not the read-only cache path.
     float4 *gp4 = reinterpret_cast<float4 *>(gp0);
+    // Which thread folds which point.  Several blocks per group: thread t takes points t, t + kThreads, ...;
+    // the first ncache points are cached (slot i), the rest are in the gathered copy (slot i - ncache).
+    // A block alone in its group (with a gathered copy): warp w takes the consecutive range [wlo, whi) and
+    // lane l the consecutive piece [wlo + l*piece, wlo + (l+1)*piece) of it, so that the lane and warp sums
+    // are sums of consecutive points and the walk goes straight to one piece.  The first cpl points of
+    // every piece are cached, so that every lane has the same share of shared-memory and gathered points;
+    // cache and gathered copy store point k of lane l's piece at slot 32k + l of the warp's part, so that a
+    // warp's loads are consecutive.
+    const bool wr = solo && gp0 != nullptr;
+    const int wid = tid >> 5, lane = tid & 31;
+    const int wlen = (int)(((int64_t)cnt + 32 * kWarps - 1) / (32 * kWarps)) * 32;
+    const int piece = wlen / 32;
+    const int wlo = wr ? min(cnt, wid * wlen) : 0;
+    const int whi = wr ? min(cnt, wlo + wlen) : cnt;
+    const int cpw = wr ? min(wlen, (a.ncache / kWarps) & ~31) : 0;
+    const int cpl = cpw / 32;
+    const int pfirst = wr ? min(whi, wlo + lane * piece) : tid;   // a thread's first point
+    const int pstep = wr ? 1 : kThreads;                          // and the stride of its points
+    const int pend = wr ? min(whi, pfirst + piece) : cnt;         // up to
+    const int pcache = wr ? min(pend, pfirst + cpl) : ncache;     // its points below pcache are cached
+    const int smul = wr ? 32 : 1;                                 // slot of point i: (i - pfirst) * smul + base
+    const int cbase = wr ? wid * cpw + lane : pfirst;
+    const int gbase = wr ? wid * (wlen - cpw) + lane - 32 * cpl : pfirst - ncache;
+    // cache rows: the transposed slots of a range can pass its point count, so the warp-range layout uses
+    // the allocation's row length (slots < kWarps * cpw <= a.ncache)
+    const int cstride = wr ? a.ncache : ncache;
+    auto cslot = [&](int i) { return (i - pfirst) * smul + cbase; };
+    auto gslot = [&](int i) { return (i - pfirst) * smul + gbase; };
     auto upiece = [&](int i, int q) -> float4 {
-        return gp0 ? __ldcg(gp4 + (size_t)q * a.ustride + (i - ncache))
+        return gp0 ? __ldcg(gp4 + (size_t)q * a.ustride + gslot(i))
                    : __ldg(reinterpret_cast<const float4 *>(point(i0 + i)) + q);
     };
     const float4 *pts4 = s_dyn + a.nb_pad / 4;
@@ -287,14 +315,14 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
     }
     __syncthreads();
     float lmax = 0.0f;
-    for (int i = tid; i < cnt; i += kThreads) {
+    for (int i = pfirst; i < pend; i += pstep) {
         float d;
-        if (i < ncache) {
+        if (i < pcache) {
             const float *x = point(i0 + i);
             float acc = 0.0f;
             for (int q = 0; q < ds / 4; ++q) {
                 const float4 v = __ldg(reinterpret_cast<const float4 *>(x) + q);
-                pts4w[q * ncache + i] = v;
+                pts4w[q * cstride + cslot(i)] = v;
                 const float4 cc = *reinterpret_cast<const float4 *>(s_center + 4 * q);
                 const float e[4] = {v.x, v.y, v.z, v.w};
                 const float f[4] = {cc.x, cc.y, cc.z, cc.w};
@@ -307,7 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
             d = acc;
         } else if (gp0) {
             const float *x = point(i0 + i);
-            float4 *dst = gp4 + (i - ncache);
+            float4 *dst = gp4 + gslot(i);
             float acc = 0.0f;
             for (int q = 0; q < ds / 4; ++q) {
                 const float4 v = __ldg(reinterpret_cast<const float4 *>(x) + q);
@@ -359,23 +387,23 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
         // the block's own D2 values live in shared memory, the global copy serves the walk
         uint64_t part = 0;
         if (t == 1) {
-            for (int i = tid; i < cnt; i += kThreads) part += weight(s_d2[i], sh, any);
+            for (int i = pfirst; i < pend; i += pstep) part += weight(s_d2[i], sh, any);
         } else {
-            int i = tid;
-            for (; i < ncache; i += kThreads) {
-                const float d = fminf(d2_f32_smem(pts4, ncache, i, s_center, ds), s_d2[i]);
+            int i = pfirst;
+            for (; i < pcache; i += pstep) {
+                const float d = fminf(d2_f32_smem(pts4, cstride, cslot(i), s_center, ds), s_d2[i]);
                 s_d2[i] = d;
                 if (!solo) D2c[i0 + i] = d;
                 part += weight(d, sh, any);
             }
             if (vec_ok && ds == 8) {
                 // eight uncached points per thread, all their loads in flight before the sums
-                for (; i + 7 * kThreads < cnt; i += 8 * kThreads) {
+                for (; i + 7 * pstep < pend; i += 8 * pstep) {
                     float4 u[8][2];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
-                        u[q][0] = upiece(i + q * kThreads, 0);
-                        u[q][1] = upiece(i + q * kThreads, 1);
+                        u[q][0] = upiece(i + q * pstep, 0);
+                        u[q][1] = upiece(i + q * pstep, 1);
                     }
                     const float4 c0 = *reinterpret_cast<const float4 *>(s_center);
                     const float4 c1 = *reinterpret_cast<const float4 *>(s_center + 4);
@@ -390,7 +418,7 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
                             const float t = __fsub_rn(e[r], f[r]);
                             acc = __fadd_rn(acc, __fmul_rn(t, t));
                         }
-                        const int ii = i + q * kThreads;
+                        const int ii = i + q * pstep;
                         const float d = fminf(acc, s_d2[ii]);
                         s_d2[ii] = d;
                         if (!solo) D2c[i0 + ii] = d;
@@ -399,23 +427,23 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
                 }
             }
             if (vec_ok) {
-                for (; i + kThreads < cnt; i += 2 * kThreads) {
+                for (; i + pstep < pend; i += 2 * pstep) {
                     float d0, d1;
-                    const int ia = i, ib = i + kThreads;
+                    const int ia = i, ib = i + pstep;
                     d2_f32_pieces2([&](int q) { return upiece(ia, q); }, [&](int q) { return upiece(ib, q); }, s_center, ds,
                                    d0, d1);
                     d0 = fminf(d0, s_d2[i]);
-                    d1 = fminf(d1, s_d2[i + kThreads]);
+                    d1 = fminf(d1, s_d2[i + pstep]);
                     s_d2[i] = d0;
-                    s_d2[i + kThreads] = d1;
+                    s_d2[i + pstep] = d1;
                     if (!solo) {
                         D2c[i0 + i] = d0;
-                        D2c[i0 + i + kThreads] = d1;
+                        D2c[i0 + i + pstep] = d1;
                     }
                     part += weight(d0, sh, any) + weight(d1, sh, any);
                 }
             }
-            for (; i < cnt; i += kThreads) {
+            for (; i < pend; i += pstep) {
                 const int ia = i;
                 const float d = fminf(vec_ok ? d2_f32_pieces([&](int q) { return upiece(ia, q); }, s_center, ds)
                                              : d2_f32_exact(point(i0 + i), s_center, ds),
@@ -425,23 +453,31 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
                 part += weight(d, sh, any);
             }
         }
+        const uint64_t lane_part = part;  // the sum of this lane's piece (warp-range layout)
         part = warp_sum(part);
         if ((tid & 31) == 0) s_warp[tid >> 5] = part;
         __syncthreads();
         const uint64_t r = rng_draw(seed, (uint64_t)m, (uint64_t)t) >> 11;
         if (solo) {
-            // a block alone in its group owns the whole threshold: no publication and no poll
-            if (tid == 0) {
-                uint64_t W = 0;
-                for (int w = 0; w < kWarps; ++w) W += s_warp[w];
-                s_fail = 0;
+            // a block alone in its group owns the whole threshold: no publication and no poll.  Warp 0 scans
+            // the warp sums; in the warp-range layout the first warp whose inclusive sum passes the
+            // threshold holds it
+            if (tid < 32) {
+                const uint64_t v = tid < kWarps ? s_warp[tid] : 0ull;
+                const uint64_t incl = warp_incl_scan(v);
+                const uint64_t W = __shfl_sync(0xffffffffu, incl, 31);
                 if (W == 0) {
-                    s_pick = scale_index(r, (uint64_t)n);
+                    if (tid == 0) s_pick = scale_index(r, (uint64_t)n);
                 } else {
-                    s_pick = -1;
-                    s_owner = b;
-                    s_thr = (__umul64hi(r, W) << 11) | ((r * W) >> 53);
+                    const uint64_t thr = (__umul64hi(r, W) << 11) | ((r * W) >> 53);
+                    const int ow = __ffs(__ballot_sync(0xffffffffu, tid < kWarps && incl > thr)) - 1;
+                    if (tid == 0) {
+                        s_pick = -1;
+                        s_owner = wr ? ow : b;
+                    }
+                    if (tid == ow) s_thr = wr ? thr - (incl - v) : thr;
                 }
+                if (tid == 0) s_fail = 0;
             }
         } else {
             if (tid == 0) {
@@ -515,7 +551,31 @@ __global__ void __launch_bounds__(kThreads, 1) kmeanspp_kernel(KppArgs a)
         }
         __syncthreads();
         if (s_fail) return;
-        if (s_pick < 0) {
+        if (wr && s_pick < 0) {
+            // only the warp whose range holds the threshold walks: each lane sums a consecutive piece
+            // of the range, one scan of the piece sums finds the lane, which walks its piece
+            if (wid == s_owner) {
+                const uint64_t thr_w = s_thr;
+                const uint64_t incl = warp_incl_scan(lane_part);
+                const uint64_t excl = incl - lane_part;
+                const int hl = __ffs(__ballot_sync(0xffffffffu, excl <= thr_w && thr_w < incl)) - 1;
+                // that lane's piece, 32 values at a time: one weight per lane, a scan, the first lane past
+                // the threshold
+                uint64_t acc = __shfl_sync(0xffffffffu, excl, hl);
+                const int p0 = min(whi, wlo + hl * piece), p1 = min(whi, p0 + piece);
+                for (int base = p0; base < p1; base += 32) {
+                    const int j = base + lane;
+                    const uint64_t inc = warp_incl_scan(j < p1 ? weight(s_d2[j], sh, any) : 0ull) + acc;
+                    const unsigned past = __ballot_sync(0xffffffffu, j < p1 && inc > thr_w);
+                    if (past) {
+                        if (lane == __ffs(past) - 1) s_pick = i0 + j;
+                        break;
+                    }
+                    acc = __shfl_sync(0xffffffffu, inc, 31);
+                }
+            }
+            __syncthreads();
+        } else if (s_pick < 0) {
             // walk the owner's D2 values in order to the threshold (the owner reads its own copy)
             const int owner = s_owner;
             const uint64_t thr_local = s_thr;
@@ -685,6 +745,13 @@ int launch_kmeanspp_chunks(const float *X, int64_t ld, const SeedChunk *chunks, 
         return fail(PQ_ENOTSUP, "k-means++ seeding: %lld points per block exceed shared memory", (long long)nb);
     a.ncache = (ds % 4 == 0) ? (int)std::min<int64_t>(nb, (kDynSmemCap - (int64_t)a.nb_pad * 4) / (ds * 4)) : 0;
     a.ustride = (ds % 4 == 0) ? (int)(a.nb_pad - a.ncache) : 0;
+    if (bps == 1 && a.ustride > 0) {
+        // a block alone in its group caches the first cpw points of each warp's range (see the kernel):
+        // the gathered copy then holds up to kWarps * (wlen - cpw) points
+        const int64_t wlen = (nb + 32 * kWarps - 1) / (32 * kWarps) * 32;
+        const int64_t cpw = std::min<int64_t>(wlen, (a.ncache / kWarps) & ~31);
+        a.ustride = (int)std::max<int64_t>(a.ustride, kWarps * (wlen - cpw));
+    }
     a.gpts = nullptr;
     const size_t dyn = (size_t)a.nb_pad * 4 + (size_t)a.ncache * ds * 4;
     PQ_TRY_CUDA(cudaFuncSetAttribute(kmeanspp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
