@@ -607,6 +607,9 @@ int ivf_build(const float *X, const uint8_t *codes, int64_t N, int32_t D, int32_
         unsigned *xrange = ws.get<unsigned>(2);
         if (ws.status) return cleanup(ws.status);
         CoarseBound b{idx->half_norm, idx->maxes};
+        ListMeanScratch lm;
+        if (iters > 0) st = list_mean_scratch(N, D, nlist, ws, lm);
+        if (st) return cleanup(st);
         if (iters > 0) st = launch_x_exponent_range(X, N, D, xrange, s);
         if (st) return cleanup(st);
         st = seed_codebooks(X, N, D, 1, nlist, seed, idx->coarse, ws, err, s, "kmeanspp_coarse");
@@ -614,7 +617,7 @@ int ivf_build(const float *X, const uint8_t *codes, int64_t N, int32_t D, int32_
             st = launch_coarse_norms(idx->coarse, nlist, D, b, s);
             if (!st) st = coarse_assign(X, N, D, idx->coarse, nlist, b, lst, ws, prec, s);
             if (!st) st = bucket_rows(lst, N, nlist, nullptr, M, idx->offsets, idx->ids, nullptr, ws, s);
-            if (!st) st = launch_list_mean(X, D, idx->offsets, idx->ids, nlist, xrange, idx->coarse, s);
+            if (!st) st = launch_list_mean(X, D, idx->offsets, idx->ids, nlist, xrange, idx->coarse, lm, s);
         }
         if (!st) st = launch_coarse_norms(idx->coarse, nlist, D, b, s);
         if (!st) st = coarse_assign(X, N, D, idx->coarse, nlist, b, lst, ws, prec, s);

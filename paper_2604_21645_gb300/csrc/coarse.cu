@@ -13,6 +13,7 @@
 // one thread per dimension, which is exactly the reference computation.
 #include <algorithm>
 #include <cfloat>
+#include <climits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -486,37 +487,77 @@ __device__ double list_sum_fp64_warp(const float *__restrict__ X, int D, const i
     return s;
 }
 
-// One block per list, threads = row groups x columns.  Each thread adds its rows (a stride of
-// the list) exactly into a 128-bit integer; the row groups' partials are combined exactly, so
-// the sum is the same whatever the split.
-__global__ void __launch_bounds__(kMeanThreads) list_mean_kernel(const float *__restrict__ X, int D,
-                                                                 const int64_t *__restrict__ offsets,
-                                                                 const int64_t *__restrict__ ids,
-                                                                 const unsigned *__restrict__ xrange,
-                                                                 float *__restrict__ C)
+// The exact list sums in two kernels, so that a long list is spread over many blocks: its rows are
+// cut into pieces of kPieceRows.  list_partial_kernel: one block per piece, threads = row groups x
+// columns; each thread adds its rows (a stride of the piece) exactly into a 128-bit integer and the
+// row groups' partials are combined exactly.  list_mean_kernel: one block per list adds its pieces'
+// partials exactly, so the sum is the same whatever the split.
+constexpr int kPieceRows = 2048;
+
+// Pieces of every list: list l has pieces [pbeg[l], pbeg[l+1]) (ceil(n_l / kPieceRows) of them), and
+// piece_list[p] is the list of piece p.  One block: thread t takes the lists [t*per, (t+1)*per).
+__global__ void __launch_bounds__(1024) list_pieces_kernel(const int64_t *__restrict__ offsets, int nlist,
+                                                           int *__restrict__ pbeg, int *__restrict__ piece_list)
+{
+    __shared__ int s_sum[1024];
+    const int t = threadIdx.x;
+    const int per = (nlist + 1023) / 1024;
+    const int l0 = min(nlist, t * per), l1 = min(nlist, l0 + per);
+    int c = 0;
+    for (int l = l0; l < l1; ++l) c += (int)((offsets[l + 1] - offsets[l] + kPieceRows - 1) / kPieceRows);
+    s_sum[t] = c;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan of the thread counts
+        const int v = t >= o ? s_sum[t - o] : 0;
+        __syncthreads();
+        s_sum[t] += v;
+        __syncthreads();
+    }
+    int q = s_sum[t] - c;
+    for (int l = l0; l < l1; ++l) {
+        pbeg[l] = q;
+        const int k = (int)((offsets[l + 1] - offsets[l] + kPieceRows - 1) / kPieceRows);
+        for (int i = 0; i < k; ++i) piece_list[q + i] = l;
+        q += k;
+    }
+    if (t == 1023) pbeg[nlist] = s_sum[1023];
+}
+
+// Exact-sum test of a list of n rows: the integer sums fit 128 bits.
+__device__ __forceinline__ bool list_sum_fast(unsigned g, unsigned gmax, int64_t n)
+{
+    const int nbits = 64 - __clzll((unsigned long long)n);
+    return gmax < 255u && (int)(gmax - g) + 24 + nbits + 1 <= 127;
+}
+
+__global__ void __launch_bounds__(kMeanThreads) list_partial_kernel(const float *__restrict__ X, int D,
+                                                                    const int64_t *__restrict__ offsets,
+                                                                    const int64_t *__restrict__ ids,
+                                                                    const unsigned *__restrict__ xrange,
+                                                                    const int *__restrict__ pbeg, int nlist,
+                                                                    const int *__restrict__ piece_list,
+                                                                    const ListMeanScratch part)
 {
     __shared__ unsigned long long s_lo[kMeanThreads], s_hi[kMeanThreads];
     __shared__ unsigned s_neg[kMeanThreads], s_emin[kMeanThreads];
     __shared__ float s_abs[kMeanThreads];
-    __shared__ int s_flag[256];
-    __shared__ int s_nflag;
-    const int l = blockIdx.x;
-    const int64_t b = offsets[l], e = offsets[l + 1];
-    if (e == b) return;  // empty list keeps its centroid
-    const int64_t n = e - b;
-    const int Dp = (D + 31) & ~31, RG = blockDim.x / Dp;
-    const int j = threadIdx.x % Dp, rg = threadIdx.x / Dp;
+    const int pc = blockIdx.x;
+    if (pc >= pbeg[nlist]) return;
+    const int l = piece_list[pc];
+    const int64_t lb = offsets[l], le = offsets[l + 1];
+    const int64_t b = lb + (int64_t)(pc - pbeg[l]) * kPieceRows, e = min(le, b + kPieceRows);
     unsigned g = xrange[0], gmax = xrange[1];
     if (g > gmax) g = gmax = 1u;  // X is all zeros
     // |sum| < n 2^(gmax - 126) = 2^(log2 n + gmax - g + 24) units, plus a sign bit
-    const int nbits = 64 - __clzll((unsigned long long)n);
-    const bool fast = gmax < 255u && (int)(gmax - g) + 24 + nbits + 1 <= 127;
-    if (threadIdx.x == 0) s_nflag = 0;
-    if (fast && rg < RG) {
+    if (!list_sum_fast(g, gmax, le - lb)) return;  // the list is summed in row order by list_mean_kernel
+    const int Dp = (D + 31) & ~31, RG = blockDim.x / Dp;
+    const int j = threadIdx.x % Dp, rg = threadIdx.x / Dp;
+    {
         unsigned long long lo = 0ull, hi = 0ull;
         unsigned nneg = 0u, emin = 255u;
         float sabs = 0.0f;
-        if (j < D) {
+        {
+            // every lane takes part (the shuffles need the whole warp); lanes past the last column add zeros
             const uint32_t *xb = reinterpret_cast<const uint32_t *>(X);
             auto add = [&](uint32_t w) {
                 const unsigned f = (w >> 23) & 0xFFu;
@@ -538,15 +579,30 @@ __global__ void __launch_bounds__(kMeanThreads) list_mean_kernel(const float *__
                 nneg += (unsigned)(w >> 31);
                 asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(vlo ^ neg), "l"(vhi ^ neg));
             };
-            int64_t p = b + rg;
-            for (; p + 3 * RG < e; p += 4 * RG) {
-                uint32_t w[4];
+            // row group rg takes a consecutive run of the piece; its warps read 32 ids at a time (one per
+            // lane, consecutive) and hand them round by shuffles, with eight row loads in flight
+            const int64_t per = (e - b + RG - 1) / RG;
+            const int64_t r0 = min(e, b + rg * per), r1 = min(e, r0 + per);
+            const int lane = threadIdx.x & 31;
+            for (int64_t p0 = r0; p0 < r1; p0 += 32) {
+                const int cnt = (int)min((int64_t)32, r1 - p0);
+                const int64_t myid = lane < cnt ? ids[p0 + lane] : 0;
+                int t = 0;
+                for (; t + 8 <= cnt; t += 8) {
+                    uint32_t w[8];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) w[q] = xb[ids[p + q * RG] * D + j];
+                    for (int q = 0; q < 8; ++q) {
+                        const int64_t row = __shfl_sync(0xffffffffu, myid, t + q);
+                        w[q] = j < D ? xb[row * D + j] : 0u;
+                    }
 #pragma unroll
-                for (int q = 0; q < 4; ++q) add(w[q]);
+                    for (int q = 0; q < 8; ++q) add(w[q]);
+                }
+                for (; t < cnt; ++t) {
+                    const int64_t row = __shfl_sync(0xffffffffu, myid, t);
+                    add(j < D ? xb[row * D + j] : 0u);
+                }
             }
-            for (; p < e; p += RG) add(xb[ids[p] * D + j]);
         }
         s_lo[threadIdx.x] = lo;
         s_hi[threadIdx.x] = hi;
@@ -556,18 +612,59 @@ __global__ void __launch_bounds__(kMeanThreads) list_mean_kernel(const float *__
     }
     __syncthreads();
     if (rg == 0 && j < D) {
+        unsigned long long lo = 0ull, hi = 0ull;
+        unsigned nneg = 0u, emin = 255u;
+        float sabs = 0.0f;
+        for (int r = 0; r < RG; ++r) {
+            const int t = r * Dp + j;
+            asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(s_lo[t]), "l"(s_hi[t]));
+            nneg += s_neg[t];
+            emin = min(emin, s_emin[t]);
+            sabs += s_abs[t];
+        }
+        const size_t o = (size_t)pc * D + j;
+        part.lo[o] = lo;
+        part.hi[o] = hi;
+        part.neg[o] = nneg;
+        part.emin[o] = emin;
+        part.abs[o] = sabs;
+    }
+}
+
+// The mean of every column of list l from its pieces' partials: exact when the row-order FP64 sum is
+// provably the exact sum, else (flagged columns) that row-order sum by one warp per column.
+__global__ void __launch_bounds__(kMeanThreads) list_mean_kernel(const float *__restrict__ X, int D,
+                                                                 const int64_t *__restrict__ offsets,
+                                                                 const int64_t *__restrict__ ids,
+                                                                 const unsigned *__restrict__ xrange,
+                                                                 const int *__restrict__ pbeg,
+                                                                 const ListMeanScratch part, float *__restrict__ C)
+{
+    __shared__ int s_flag[256];
+    __shared__ int s_nflag;
+    const int l = blockIdx.x;
+    const int64_t b = offsets[l], e = offsets[l + 1];
+    if (e == b) return;  // empty list keeps its centroid
+    const int64_t n = e - b;
+    const int j = threadIdx.x;
+    unsigned g = xrange[0], gmax = xrange[1];
+    if (g > gmax) g = gmax = 1u;  // X is all zeros
+    const bool fast = list_sum_fast(g, gmax, n);
+    if (threadIdx.x == 0) s_nflag = 0;
+    __syncthreads();
+    if (j < D) {
         bool exact = false;
         double sum = 0.0;
         if (fast) {
             unsigned long long lo = 0ull, hi = 0ull, nneg = 0ull;
             unsigned emin = 255u;
             float sabs = 0.0f;
-            for (int r = 0; r < RG; ++r) {
-                const int t = r * Dp + j;
-                asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(s_lo[t]), "l"(s_hi[t]));
-                nneg += s_neg[t];
-                emin = min(emin, s_emin[t]);
-                sabs += s_abs[t];
+            for (int pc = pbeg[l]; pc < pbeg[l + 1]; ++pc) {
+                const size_t o = (size_t)pc * D + j;
+                asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(part.lo[o]), "l"(part.hi[o]));
+                nneg += part.neg[o];
+                emin = min(emin, part.emin[o]);
+                sabs += part.abs[o];
             }
             asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(lo), "+l"(hi) : "l"(nneg));
             if (emin == 255u) {
@@ -696,14 +793,33 @@ int launch_x_exponent_range(const float *X, int64_t N, int D, unsigned *xrange, 
     return PQ_OK;
 }
 
-int launch_list_mean(const float *X, int D, const int64_t *offsets, const int64_t *ids, int nlist,
-                     const unsigned *xrange, float *C, cudaStream_t s)
+int list_mean_scratch(int64_t N, int D, int nlist, Scratch &ws, ListMeanScratch &lm)
 {
-    ProfScope ps("list_mean", s);
+    // at most N / kPieceRows + nlist pieces (every list rounds its piece count up once)
+    lm.pmax = N / kPieceRows + nlist + 1;
+    if (lm.pmax > INT_MAX / 2) return fail(PQ_ENOTSUP, "too many rows for list means");
+    lm.pbeg = ws.get<int>((size_t)nlist + 1);
+    lm.piece_list = ws.get<int>((size_t)lm.pmax);
+    lm.lo = ws.get<unsigned long long>((size_t)lm.pmax * D);
+    lm.hi = ws.get<unsigned long long>((size_t)lm.pmax * D);
+    lm.neg = ws.get<unsigned>((size_t)lm.pmax * D);
+    lm.emin = ws.get<unsigned>((size_t)lm.pmax * D);
+    lm.abs = ws.get<float>((size_t)lm.pmax * D);
+    return ws.status;
+}
+
+int launch_list_mean(const float *X, int D, const int64_t *offsets, const int64_t *ids, int nlist,
+                     const unsigned *xrange, float *C, const ListMeanScratch &lm, cudaStream_t s)
+{
     if (D > 256) return fail(PQ_ENOTSUP, "list means support D <= 256");
+    if (lm.pmax <= 0) return fail(PQ_EINTERNAL, "list means without scratch");
+    ProfScope ps("list_mean", s);
     const int Dp = (D + 31) / 32 * 32;
-    list_mean_kernel<<<nlist, Dp * (kMeanThreads / Dp), 0, s>>>(X, D, offsets, ids, xrange, C);
-    count_launch();
+    list_pieces_kernel<<<1, 1024, 0, s>>>(offsets, nlist, lm.pbeg, lm.piece_list);
+    list_partial_kernel<<<(unsigned)lm.pmax, Dp * (kMeanThreads / Dp), 0, s>>>(X, D, offsets, ids, xrange, lm.pbeg,
+                                                                               nlist, lm.piece_list, lm);
+    list_mean_kernel<<<nlist, kMeanThreads, 0, s>>>(X, D, offsets, ids, xrange, lm.pbeg, lm, C);
+    count_launch(3);
     PQ_TRY_CUDA(cudaGetLastError());
     return PQ_OK;
 }

@@ -175,8 +175,19 @@ int bucket_rows(const int32_t *list_of_row, int64_t N, int nlist, const uint8_t 
 // exact integer sums where those are provably equal).  xrange = [min, max] biased exponent of
 // the nonzero elements of X, from launch_x_exponent_range (X is the same for every update).
 int launch_x_exponent_range(const float *X, int64_t N, int D, unsigned *xrange, cudaStream_t s);
+// The update cuts every list into pieces of up to 2,048 rows (one block each) and then adds each
+// list's piece sums: its scratch, for N rows in nlist lists, is allocated once per build.
+struct ListMeanScratch {
+    int64_t pmax = 0;                       // pieces at most
+    int *pbeg = nullptr;                    // [nlist + 1] first piece of every list
+    int *piece_list = nullptr;              // [pmax] list of every piece
+    unsigned long long *lo = nullptr, *hi = nullptr;  // [pmax][D] 128-bit integer column sums of a piece
+    unsigned *neg = nullptr, *emin = nullptr;         // [pmax][D] negative terms, smallest exponent
+    float *abs = nullptr;                   // [pmax][D] FP32 sum of magnitudes
+};
+int list_mean_scratch(int64_t N, int D, int nlist, Scratch &ws, ListMeanScratch &lm);
 int launch_list_mean(const float *X, int D, const int64_t *offsets, const int64_t *ids, int nlist,
-                     const unsigned *xrange, float *C, cudaStream_t s);
+                     const unsigned *xrange, float *C, const ListMeanScratch &lm, cudaStream_t s);
 
 // ---- code-space coarse quantizer (codes_ivf.cu) ----------------------------
 // Centre codes [nlist][M] by k-means over the PQ codes (symmetric distance), the decoded
